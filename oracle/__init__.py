@@ -1,0 +1,392 @@
+"""Plain FP64 CPU oracle for the vdW-DF nonlocal correlation hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
+this package.  The library (``paper_0810_2273_gb300``) never imports it, and
+it never imports the library: the two share no code.  Inputs come from the
+seeded generators in ``paper_0810_2273_gb300.inputs`` (which hold none of the
+method's arithmetic) as plain NumPy arrays.
+
+The arithmetic lives in ``oracle.c`` (FP64, OpenMP over independent outputs);
+this module is marshalling plus the grid-level assembly, each step citing the
+passage it follows.  Paper: Lazic et al., "JuNoLo", arXiv 0810.2273.
+
+Parity status: see the header of ``oracle.c``.  The paper's own Appendix
+energies are *parity unpinned* (the density file they come from is absent).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# Quadrature settings for Dion eq. (14): (a_min, log_ratio, n_log, m_half, n_osc);
+# the a- and b-integrals are truncated at A = (m_half + 1/2) pi, where cos A = 0.
+# REFERENCE: A = 255.5 pi ~ 803, truncation error ~ 4/A^4 ~ 1e-11.
+QUAD_REFERENCE = dict(a_min=1e-7, log_ratio=1.5, n_log=8, m_half=255, n_osc=10)
+# TABLE: the node table the parity tests feed to both sides (A ~ 99, ~4e-8).
+QUAD_TABLE = dict(a_min=1e-7, log_ratio=2.0, n_log=8, m_half=31, n_osc=10)
+# FAST: per-pair direct quadrature in the brute-force pin (A ~ 49, ~7e-7).
+QUAD_FAST = dict(a_min=1e-6, log_ratio=2.0, n_log=6, m_half=15, n_osc=8)
+
+C_ASYM = 12.0 * (4.0 * np.pi / 9.0) ** 3   # Dion eq. (17)
+ZAB = -0.8491                               # Dion eq. (12)
+
+_LIB = None
+_d = ctypes.c_double
+_i = ctypes.c_int
+_p = ctypes.c_void_p
+
+
+def lib():
+    """Load (building first if needed) the oracle's shared library."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.orc_grid_size.restype = _i
+        L.orc_grid_size.argtypes = [_d, _d, _i, _i, _i]
+        L.orc_grid.restype = _i
+        L.orc_grid.argtypes = [_d, _d, _i, _i, _i, _p, _p]
+        L.orc_W.restype = _d
+        L.orc_W.argtypes = [_d, _d]
+        L.orc_phi_many.restype = _i
+        L.orc_phi_many.argtypes = [_i, _p, _p, _p, _d, _d, _i, _i, _i]
+        L.orc_phi_table.restype = _i
+        L.orc_phi_table.argtypes = [_i, _d, _i, _p, _d, _d, _i, _i, _i]
+        L.orc_spline_prepare.restype = _i
+        L.orc_spline_prepare.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p]
+        L.orc_spline_eval_many.restype = _i
+        L.orc_spline_eval_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p]
+        L.orc_kernel_many.restype = _i
+        L.orc_kernel_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p]
+        L.orc_pair_AU.restype = _i
+        L.orc_pair_AU.argtypes = ([_i, _p, _p, _p, _p, _p, _i, _i, _i, _d, _d, _d, _i, _i, _i, _d,
+                                   _i, _d, _i, _d, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p])
+        L.orc_pair_brute.restype = _i
+        L.orc_pair_brute.argtypes = ([_i, _p, _p, _p, _p, _p, _i, _i, _i, _d, _d, _d, _i, _i, _i,
+                                      _d, _d, _d, _d, _d, _i, _i, _i, _p])
+        L.orc_gradient.restype = _i
+        L.orc_gradient.argtypes = [_i, _i, _i, _d, _d, _d, _p, _p]
+        L.orc_gradient_T.restype = _i
+        L.orc_gradient_T.argtypes = [_i, _i, _i, _d, _d, _d, _p, _p]
+        L.orc_eps_c.restype = _i
+        L.orc_eps_c.argtypes = [_i, _p, _p, _p]
+        L.orc_q0.restype = _i
+        L.orc_q0.argtypes = [_i, _p, _p, _p, _p, _p]
+        _LIB = L
+    return _LIB
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _q(quad):
+    return (quad["a_min"], quad["log_ratio"], quad["n_log"], quad["m_half"], quad["n_osc"])
+
+
+# --------------------------------------------------------------------------
+# Kernel phi (section 2; Dion eq. 14 and 17)
+# --------------------------------------------------------------------------
+def grid(quad=QUAD_REFERENCE):
+    """Quadrature nodes and weights on (0, (m_half + 1/2) pi]."""
+    L = lib()
+    n = L.orc_grid_size(*_q(quad))
+    a = np.zeros(n)
+    w = np.zeros(n)
+    if L.orc_grid(*_q(quad), _ptr(a), _ptr(w)) != n:
+        raise ValueError("bad quadrature settings")
+    return a, w
+
+
+def W(a, b):
+    """Dion's W(a, b) (eq. 14), from the factored form (see oracle.c)."""
+    L = lib()
+    a = np.atleast_1d(np.asarray(a, dtype=np.float64))
+    b = np.atleast_1d(np.asarray(b, dtype=np.float64))
+    a, b = np.broadcast_arrays(a, b)
+    return np.array([L.orc_W(float(x), float(y)) for x, y in zip(a.ravel(), b.ravel())]).reshape(a.shape)
+
+
+def phi(d1, d2, quad=QUAD_REFERENCE):
+    """phi(d1, d2) by direct quadrature of Dion eq. (14)."""
+    d1 = np.atleast_1d(_f64(d1))
+    d2 = np.atleast_1d(_f64(d2))
+    d1, d2 = np.broadcast_arrays(d1, d2)
+    d1 = _f64(d1.ravel())
+    d2 = _f64(d2.ravel())
+    out = np.zeros_like(d1)
+    rc = lib().orc_phi_many(len(d1), _ptr(d1), _ptr(d2), _ptr(out), *_q(quad))
+    if rc != 0:
+        raise RuntimeError("orc_phi_many failed (%d)" % rc)
+    return out
+
+
+def phi_asym(d1, d2):
+    """Large-D asymptote, Dion eq. (17): -C / (d1^2 d2^2 (d1^2 + d2^2))."""
+    d1 = np.asarray(d1, dtype=np.float64)
+    d2 = np.asarray(d2, dtype=np.float64)
+    return -C_ASYM / (d1 ** 2 * d2 ** 2 * (d1 ** 2 + d2 ** 2))
+
+
+def phi_table(nD=400, Dmax=30.0, ndelta=200, quad=QUAD_TABLE):
+    """Node table phi(D_k, delta_l), D_k = Dmax k/(nD-1), delta_l = l/ndelta.
+
+    Row 0 (D = 0, where eq. 14 diverges logarithmically) holds
+    (4 phi(D_1) - phi(D_2)) / 3, the even quadratic through rows 1 and 2.
+    """
+    nodes = np.zeros((nD, ndelta))
+    rc = lib().orc_phi_table(nD, Dmax, ndelta, _ptr(nodes), *_q(quad))
+    if rc != 0:
+        raise RuntimeError("orc_phi_table failed (%d)" % rc)
+    return nodes
+
+
+class Spline:
+    """Tensor-product cubic spline through the node table (M form).
+
+    Boundary conditions: zero slope at D = 0 and delta = 0, zero curvature at
+    the last node of each axis.  ``kernel`` adds the D > Dmax asymptote.
+    """
+
+    def __init__(self, nodes, Dmax=30.0):
+        self.f = _f64(nodes)
+        self.nD, self.nd = self.f.shape
+        self.Dmax = float(Dmax)
+        self.hD = self.Dmax / (self.nD - 1)
+        self.hd = 1.0 / self.nd
+        self.fDD = np.zeros_like(self.f)
+        self.fdd = np.zeros_like(self.f)
+        self.fDDdd = np.zeros_like(self.f)
+        rc = lib().orc_spline_prepare(self.nD, self.hD, self.nd, self.hd, _ptr(self.f),
+                                      _ptr(self.fDD), _ptr(self.fdd), _ptr(self.fDDdd))
+        if rc != 0:
+            raise RuntimeError("orc_spline_prepare failed (%d)" % rc)
+
+    def _args(self):
+        return (self.nD, self.hD, self.nd, self.hd, _ptr(self.f), _ptr(self.fDD),
+                _ptr(self.fdd), _ptr(self.fDDdd))
+
+    def eval(self, D, dl):
+        """Spline value and partials (phi, dphi/dD, dphi/ddelta) inside the table."""
+        D = np.atleast_1d(_f64(D))
+        dl = np.atleast_1d(_f64(dl))
+        D, dl = np.broadcast_arrays(D, dl)
+        D = _f64(D.ravel())
+        dl = _f64(dl.ravel())
+        p, pD, pd = (np.zeros_like(D) for _ in range(3))
+        lib().orc_spline_eval_many(*self._args(), len(D), _ptr(D), _ptr(dl), _ptr(p), _ptr(pD), _ptr(pd))
+        return p, pD, pd
+
+    def kernel(self, r, qi, qj):
+        """phi and r dphi/dd1 for pairs (d1 = qi r, d2 = qj r); returns (phi, rdphi1, nclamped)."""
+        r, qi, qj = (np.atleast_1d(_f64(x)) for x in (r, qi, qj))
+        r, qi, qj = (_f64(x.ravel()) for x in np.broadcast_arrays(r, qi, qj))
+        p = np.zeros_like(r)
+        rd = np.zeros_like(r)
+        ncl = lib().orc_kernel_many(*self._args(), len(r), _ptr(r), _ptr(qi), _ptr(qj), _ptr(p), _ptr(rd))
+        return p, rd, ncl
+
+
+# --------------------------------------------------------------------------
+# Gradient and q0 (section 3 "gradient"; Dion eqs. 11-12)
+# --------------------------------------------------------------------------
+def gradient(f, h):
+    """4th-order periodic central differences along the three axes -> (3, n0, n1, n2)."""
+    f = _f64(f)
+    g = np.zeros((3,) + f.shape)
+    lib().orc_gradient(*f.shape, *map(float, h), _ptr(f), _ptr(g))
+    return g
+
+
+def gradient_T(w, h):
+    """sum over axes of the transposed stencil applied to w (3, n0, n1, n2)."""
+    w = _f64(w)
+    out = np.zeros(w.shape[1:])
+    lib().orc_gradient_T(*w.shape[1:], *map(float, h), _ptr(w), _ptr(out))
+    return out
+
+
+def eps_c(rs):
+    """PW92 LDA correlation energy per electron and d eps_c / d rs (Hartree)."""
+    rs = np.atleast_1d(_f64(rs))
+    e = np.zeros_like(rs)
+    de = np.zeros_like(rs)
+    lib().orc_eps_c(len(rs), _ptr(rs), _ptr(e), _ptr(de))
+    return e, de
+
+
+def q0(n, g):
+    """q0 and its partials dq0/dn, dq0/dgrad n at every grid point."""
+    n = _f64(n)
+    g = _f64(g).reshape((3,) + n.shape)
+    N = n.size
+    q = np.zeros(n.shape)
+    qn = np.zeros(n.shape)
+    qg = np.zeros((3,) + n.shape)
+    lib().orc_q0(N, _ptr(n), _ptr(g), _ptr(q), _ptr(qn), _ptr(qg))
+    return q, qn, qg
+
+
+# --------------------------------------------------------------------------
+# The double sum and its adjoint (section 2 eq. 2; section 3)
+# --------------------------------------------------------------------------
+class Problem:
+    """A density on an orthorhombic periodic grid, trimmed at n_cut.
+
+    dims: (n0, n1, n2); lengths: (L0, L1, L2) bohr; periodic: 3 flags;
+    rc: spherical pair cutoff in bohr (<= 0: none; required if periodic).
+    """
+
+    def __init__(self, density, lengths, periodic, n_cut, rc, spline):
+        self.n = _f64(density)
+        self.dims = self.n.shape
+        self.lengths = tuple(float(x) for x in lengths)
+        self.periodic = tuple(int(bool(p)) for p in periodic)
+        self.n_cut = float(n_cut)
+        self.rc = float(rc)
+        self.spline = spline
+        self.h = tuple(L / d for L, d in zip(self.lengths, self.dims))
+        self.dV = float(np.prod(self.lengths)) / float(np.prod(self.dims))
+        self.g = gradient(self.n, self.h)
+        self.q0, self.dq0dn, self.dq0dg = q0(self.n, self.g)
+        flat = self.n.ravel()
+        self.active = np.nonzero(flat >= self.n_cut)[0]          # row-major order
+        self.slot = -np.ones(flat.size, dtype=np.int64)
+        self.slot[self.active] = np.arange(len(self.active))
+        i0, i1, i2 = np.unravel_index(self.active, self.dims)
+        self.i0, self.i1, self.i2 = _i32(i0), _i32(i1), _i32(i2)
+        self.na = _f64(flat[self.active])
+        self.qa = _f64(self.q0.ravel()[self.active])
+
+    @property
+    def n_active(self):
+        return len(self.active)
+
+    def AU(self, queries=None):
+        """A_i, U_i, pair counts and clamp counts for active slots ``queries``."""
+        if queries is None:
+            queries = np.arange(self.n_active)
+        qidx = _i32(queries)
+        A = np.zeros(len(qidx))
+        U = np.zeros(len(qidx))
+        npairs = np.zeros(len(qidx), dtype=np.int64)
+        ncl = np.zeros(len(qidx), dtype=np.int64)
+        s = self.spline
+        rc = lib().orc_pair_AU(self.n_active, _ptr(self.i0), _ptr(self.i1), _ptr(self.i2),
+                               _ptr(self.na), _ptr(self.qa), *self.dims, *self.lengths,
+                               *self.periodic, self.rc, *s._args(), len(qidx), _ptr(qidx),
+                               _ptr(A), _ptr(U), _ptr(npairs), _ptr(ncl))
+        if rc != 0:
+            raise RuntimeError("orc_pair_AU failed (%d)" % rc)
+        return A, U, npairs, ncl
+
+    def energy(self):
+        """E = 1/2 dV^2 sum_i n_i A_i, its self-term part, pair count (all active points)."""
+        A, U, npairs, ncl = self.AU()
+        E = 0.5 * self.dV ** 2 * float(np.dot(self.na, A))
+        E_diag = 0.5 * self.dV ** 2 * float(np.dot(self.na, self.na)) * self.spline.f[0, 0]
+        return dict(E=E, E_diag=E_diag, pairs=int(npairs.sum()), clamped=int(ncl.sum()), A=A, U=U)
+
+    def potential(self, A=None, U=None):
+        """v = dE/dn / dV on the whole grid (mask frozen):
+        v_m = dV [chi_m (A_m + U_m dq0/dn_m) + sum_ax (D_ax^T w_ax)_m],
+        w_ax = chi U dq0/dgrad_ax.  Needs A, U at every active point."""
+        if A is None or U is None:
+            A, U, _, _ = self.AU()
+        flat_n = self.n.size
+        Ag = np.zeros(flat_n)
+        Ug = np.zeros(flat_n)
+        Ag[self.active] = A
+        Ug[self.active] = U
+        w = self.dq0dg.reshape(3, -1) * Ug[None, :]
+        div = gradient_T(w.reshape((3,) + self.dims), self.h).ravel()
+        chi = np.zeros(flat_n)
+        chi[self.active] = 1.0
+        v = self.dV * (chi * (Ag + Ug * self.dq0dn.ravel()) + div)
+        return v.reshape(self.dims)
+
+    def potential_at(self, points):
+        """v at flat grid indices ``points`` from A, U at only the active points
+        in their stencil neighbourhoods (each point and +-1, +-2 along each axis)."""
+        points = np.asarray(points, dtype=np.int64)
+        d = self.dims
+        need = set()
+        coords = np.stack(np.unravel_index(points, d), axis=1)
+        for c in coords:
+            for ax in range(3):
+                for o in (-2, -1, 0, 1, 2):
+                    cc = list(c)
+                    cc[ax] = (cc[ax] + o) % d[ax]
+                    m = np.ravel_multi_index(cc, d)
+                    if self.slot[m] >= 0:
+                        need.add(int(self.slot[m]))
+        need = np.array(sorted(need), dtype=np.int64)
+        A, U, _, _ = self.AU(need)
+        Amap = dict(zip(need.tolist(), A.tolist()))
+        Umap = dict(zip(need.tolist(), U.tolist()))
+        c4 = (1.0 / 12.0, -8.0 / 12.0, 0.0, 8.0 / 12.0, -1.0 / 12.0)
+        out = np.zeros(len(points))
+        qn = self.dq0dn.ravel()
+        qg = self.dq0dg.reshape(3, -1)
+        for t, (m, c) in enumerate(zip(points, coords)):
+            val = 0.0
+            s = int(self.slot[m])
+            if s >= 0:
+                val += Amap[s] + Umap[s] * qn[m]
+            # sum_ax (D^T w)_m = sum_ax sum_o c_o w_{m-o} / h_ax
+            for ax in range(3):
+                for o in (-2, -1, 1, 2):
+                    cc = list(c)
+                    cc[ax] = (cc[ax] - o) % d[ax]
+                    mm = int(np.ravel_multi_index(cc, d))
+                    ss = int(self.slot[mm])
+                    if ss >= 0:
+                        val += c4[o + 2] * Umap[ss] * qg[ax, mm] / self.h[ax]
+            out[t] = self.dV * val
+        return out
+
+    def brute_energy(self, quad=QUAD_FAST):
+        """E from direct quadrature of eq. (14) at every pair (no table)."""
+        out = ctypes.c_double(0.0)
+        rc = lib().orc_pair_brute(self.n_active, _ptr(self.i0), _ptr(self.i1), _ptr(self.i2),
+                                  _ptr(self.na), _ptr(self.qa), *self.dims, *self.lengths,
+                                  *self.periodic, self.rc, self.spline.Dmax,
+                                  float(self.spline.f[0, 0]), *_q(quad), ctypes.byref(out))
+        if rc != 0:
+            raise RuntimeError("orc_pair_brute failed (%d)" % rc)
+        return 0.5 * self.dV ** 2 * out.value
+
+
+_TABLE_CACHE = {}
+
+
+def cached_table(nD=400, Dmax=30.0, ndelta=200, quad=QUAD_TABLE, cache_dir=None):
+    """phi_table(), memoised in-process and on disk (under .cache/ at the repo root)."""
+    key = (nD, float(Dmax), ndelta) + _q(quad)
+    if key in _TABLE_CACHE:
+        return _TABLE_CACHE[key]
+    if cache_dir is None:
+        cache_dir = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), ".cache")
+    name = "oracle_phi_%d_%g_%d_%g_%g_%d_%d_%d.npy" % key
+    path = os.path.join(cache_dir, name)
+    if os.path.exists(path):
+        nodes = np.load(path)
+    else:
+        nodes = phi_table(nD, Dmax, ndelta, quad)
+        os.makedirs(cache_dir, exist_ok=True)
+        tmp = path + ".tmp%d.npy" % os.getpid()
+        np.save(tmp, nodes)
+        os.replace(tmp, path)
+    _TABLE_CACHE[key] = nodes
+    return nodes

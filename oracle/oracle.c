@@ -1,0 +1,727 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU oracle for the vdW-DF nonlocal correlation
+ * hot path of JuNoLo (Lazic et al., arXiv 0810.2273).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library (paper_0810_2273_gb300/)
+ * may include, link, load or call this file.  Only tests/, the smoke() check in
+ * __graft_entry__.py and the cpu_baseline / reference arm of bench.py use it.
+ * It shares no code, header, table or constant generator with the CUDA path.
+ *
+ * What it computes (paper section 2, eqs. (1)-(2)):
+ *     E_c^nl = 1/2 sum_i sum_j n_i phi(q0_i r_ij, q0_j r_ij) n_j  dV^2
+ * over grid points with n >= n_cut (section 3, density trimming), including
+ * periodic images (section 3, "the charge density from the 0th cell must be
+ * repeated in space"), with the kernel phi of Dion et al. (PRL 92, 246401,
+ * eq. 14) tabulated in (D, delta) (section 2: "redefined to depend on two
+ * quantities, D >= 0 and 0 <= delta < 1") and its large-D asymptote (Dion
+ * eq. 17, section 2).  It also gives the adjoint potential v = dE/dn / dV.
+ *
+ * Every function below is written straight from its definition, with no
+ * blocking, fusion or reordering beyond what the definition states.  Where the
+ * paper is silent the reading used is stated at the function.
+ *
+ * Parity status of each function (pins live in tests/test_oracle_*.py):
+ *   orc_W, orc_phi, orc_phi_table  pinned: symmetry, zero integral, large-D
+ *                                   asymptote, small-D logarithm, printed-W
+ *                                   formula at high precision
+ *   orc_spline_*                    pinned: node reproduction, exact cubic
+ *                                   reproduction, 1-D library spline
+ *   orc_eps_c, orc_q0               pinned: k_F and gradient-term hand values,
+ *                                   high-density limit, partials vs FD
+ *   orc_gradient, orc_gradient_T    pinned: Fourier symbol, adjoint identity
+ *   orc_pair_AU                     pinned: brute force with direct
+ *                                   quadrature, translation invariance,
+ *                                   far-fragment asymptotic sum
+ *   paper-level energies            parity unpinned: the paper's Xe density
+ *                                   file is not available
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ---------------------------------------------------------------------- */
+/* Gauss-Legendre rule on [-1, 1]: roots of P_n by Newton's method on the   */
+/* three-term recurrence (textbook; Abramowitz & Stegun 25.4.29).           */
+/* ---------------------------------------------------------------------- */
+static void gl_rule(int n, double *x, double *w)
+{
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double pn = 0.0, dpn = 1.0;
+        for (int it = 0; it < 200; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            pn = (n == 1) ? z : p1;
+            double pm = (n == 1) ? 1.0 : p0;
+            dpn = n * (z * pn - pm) / (z * z - 1.0);
+            double dz = pn / dpn;
+            z -= dz;
+            if (fabs(dz) < 1e-15) {
+                /* one more evaluation of P'_n at the converged root */
+                p0 = 1.0; p1 = z;
+                for (int k = 2; k <= n; ++k) {
+                    double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                pn = (n == 1) ? z : p1;
+                pm = (n == 1) ? 1.0 : p0;
+                dpn = n * (z * pn - pm) / (z * z - 1.0);
+                break;
+            }
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dpn * dpn);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Quadrature grid on (0, A], A = (m + 1/2) pi.                             */
+/*  - (0, a_min) is dropped: the integrand vanishes like a^2 there.          */
+/*  - [a_min, 1]: panels of equal ratio (about log_ratio), n_log GL points.  */
+/*  - [1, A]: [1, 3pi/2] then unit-pi panels [(k-1/2)pi, (k+1/2)pi]; a panel */
+/*    starting at a_lo is cut into ceil(width / max(a_lo/4, pi/4)) equal     */
+/*    pieces (the switch of h(a/d) near a ~ d needs them for d of order 1),  */
+/*    n_osc GL points each.  Ending at cos(A) = 0 removes the leading 1/A^3  */
+/*    term of the truncated oscillatory tail (left error ~ 4/A^4).           */
+/* When a is NULL only the node count is returned.                          */
+/* ---------------------------------------------------------------------- */
+static int grid_fill(double a_min, double log_ratio, int n_log, int m_half, int n_osc,
+                     double *a, double *w)
+{
+    if (a_min <= 0.0 || a_min >= 1.0 || log_ratio <= 1.0 || n_log < 1 ||
+        m_half < 1 || n_osc < 1 || n_log > 64 || n_osc > 64)
+        return -1;
+    double xl[64], wl[64], xo[64], wo[64];
+    gl_rule(n_log, xl, wl);
+    gl_rule(n_osc, xo, wo);
+    int nlp = (int)ceil(log(1.0 / a_min) / log(log_ratio) - 1e-12);
+    if (nlp < 1) nlp = 1;
+    double rho = pow(1.0 / a_min, 1.0 / nlp);
+    int c = 0;
+    for (int p = 0; p < nlp; ++p) {
+        double lo = a_min * pow(rho, p);
+        double hi = (p == nlp - 1) ? 1.0 : a_min * pow(rho, p + 1);
+        for (int i = 0; i < n_log; ++i) {
+            if (a) {
+                a[c] = 0.5 * (lo + hi) + 0.5 * (hi - lo) * xl[i];
+                w[c] = 0.5 * (hi - lo) * wl[i];
+            }
+            ++c;
+        }
+    }
+    for (int k = 1; k <= m_half; ++k) {
+        double lo = (k == 1) ? 1.0 : (k - 0.5) * M_PI;
+        double hi = (k + 0.5) * M_PI;
+        double wmax = 0.25 * lo > 0.25 * M_PI ? 0.25 * lo : 0.25 * M_PI;
+        int sub = (int)ceil((hi - lo) / wmax - 1e-12);
+        if (sub < 1) sub = 1;
+        for (int q = 0; q < sub; ++q) {
+            double l2 = lo + (hi - lo) * q / sub, h2 = lo + (hi - lo) * (q + 1) / sub;
+            for (int i = 0; i < n_osc; ++i) {
+                if (a) {
+                    a[c] = 0.5 * (l2 + h2) + 0.5 * (h2 - l2) * xo[i];
+                    w[c] = 0.5 * (h2 - l2) * wo[i];
+                }
+                ++c;
+            }
+        }
+    }
+    return c;
+}
+
+int orc_grid_size(double a_min, double log_ratio, int n_log, int m_half, int n_osc)
+{
+    return grid_fill(a_min, log_ratio, n_log, m_half, n_osc, NULL, NULL);
+}
+
+int orc_grid(double a_min, double log_ratio, int n_log, int m_half, int n_osc,
+             double *a, double *w)
+{
+    return grid_fill(a_min, log_ratio, n_log, m_half, n_osc, a, w);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Dion eq. (14) ingredients.                                              */
+/*   W(a,b) = 2[(3-a^2) b cos b sin a + (3-b^2) a cos a sin b               */
+/*             + (a^2+b^2-3) sin a sin b - 3 a b cos a cos b] / (a^3 b^3)  */
+/* Collecting the bracket gives                                             */
+/*   a^2 sin a (sin b - b cos b) + b^2 sin b (sin a - a cos a)              */
+/*   - 3 (sin a - a cos a)(sin b - b cos b),                                */
+/* so with s(a) = sin a / a and u(a) = (sin a - a cos a)/a^3,               */
+/*   W = 2 [ s(a) u(b) + s(b) u(a) - 3 u(a) u(b) ].                         */
+/* u(a) is evaluated by its Maclaurin series for small a, where the printed */
+/* form cancels: u(a) = sum_k (-1)^k (2k+2) a^(2k) / (2k+3)!.               */
+/* ---------------------------------------------------------------------- */
+static double orc_s(double a) { return sin(a) / a; }
+
+static double orc_u(double a)
+{
+    if (a < 0.25) {
+        double a2 = a * a, term = 1.0, sum = 0.0, fact = 6.0; /* (2k+3)! at k=0 */
+        for (int k = 0; k < 10; ++k) {
+            sum += ((k & 1) ? -1.0 : 1.0) * (2.0 * k + 2.0) * term / fact;
+            term *= a2;
+            fact *= (2.0 * k + 4.0) * (2.0 * k + 5.0);
+        }
+        return sum;
+    }
+    return (sin(a) - a * cos(a)) / (a * a * a);
+}
+
+double orc_W(double a, double b)
+{
+    double sa = orc_s(a), sb = orc_s(b), ua = orc_u(a), ub = orc_u(b);
+    return 2.0 * (sa * ub + sb * ua - 3.0 * ua * ub);
+}
+
+/* h(y) = 1 - exp(-gamma y^2), gamma = 4 pi / 9 (Dion eq. 16);
+ * nu(y) = y^2 / (2 h(y/d)) (Dion eq. 15).  d = 0 gives h = 1. */
+static double orc_nu(double y, double d)
+{
+    if (d <= 0.0) return 0.5 * y * y;
+    const double gam = 4.0 * M_PI / 9.0;
+    double x = y / d;
+    double h = -expm1(-gam * x * x);
+    return 0.5 * y * y / h;
+}
+
+/* T(w,x,y,z) = 1/2 [1/(w+x) + 1/(y+z)] [1/((w+y)(x+z)) + 1/((w+z)(y+x))] */
+static double orc_T(double w, double x, double y, double z)
+{
+    return 0.5 * (1.0 / (w + x) + 1.0 / (y + z)) *
+           (1.0 / ((w + y) * (x + z)) + 1.0 / ((w + z) * (y + x)));
+}
+
+/* phi(d1, d2) = 2/pi^2 int_0^inf a^2 da int_0^inf b^2 db W(a,b)
+ *               T(nu(a), nu(b), nu'(a), nu'(b)),  nu uses d1, nu' uses d2.
+ * Full tensor-product double loop (no symmetry folding). */
+static double phi_on_grid(int N, const double *a, const double *WW,
+                          double d1, double d2, double *nu1, double *nu2)
+{
+    for (int i = 0; i < N; ++i) {
+        nu1[i] = orc_nu(a[i], d1);
+        nu2[i] = orc_nu(a[i], d2);
+    }
+    double total = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double row = 0.0;
+        const double *Wi = WW + (size_t)i * N;
+        for (int j = 0; j < N; ++j)
+            row += Wi[j] * orc_T(nu1[i], nu1[j], nu2[i], nu2[j]);
+        total += row;
+    }
+    return 2.0 / (M_PI * M_PI) * total;
+}
+
+static double *make_WW(int N, const double *a, const double *w)
+{
+    double *WW = (double *)malloc(sizeof(double) * (size_t)N * N);
+    if (!WW) return NULL;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+            WW[(size_t)i * N + j] = w[i] * w[j] * a[i] * a[i] * a[j] * a[j] * orc_W(a[i], a[j]);
+    return WW;
+}
+
+/* phi at a list of (d1, d2) points. */
+int orc_phi_many(int npts, const double *d1, const double *d2, double *out,
+                 double a_min, double log_ratio, int n_log, int m_half, int n_osc)
+{
+    int N = orc_grid_size(a_min, log_ratio, n_log, m_half, n_osc);
+    double *a = (double *)malloc(sizeof(double) * N);
+    double *w = (double *)malloc(sizeof(double) * N);
+    if (!a || !w) { free(a); free(w); return -2; }
+    if (orc_grid(a_min, log_ratio, n_log, m_half, n_osc, a, w) != N) { free(a); free(w); return -1; }
+    double *WW = make_WW(N, a, w);
+    if (!WW) { free(a); free(w); return -2; }
+    int err = 0;
+#pragma omp parallel
+    {
+        double *nu1 = (double *)malloc(sizeof(double) * N);
+        double *nu2 = (double *)malloc(sizeof(double) * N);
+        if (!nu1 || !nu2) {
+#pragma omp atomic write
+            err = -2;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int p = 0; p < npts; ++p)
+                out[p] = phi_on_grid(N, a, WW, d1[p], d2[p], nu1, nu2);
+        }
+        free(nu1);
+        free(nu2);
+    }
+    free(WW); free(a); free(w);
+    return err;
+}
+
+/* Node table phi(D_k, delta_l), D_k = Dmax k/(nD-1), delta_l = l/ndelta
+ * (section 2: phi tabulated in D and delta; section 7: grid limits fixed by
+ * refinement).  Row k = 0 (D = 0): eq. (14) diverges like -(2/pi) ln D there,
+ * so the row holds the value at D = 0 of the even quadratic c0 + c2 D^2
+ * through the nodes D_1 and D_2:  phi(0, delta) = (4 phi(D_1) - phi(D_2))/3. */
+int orc_phi_table(int nD, double Dmax, int ndelta, double *nodes,
+                  double a_min, double log_ratio, int n_log, int m_half, int n_osc)
+{
+    if (nD < 3 || ndelta < 2 || Dmax <= 0.0) return -1;
+    int npts = (nD - 1) * ndelta;
+    double *d1 = (double *)malloc(sizeof(double) * npts);
+    double *d2 = (double *)malloc(sizeof(double) * npts);
+    double *v = (double *)malloc(sizeof(double) * npts);
+    if (!d1 || !d2 || !v) { free(d1); free(d2); free(v); return -2; }
+    for (int k = 1; k < nD; ++k)
+        for (int l = 0; l < ndelta; ++l) {
+            double D = Dmax * k / (nD - 1), dl = (double)l / ndelta;
+            d1[(k - 1) * ndelta + l] = D * (1.0 + dl);
+            d2[(k - 1) * ndelta + l] = D * (1.0 - dl);
+        }
+    int rc = orc_phi_many(npts, d1, d2, v, a_min, log_ratio, n_log, m_half, n_osc);
+    if (rc == 0) {
+        for (int k = 1; k < nD; ++k)
+            for (int l = 0; l < ndelta; ++l)
+                nodes[(size_t)k * ndelta + l] = v[(k - 1) * ndelta + l];
+        for (int l = 0; l < ndelta; ++l)
+            nodes[l] = (4.0 * nodes[ndelta + l] - nodes[2 * ndelta + l]) / 3.0;
+    }
+    free(d1); free(d2); free(v);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Tensor-product cubic interpolating spline on the uniform (D, delta)      */
+/* node grid, written with second derivatives (the "M" form).  Boundary     */
+/* conditions (reading; the paper only says "lookup table", section 7):     */
+/* zero slope at D = 0 and delta = 0 (phi is even in r and in delta),       */
+/* zero second derivative at the last node of each axis.                    */
+/* ---------------------------------------------------------------------- */
+/* Solve for M_0..M_{N-1} of the 1-D spline through f (stride fs) with
+ * S'(x_0) = 0 and M_{N-1} = 0; result to M (stride ms). */
+static void spline_M_1d(int N, double h, const double *f, int fs, double *M, int ms,
+                        double *cp, double *dp)
+{
+    /* rows: 0: 2 M0 + M1 = 6 (f1 - f0)/h^2
+     *       i: M_{i-1} + 4 M_i + M_{i+1} = 6 (f_{i+1} - 2 f_i + f_{i-1})/h^2
+     *       N-1: M_{N-1} = 0                                                 */
+    double h2 = h * h;
+    /* Thomas algorithm on rows 0..N-2 with M_{N-1} = 0 substituted. */
+    int n = N - 1;
+    for (int i = 0; i < n; ++i) {
+        double diag, sup, rhs, sub;
+        if (i == 0) {
+            sub = 0.0; diag = 2.0; sup = 1.0;
+            rhs = 6.0 * (f[fs * 1] - f[0]) / h2;
+        } else {
+            sub = 1.0; diag = 4.0; sup = (i == n - 1) ? 0.0 : 1.0;
+            rhs = 6.0 * (f[fs * (i + 1)] - 2.0 * f[fs * i] + f[fs * (i - 1)]) / h2;
+        }
+        if (i == 0) {
+            cp[i] = sup / diag;
+            dp[i] = rhs / diag;
+        } else {
+            double den = diag - sub * cp[i - 1];
+            cp[i] = sup / den;
+            dp[i] = (rhs - sub * dp[i - 1]) / den;
+        }
+    }
+    M[ms * (N - 1)] = 0.0;
+    M[ms * (n - 1)] = dp[n - 1];
+    for (int i = n - 2; i >= 0; --i) M[ms * i] = dp[i] - cp[i] * M[ms * (i + 1)];
+}
+
+/* f: nD x nd nodes (row-major, D outer).  Outputs fDD, fdd, fDDdd same shape. */
+int orc_spline_prepare(int nD, double hD, int nd, double hd, const double *f,
+                       double *fDD, double *fdd, double *fDDdd)
+{
+    if (nD < 3 || nd < 3) return -1;
+    int nmax = nD > nd ? nD : nd;
+    double *cp = (double *)malloc(sizeof(double) * nmax);
+    double *dp = (double *)malloc(sizeof(double) * nmax);
+    if (!cp || !dp) { free(cp); free(dp); return -2; }
+    for (int l = 0; l < nd; ++l) spline_M_1d(nD, hD, f + l, nd, fDD + l, nd, cp, dp);
+    for (int k = 0; k < nD; ++k) spline_M_1d(nd, hd, f + (size_t)k * nd, 1, fdd + (size_t)k * nd, 1, cp, dp);
+    for (int k = 0; k < nD; ++k) spline_M_1d(nd, hd, fDD + (size_t)k * nd, 1, fDDdd + (size_t)k * nd, 1, cp, dp);
+    free(cp); free(dp);
+    return 0;
+}
+
+typedef struct {
+    int nD, nd;
+    double hD, hd;
+    const double *f, *fDD, *fdd, *fDDdd;
+} orc_spline;
+
+/* S(D, delta) and its partials, D in [0, (nD-1) hD], delta in [0, (nd-1) hd]. */
+static void spline_eval(const orc_spline *s, double D, double dl,
+                        double *phi, double *phiD, double *phid)
+{
+    double tD = D / s->hD, td = dl / s->hd;
+    int k = (int)floor(tD), l = (int)floor(td);
+    if (k > s->nD - 2) k = s->nD - 2;
+    if (k < 0) k = 0;
+    if (l > s->nd - 2) l = s->nd - 2;
+    if (l < 0) l = 0;
+    double t = tD - k, u = td - l;
+    double hD = s->hD, hd = s->hd;
+    /* 1-D cubic spline basis in the M form, and their derivatives. */
+    double al[2] = {1.0 - t, t};
+    double ga[2] = {((1.0 - t) * (1.0 - t) * (1.0 - t) - (1.0 - t)) * hD * hD / 6.0,
+                    (t * t * t - t) * hD * hD / 6.0};
+    double dal[2] = {-1.0 / hD, 1.0 / hD};
+    double dga[2] = {-(3.0 * (1.0 - t) * (1.0 - t) - 1.0) * hD / 6.0,
+                     (3.0 * t * t - 1.0) * hD / 6.0};
+    double be[2] = {1.0 - u, u};
+    double et[2] = {((1.0 - u) * (1.0 - u) * (1.0 - u) - (1.0 - u)) * hd * hd / 6.0,
+                    (u * u * u - u) * hd * hd / 6.0};
+    double dbe[2] = {-1.0 / hd, 1.0 / hd};
+    double det[2] = {-(3.0 * (1.0 - u) * (1.0 - u) - 1.0) * hd / 6.0,
+                     (3.0 * u * u - 1.0) * hd / 6.0};
+    double p = 0.0, pD = 0.0, pd = 0.0;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            size_t o = (size_t)(k + i) * s->nd + (l + j);
+            double F = s->f[o], FDD = s->fDD[o], Fdd = s->fdd[o], FDDdd = s->fDDdd[o];
+            p += al[i] * be[j] * F + ga[i] * be[j] * FDD + al[i] * et[j] * Fdd + ga[i] * et[j] * FDDdd;
+            pD += dal[i] * be[j] * F + dga[i] * be[j] * FDD + dal[i] * et[j] * Fdd + dga[i] * et[j] * FDDdd;
+            pd += al[i] * dbe[j] * F + ga[i] * dbe[j] * FDD + al[i] * det[j] * Fdd + ga[i] * det[j] * FDDdd;
+        }
+    *phi = p;
+    *phiD = pD;
+    *phid = pd;
+}
+
+int orc_spline_eval_many(int nD, double hD, int nd, double hd, const double *f,
+                         const double *fDD, const double *fdd, const double *fDDdd,
+                         int npts, const double *D, const double *dl,
+                         double *phi, double *phiD, double *phid)
+{
+    orc_spline s = {nD, nd, hD, hd, f, fDD, fdd, fDDdd};
+    for (int p = 0; p < npts; ++p) spline_eval(&s, D[p], dl[p], &phi[p], &phiD[p], &phid[p]);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* The kernel as the double sum uses it (section 2):                        */
+/*   D <= Dmax: the spline of the node table, delta clamped to the last     */
+/*              delta node (then d phi / d delta = 0);                      */
+/*   D >  Dmax: Dion eq. (17), phi = -C / (d1^2 d2^2 (d1^2 + d2^2)),        */
+/*              C = 12 (4 pi / 9)^3, d1 = D (1 + delta), d2 = D (1 - delta).*/
+/* Returns phi, and r * dphi/dd1 for the pair (d1 = q_i r, d2 = q_j r),     */
+/* with signed ds = (q_i - q_j)/(q_i + q_j) and                             */
+/*   dphi/dd1 = 1/2 phi_D + (1 - ds)/(2 D) phi_ds.                          */
+/* ---------------------------------------------------------------------- */
+static void kernel_pair(const orc_spline *s, double Dmax, double r, double qi, double qj,
+                        double *phi, double *rdphi1, int *clamped)
+{
+    const double C = 12.0 * pow(4.0 * M_PI / 9.0, 3);
+    double sq = qi + qj;
+    double D = 0.5 * r * sq;
+    double ds = (qi - qj) / sq;
+    double dl = fabs(ds);
+    if (D > Dmax) {
+        double d1 = qi * r, d2 = qj * r;
+        double d12 = d1 * d1, d22 = d2 * d2;
+        double p = -C / (d12 * d22 * (d12 + d22));
+        *phi = p;
+        double dp1 = -p * (2.0 / d1 + 2.0 * d1 / (d12 + d22));
+        *rdphi1 = r * dp1;
+        return;
+    }
+    double dlast = (s->nd - 1) * s->hd;
+    int cl = 0;
+    if (dl > dlast) { dl = dlast; cl = 1; }
+    double p, pD, pd;
+    spline_eval(s, D, dl, &p, &pD, &pd);
+    if (cl) pd = 0.0;
+    *clamped += cl;
+    *phi = p;
+    double sgn = (ds > 0.0) ? 1.0 : ((ds < 0.0) ? -1.0 : 0.0);
+    if (D > 0.0)
+        *rdphi1 = r * (0.5 * pD + (1.0 - ds) / (2.0 * D) * sgn * pd);
+    else
+        *rdphi1 = 0.0;
+}
+
+int orc_kernel_many(int nD, double hD, int nd, double hd, const double *f,
+                    const double *fDD, const double *fdd, const double *fDDdd,
+                    int npts, const double *r, const double *qi, const double *qj,
+                    double *phi, double *rdphi1)
+{
+    orc_spline s = {nD, nd, hD, hd, f, fDD, fdd, fDDdd};
+    double Dmax = (nD - 1) * hD;
+    int cl = 0;
+    for (int p = 0; p < npts; ++p) kernel_pair(&s, Dmax, r[p], qi[p], qj[p], &phi[p], &rdphi1[p], &cl);
+    return cl;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Pair sums (section 2 eq. (2), section 3: trimming, 0th cell + images).   */
+/* Active points p = 0..Na-1 at integer grid indices (i0,i1,i2) of an       */
+/* orthorhombic cell L0 x L1 x L2 on an n0 x n1 x n2 grid: r = (i0 L0/n0,    */
+/* i1 L1/n1, i2 L2/n2).  Periodic axes add images m L (|m| <= M); pairs with */
+/* |r_i - r_j + L| > rc are dropped when rc > 0 (spherical cutoff; the       */
+/* paper repeats cells until convergence, section 3 and 6.2).  The self     */
+/* term i = j, L = 0 is n_i phi(0,0) and always included.                   */
+/*   A_i = sum_{j,L} n_j phi_ijL,  U_i = n_i sum_{j,L} n_j r dphi/dd1.       */
+/* Also returns, per query, the number of (j, L) terms other than the self  */
+/* term (the ordered pair count) and how many had delta clamped.            */
+/* ---------------------------------------------------------------------- */
+int orc_pair_AU(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2,
+                const double *n, const double *q,
+                int n0, int n1, int n2, double L0, double L1, double L2,
+                int per0, int per1, int per2, double rc,
+                int nD, double hD, int nd, double hd, const double *f,
+                const double *fDD, const double *fdd, const double *fDDdd,
+                int nq, const int32_t *qidx, double *A, double *U,
+                int64_t *npairs, int64_t *nclamp)
+{
+    if ((per0 || per1 || per2) && !(rc > 0.0)) return -1;
+    orc_spline s = {nD, nd, hD, hd, f, fDD, fdd, fDDdd};
+    double Dmax = (nD - 1) * hD;
+    int M0 = per0 ? (int)ceil(rc / L0) + 1 : 0;
+    int M1 = per1 ? (int)ceil(rc / L1) + 1 : 0;
+    int M2 = per2 ? (int)ceil(rc / L2) + 1 : 0;
+    double h0 = L0 / n0, h1 = L1 / n1, h2 = L2 / n2;
+    double phi00 = f[0];
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int t = 0; t < nq; ++t) {
+        int i = qidx[t];
+        double xi = i0[i] * h0, yi = i1[i] * h1, zi = i2[i] * h2;
+        double a = 0.0, u = 0.0;
+        int64_t cnt = 0;
+        int cl = 0;
+        for (int j = 0; j < Na; ++j) {
+            double xj = i0[j] * h0, yj = i1[j] * h1, zj = i2[j] * h2;
+            for (int m0 = -M0; m0 <= M0; ++m0)
+                for (int m1 = -M1; m1 <= M1; ++m1)
+                    for (int m2 = -M2; m2 <= M2; ++m2) {
+                        if (j == i && m0 == 0 && m1 == 0 && m2 == 0) {
+                            a += n[i] * phi00;
+                            continue;
+                        }
+                        double dx = xi - xj + m0 * L0, dy = yi - yj + m1 * L1, dz = zi - zj + m2 * L2;
+                        double r = sqrt(dx * dx + dy * dy + dz * dz);
+                        if (rc > 0.0 && r > rc) continue;
+                        double p, rd;
+                        kernel_pair(&s, Dmax, r, q[i], q[j], &p, &rd, &cl);
+                        a += n[j] * p;
+                        u += n[j] * rd;
+                        ++cnt;
+                    }
+        }
+        A[t] = a;
+        U[t] = n[i] * u;
+        if (npairs) npairs[t] = cnt;
+        if (nclamp) nclamp[t] = cl;
+    }
+    return 0;
+}
+
+/* Brute force of the same sum with phi from direct quadrature of eq. (14)
+ * at every pair (no table, no spline); D > Dmax still takes eq. (17) and the
+ * self term uses phi00 given by the caller.  Returns sum_i n_i A_i. */
+int orc_pair_brute(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2,
+                   const double *n, const double *q,
+                   int n0, int n1, int n2, double L0, double L1, double L2,
+                   int per0, int per1, int per2, double rc, double Dmax, double phi00,
+                   double a_min, double log_ratio, int n_log, int m_half, int n_osc,
+                   double *sum_out)
+{
+    if ((per0 || per1 || per2) && !(rc > 0.0)) return -1;
+    const double C = 12.0 * pow(4.0 * M_PI / 9.0, 3);
+    int M0 = per0 ? (int)ceil(rc / L0) + 1 : 0;
+    int M1 = per1 ? (int)ceil(rc / L1) + 1 : 0;
+    int M2 = per2 ? (int)ceil(rc / L2) + 1 : 0;
+    double h0 = L0 / n0, h1 = L1 / n1, h2 = L2 / n2;
+    /* gather every ordered non-self term within the cutoff */
+    size_t cap = 1024, cnt = 0;
+    double *d1 = (double *)malloc(sizeof(double) * cap);
+    double *d2 = (double *)malloc(sizeof(double) * cap);
+    double *wt = (double *)malloc(sizeof(double) * cap);
+    if (!d1 || !d2 || !wt) { free(d1); free(d2); free(wt); return -2; }
+    double asym = 0.0, self = 0.0;
+    for (int i = 0; i < Na; ++i) {
+        self += n[i] * n[i] * phi00;
+        for (int j = 0; j < Na; ++j)
+            for (int m0 = -M0; m0 <= M0; ++m0)
+                for (int m1 = -M1; m1 <= M1; ++m1)
+                    for (int m2 = -M2; m2 <= M2; ++m2) {
+                        if (j == i && m0 == 0 && m1 == 0 && m2 == 0) continue;
+                        double dx = i0[i] * h0 - i0[j] * h0 + m0 * L0;
+                        double dy = i1[i] * h1 - i1[j] * h1 + m1 * L1;
+                        double dz = i2[i] * h2 - i2[j] * h2 + m2 * L2;
+                        double r = sqrt(dx * dx + dy * dy + dz * dz);
+                        if (rc > 0.0 && r > rc) continue;
+                        double D = 0.5 * r * (q[i] + q[j]);
+                        if (D > Dmax) {
+                            double a1 = q[i] * r, a2 = q[j] * r;
+                            asym += n[i] * n[j] * (-C / (a1 * a1 * a2 * a2 * (a1 * a1 + a2 * a2)));
+                            continue;
+                        }
+                        if (cnt == cap) {
+                            cap *= 2;
+                            double *t1 = (double *)realloc(d1, sizeof(double) * cap);
+                            double *t2 = (double *)realloc(d2, sizeof(double) * cap);
+                            double *t3 = (double *)realloc(wt, sizeof(double) * cap);
+                            if (!t1 || !t2 || !t3) {
+                                free(t1 ? t1 : d1); free(t2 ? t2 : d2); free(t3 ? t3 : wt);
+                                return -2;
+                            }
+                            d1 = t1; d2 = t2; wt = t3;
+                        }
+                        d1[cnt] = q[i] * r;
+                        d2[cnt] = q[j] * r;
+                        wt[cnt] = n[i] * n[j];
+                        ++cnt;
+                    }
+    }
+    double *ph = (double *)malloc(sizeof(double) * (cnt ? cnt : 1));
+    if (!ph) { free(d1); free(d2); free(wt); return -2; }
+    int rc2 = orc_phi_many((int)cnt, d1, d2, ph, a_min, log_ratio, n_log, m_half, n_osc);
+    double tab = 0.0;
+    for (size_t p = 0; p < cnt; ++p) tab += wt[p] * ph[p];
+    *sum_out = self + tab + asym;
+    free(d1); free(d2); free(wt); free(ph);
+    return rc2;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Gradient by real-space finite differences along the (orthogonal) axes    */
+/* (section 3: "real space finite differences ... perpendicular axes only"),*/
+/* 4th order central, periodic wrap on every axis:                          */
+/*   (D_h f)_m = (f_{m-2} - 8 f_{m-1} + 8 f_{m+1} - f_{m+2}) / (12 h).      */
+/* Grid row-major [n0][n1][n2]; g is [3][N].                                */
+/* ---------------------------------------------------------------------- */
+static const double orc_fd_c[5] = {1.0 / 12.0, -8.0 / 12.0, 0.0, 8.0 / 12.0, -1.0 / 12.0};
+
+int orc_gradient(int n0, int n1, int n2, double h0, double h1, double h2,
+                 const double *f, double *g)
+{
+    size_t N = (size_t)n0 * n1 * n2;
+    int dims[3] = {n0, n1, n2};
+    double hs[3] = {h0, h1, h2};
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int a = 0; a < n0; ++a)
+        for (int b = 0; b < n1; ++b)
+            for (int c = 0; c < n2; ++c) {
+                int idx[3] = {a, b, c};
+                size_t m = ((size_t)a * n1 + b) * n2 + c;
+                for (int ax = 0; ax < 3; ++ax) {
+                    double s = 0.0;
+                    for (int o = -2; o <= 2; ++o) {
+                        int jj[3] = {idx[0], idx[1], idx[2]};
+                        jj[ax] = ((idx[ax] + o) % dims[ax] + dims[ax]) % dims[ax];
+                        s += orc_fd_c[o + 2] * f[((size_t)jj[0] * n1 + jj[1]) * n2 + jj[2]];
+                    }
+                    g[ax * N + m] = s / hs[ax];
+                }
+            }
+    return 0;
+}
+
+/* out = sum_axes D_h^T w_ax, the transpose of the stencil above written out
+ * directly: (D_h^T w)_m = sum_o c_o w_{m-o} / h. */
+int orc_gradient_T(int n0, int n1, int n2, double h0, double h1, double h2,
+                   const double *w, double *out)
+{
+    size_t N = (size_t)n0 * n1 * n2;
+    int dims[3] = {n0, n1, n2};
+    double hs[3] = {h0, h1, h2};
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int a = 0; a < n0; ++a)
+        for (int b = 0; b < n1; ++b)
+            for (int c = 0; c < n2; ++c) {
+                int idx[3] = {a, b, c};
+                size_t m = ((size_t)a * n1 + b) * n2 + c;
+                double s = 0.0;
+                for (int ax = 0; ax < 3; ++ax)
+                    for (int o = -2; o <= 2; ++o) {
+                        int jj[3] = {idx[0], idx[1], idx[2]};
+                        jj[ax] = ((idx[ax] - o) % dims[ax] + dims[ax]) % dims[ax];
+                        s += orc_fd_c[o + 2] * w[ax * N + ((size_t)jj[0] * n1 + jj[1]) * n2 + jj[2]] / hs[ax];
+                    }
+                out[m] = s;
+            }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* LDA correlation: Perdew & Wang, PRB 45, 13244 (1992), spin-unpolarised   */
+/* (the paper names only "LDA", section 2 eq. (3)); Hartree units.          */
+/*   eps_c(rs) = -2A (1 + a1 rs) ln[1 + 1/(2A (b1 rs^1/2 + b2 rs            */
+/*                                          + b3 rs^3/2 + b4 rs^2))]        */
+/* ---------------------------------------------------------------------- */
+static const double PW_A = 0.031091, PW_a1 = 0.21370;
+static const double PW_b1 = 7.5957, PW_b2 = 3.5876, PW_b3 = 1.6382, PW_b4 = 0.49294;
+
+static void pw92(double rs, double *e, double *de_drs)
+{
+    double sr = sqrt(rs);
+    double Q0 = -2.0 * PW_A * (1.0 + PW_a1 * rs);
+    double Q1 = 2.0 * PW_A * (PW_b1 * sr + PW_b2 * rs + PW_b3 * rs * sr + PW_b4 * rs * rs);
+    double Q1p = PW_A * (PW_b1 / sr + 2.0 * PW_b2 + 3.0 * PW_b3 * sr + 4.0 * PW_b4 * rs);
+    double L = log(1.0 + 1.0 / Q1);
+    *e = Q0 * L;
+    *de_drs = -2.0 * PW_A * PW_a1 * L - Q0 * Q1p / (Q1 * Q1 + Q1);
+}
+
+int orc_eps_c(int N, const double *rs, double *e, double *de)
+{
+    for (int p = 0; p < N; ++p) pw92(rs[p], &e[p], &de[p]);
+    return 0;
+}
+
+/* q0 (Dion eqs. 11-12):  q0 = -(4 pi / 3) eps_xc^0 with
+ *   eps_xc^0 = eps_c^LDA + eps_x^LDA [1 - (Zab/9) s^2],
+ *   eps_x^LDA = -3 k_F / (4 pi),  k_F = (3 pi^2 n)^(1/3),
+ *   s = |grad n| / (2 k_F n),  Zab = -0.8491.
+ * Partials (closed form):
+ *   dq0/dn    = k_F/(3n) + (7 Zab/108) |g|^2/(k_F n^3) - (4 pi/3) d eps_c/dn
+ *   dq0/dgrad = -(Zab/18) g / (k_F n^2)
+ * Points with n <= 0 get zeros. */
+int orc_q0(int N, const double *n, const double *g, double *q0, double *dq0dn, double *dq0dg)
+{
+    const double Zab = -0.8491;
+#pragma omp parallel for schedule(static)
+    for (int m = 0; m < N; ++m) {
+        double nn = n[m];
+        if (!(nn > 0.0)) {
+            q0[m] = 0.0;
+            if (dq0dn) dq0dn[m] = 0.0;
+            if (dq0dg) { dq0dg[m] = 0.0; dq0dg[(size_t)N + m] = 0.0; dq0dg[2 * (size_t)N + m] = 0.0; }
+            continue;
+        }
+        double gx = g[m], gy = g[(size_t)N + m], gz = g[2 * (size_t)N + m];
+        double g2 = gx * gx + gy * gy + gz * gz;
+        double kF = cbrt(3.0 * M_PI * M_PI * nn);
+        double s = sqrt(g2) / (2.0 * kF * nn);
+        double rs = cbrt(3.0 / (4.0 * M_PI * nn));
+        double ec, dec_drs;
+        pw92(rs, &ec, &dec_drs);
+        double ex = -3.0 * kF / (4.0 * M_PI);
+        double exc0 = ec + ex * (1.0 - (Zab / 9.0) * s * s);
+        q0[m] = -(4.0 * M_PI / 3.0) * exc0;
+        if (dq0dn) {
+            double dec_dn = dec_drs * (-rs / (3.0 * nn));
+            dq0dn[m] = kF / (3.0 * nn) + (7.0 * Zab / 108.0) * g2 / (kF * nn * nn * nn) -
+                       (4.0 * M_PI / 3.0) * dec_dn;
+        }
+        if (dq0dg) {
+            double c = -(Zab / 18.0) / (kF * nn * nn);
+            dq0dg[m] = c * gx;
+            dq0dg[(size_t)N + m] = c * gy;
+            dq0dg[2 * (size_t)N + m] = c * gz;
+        }
+    }
+    return 0;
+}
