@@ -1,0 +1,220 @@
+/*
+ * vdwdf.h -- C ABI of libvdwdf, a GB300 (sm_103a) implementation of the hot
+ * path of the vdW-DF nonlocal correlation post-processing method of JuNoLo
+ * (Lazic et al., arXiv 0810.2273).
+ *
+ * The method (paper section 2, eqs. (1)-(2)):
+ *     E_c^nl = 1/2 sum_i sum_j n(r_i) phi(q0_i |r_i - r_j|, q0_j |r_i - r_j|) n(r_j) dV^2
+ * over the points of a charge density on an equidistant grid whose density is
+ * at least a cutoff (section 3, "trimming"), including the periodic images of
+ * the cell for periodic problems (section 3, "repeated in space"), with the
+ * kernel phi of Dion et al. (PRL 92, 246401, eq. 14) tabulated in the
+ * variables D and delta (section 2) and its large-D asymptote (Dion eq. 17).
+ * q0 follows Dion eqs. 11-12 (LDA correlation plus gradient-corrected
+ * exchange, Zab = -0.8491) from n and |grad n|, with grad n by 4th-order
+ * central finite differences along the (orthogonal) axes (section 3).
+ *
+ * Units: Hartree atomic units (bohr, Hartree) at the boundary, FP64.
+ *
+ * Conventions common to every entry point:
+ *  - Return value: VDWDF_OK (0) on success, a negative VDWDF_E* code on
+ *    failure; vdwdf_strerror() names it.  No C++ exception crosses the ABI.
+ *    Invalid arguments are rejected on the host before any launch, and then
+ *    no output is written.
+ *  - Device pointers ("_dev") are ordinary CUDA global-memory pointers owned
+ *    by the caller, on the current device; they must stay valid until the
+ *    call returns.  Grids are row-major [n0][n1][n2] FP64.
+ *  - cuda_stream is a cudaStream_t (NULL = legacy default stream).  All
+ *    device work of a call is ordered on that stream.  Calls that return
+ *    host results (vdwdf_result, E_out) synchronise that stream before
+ *    returning; the others return without waiting.
+ *  - Scratch device memory is taken with cudaMallocAsync on the call's stream
+ *    and freed on it before return; the library owns it.
+ *  - Only orthorhombic cells (diagonal cell matrix) are accepted by the GPU
+ *    path (VDWDF_EUNSUPPORTED otherwise).
+ */
+#ifndef VDWDF_H
+#define VDWDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VDWDF_VERSION 10000
+
+/* status codes */
+#define VDWDF_OK 0
+#define VDWDF_EINVAL (-1)        /* bad argument: null pointer, size, value   */
+#define VDWDF_EUNSUPPORTED (-2)  /* valid but not implemented (non-orthorhombic cell) */
+#define VDWDF_ECUDA (-3)         /* a CUDA runtime call failed                */
+#define VDWDF_EALLOC (-4)        /* host or device allocation failed          */
+#define VDWDF_ETIMEOUT (-5)      /* a device-side work loop hit its iteration cap */
+#define VDWDF_ENOTABLE (-6)      /* table handle missing or of another size   */
+
+/* arithmetic of the pair sum */
+#define VDWDF_FP32 0  /* FP32 pair arithmetic and interpolation, FP64 accumulation */
+#define VDWDF_FP64 1  /* FP64 throughout                                         */
+
+/* The grid: cell rows a, b, c in bohr (grid point (i,j,k) sits at
+ * i/n0 a + j/n1 b + k/n2 c), points per axis, and per-axis periodicity
+ * (section 2: "equidistant division in all three spatial dimensions";
+ * Appendix A input: perx, pery, perz).  The density array is [n0][n1][n2]. */
+typedef struct {
+    double cell[3][3];
+    int32_t n[3];
+    int32_t periodic[3];
+} vdwdf_grid;
+
+/* Opaque kernel table: phi on the node grid D_k = Dmax k/(nD-1),
+ * delta_l = l/ndelta (section 2: "redefined to depend on two quantities,
+ * D >= 0 and 0 <= delta < 1"; section 7: limits and divisions fixed by
+ * refinement), its FP64 and FP32 cubic-spline coefficients, and their device
+ * copies.  Owned by the library; free with vdwdf_table_free. */
+typedef struct vdwdf_table vdwdf_table;
+
+/* Per-call report. */
+typedef struct {
+    double E;                /* E_c^nl, Hartree                                     */
+    double E_diag;           /* self-term part, 1/2 dV^2 sum_i n_i^2 phi(0,0)       */
+    int64_t n_active;        /* grid points with n >= n_cut                         */
+    int64_t pairs;           /* ordered pair interactions (i, j, L) other than the
+                                self term, within r_cut when r_cut > 0              */
+    int64_t pairs_evaluated; /* kernel evaluations done (folded by i<->j symmetry
+                                for energy-only calls, outside-cutoff tests included) */
+    int64_t n_clamped;       /* table lookups with delta beyond the last node      */
+    double q0_min, q0_max;   /* over active points                                 */
+    float ms_prep;           /* device time: gradient, q0, trimming, tiling        */
+    float ms_pairs;          /* device time: pair kernel(s)                         */
+    float ms_post;           /* device time: potential assembly and reductions      */
+    int32_t launches;        /* kernels launched by this call                      */
+} vdwdf_result;
+
+/* Optional launch shape of the pair kernel (NULL = defaults / tuned). */
+typedef struct {
+    int32_t threads;      /* threads per CTA: 256, 512 or 1024 (0 = default 512)      */
+    int32_t items_per_sm; /* target work items per SM for load balance (0 = default) */
+    int32_t smem_rows;    /* FP32 path: table rows resident in shared memory
+                             (0 = as many as fit, -1 = none)                          */
+    int32_t smem_row0;    /* FP32 path: first resident table row (-1 = chosen from a
+                             sampled histogram of D over the call's pairs)           */
+} vdwdf_tuning;
+
+/* --------------------------------------------------------------------- */
+/* Kernel table (host, FP64)                                              */
+/* --------------------------------------------------------------------- */
+
+/* Build the table by double quadrature of Dion eq. (14) on the host in FP64
+ * (section 2: "formula (14) ... requires a double integration"), OpenMP over
+ * nodes.  Row D = 0, where eq. (14) diverges like -(2/pi) ln D, holds the
+ * value at D = 0 of the even quadratic through rows 1 and 2.
+ *   nD >= 4 nodes in D over [0, Dmax] (Dmax > 0); ndelta >= 4 nodes
+ *   delta_l = l/ndelta.  quad_level: 0 = fast (~1e-6 of max|phi|),
+ *   1 = standard (~1e-10), 2 = fine.  phi_nodes_out: NULL or host array of
+ *   nD*ndelta doubles (D outer).  *out receives the handle.
+ * Errors: VDWDF_EINVAL, VDWDF_EALLOC. */
+int vdwdf_table_build(int nD, double Dmax, int ndelta, int quad_level,
+                      double *phi_nodes_out, vdwdf_table **out);
+
+/* Make a table from given node values (host, nD*ndelta doubles, D outer),
+ * e.g. a saved table (section 5: the kernel file is loaded, not recomputed).
+ * Same grid conventions and errors as vdwdf_table_build. */
+int vdwdf_table_from_nodes(int nD, double Dmax, int ndelta, const double *phi_nodes,
+                           vdwdf_table **out);
+
+/* Copy a table's node values to host memory (nD*ndelta doubles). */
+int vdwdf_table_nodes(const vdwdf_table *t, double *phi_nodes_out);
+
+/* Query a table's grid. Any output pointer may be NULL. */
+int vdwdf_table_info(const vdwdf_table *t, int *nD, double *Dmax, int *ndelta);
+
+/* Release a table and its device copies (NULL is ignored). */
+void vdwdf_table_free(vdwdf_table *t);
+
+/* Evaluate the kernel as the pair sum uses it, on the device, at npts pairs:
+ * inputs r (bohr), q_i, q_j (device FP64 arrays); outputs phi and
+ * r dphi/dd1 (d1 = q_i r, d2 = q_j r).  precision as in vdwdf_energy.  For
+ * checking the interpolation path in isolation. */
+int vdwdf_kernel_eval(const vdwdf_table *t, int precision, int64_t npts,
+                      const double *r_dev, const double *qi_dev, const double *qj_dev,
+                      double *phi_dev, double *rdphi_dev, void *cuda_stream);
+
+/* --------------------------------------------------------------------- */
+/* q0 (Dion eqs. 11-12)                                                    */
+/* --------------------------------------------------------------------- */
+
+/* q0 = -(4 pi/3) [eps_c^LDA + eps_x^LDA (1 - (Zab/9) s^2)],
+ * s = |grad n|/(2 k_F n), with eps_c^LDA of Perdew-Wang 1992, at every grid
+ * point; points with n <= 0 give 0.  grad_dev: NULL (library stencil: 4th
+ * order periodic central differences) or a [3][N] FP64 device array.
+ * Outputs q0_dev [N] and, when not NULL, dq0dn_dev [N], dq0dg_dev [3][N].
+ * n_cut is not used (reserved). Asynchronous. */
+int vdwdf_q0(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev,
+             double n_cut, double *q0_dev, double *dq0dn_dev, double *dq0dg_dev,
+             void *cuda_stream);
+
+/* --------------------------------------------------------------------- */
+/* The double sum (paper section 2 eq. (2), section 3)                     */
+/* --------------------------------------------------------------------- */
+
+/* E_c^nl of the density n_dev ([N] FP64) on grid.  Points with n >= n_cut
+ * take part; the self term i = j, L = 0 is n_i^2 phi(0,0).  Periodic axes add
+ * all images L with |r_i - r_j + L| <= r_cut (required > 0 when any axis is
+ * periodic); r_cut <= 0 means no cutoff for open cells.  grad_dev as in
+ * vdwdf_q0.  A pair is inside the cutoff iff |r_i - r_j + L|^2 <= r_cut^2 (1 + 1e-12)
+ * (distances equal to r_cut up to rounding count as inside, in both precisions).
+ * precision: VDWDF_FP32 or VDWDF_FP64.  Synchronises the stream.
+ * Errors: VDWDF_EINVAL, VDWDF_EUNSUPPORTED, VDWDF_ENOTABLE, VDWDF_ECUDA,
+ * VDWDF_EALLOC, VDWDF_ETIMEOUT. */
+int vdwdf_energy(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev,
+                 double n_cut, double r_cut, const vdwdf_table *table, int precision,
+                 const vdwdf_tuning *tuning, vdwdf_result *out, void *cuda_stream);
+
+/* E_c^nl and its potential v = (1/dV) dE/dn at every grid point (mask of
+ * active points frozen), written to v_dev [N] FP64:
+ *   v_m = dV [chi_m (A_m + U_m dq0/dn_m) - sum_axes D_h(U dq0/dgrad n)_m],
+ *   A_i = sum_{j,L} n_j phi_ijL,  U_i = n_i sum_{j,L} n_j r dphi/dd1,
+ * chi the active mask and D_h the library's gradient stencil (so the
+ * gradient is always computed by the library here).  A_dev, U_dev: NULL or
+ * [N] FP64 grid arrays that receive A and U (0 at inactive points).
+ * Synchronises the stream. Errors as vdwdf_energy. */
+int vdwdf_potential(const vdwdf_grid *grid, const double *n_dev, double n_cut, double r_cut,
+                    const vdwdf_table *table, int precision, const vdwdf_tuning *tuning,
+                    double *v_dev, double *A_dev, double *U_dev, vdwdf_result *out,
+                    void *cuda_stream);
+
+/* E_c^nl of ninst independent densities (grids[k], n_dev[k]) in one
+ * persistent launch of the pair kernel, recorded once into a CUDA graph and
+ * replayed on later calls with the same shapes and pointers (binding curves,
+ * section 6.1).  E_out: host array of ninst doubles.  Synchronises the
+ * stream.  Errors as vdwdf_energy. */
+int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const *n_dev,
+                         double n_cut, double r_cut, const vdwdf_table *table, int precision,
+                         const vdwdf_tuning *tuning, double *E_out, vdwdf_result *out,
+                         void *cuda_stream);
+
+/* Time candidate launch shapes of the pair kernel on this problem (energy
+ * path, a sample of the work) and write the fastest to *best. */
+int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, double r_cut,
+                   const vdwdf_table *table, int precision, vdwdf_tuning *best,
+                   void *cuda_stream);
+
+/* --------------------------------------------------------------------- */
+/* Misc                                                                    */
+/* --------------------------------------------------------------------- */
+
+/* Static string naming a status code. */
+const char *vdwdf_strerror(int status);
+
+/* VDWDF_VERSION of the built library. */
+int vdwdf_version(void);
+
+/* Number of kernels this library has launched in this process. */
+int64_t vdwdf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VDWDF_H */

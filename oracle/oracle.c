@@ -469,8 +469,10 @@ int orc_kernel_many(int nD, double hD, int nd, double hd, const double *f,
 /* Active points p = 0..Na-1 at integer grid indices (i0,i1,i2) of an       */
 /* orthorhombic cell L0 x L1 x L2 on an n0 x n1 x n2 grid: r = (i0 L0/n0,    */
 /* i1 L1/n1, i2 L2/n2).  Periodic axes add images m L (|m| <= M); pairs with */
-/* |r_i - r_j + L| > rc are dropped when rc > 0 (spherical cutoff; the       */
-/* paper repeats cells until convergence, section 3 and 6.2).  The self     */
+/* |r_i - r_j + L|^2 > rc^2 (1 + 1e-12) are dropped when rc > 0 (spherical  */
+/* cutoff, inclusive, with distances that equal rc up to rounding counted    */
+/* inside; the paper repeats cells until convergence, sections 3 and 6.2).  */
+/* The self                                                                  */
 /* term i = j, L = 0 is n_i phi(0,0) and always included.                   */
 /*   A_i = sum_{j,L} n_j phi_ijL,  U_i = n_i sum_{j,L} n_j r dphi/dd1.       */
 /* Also returns, per query, the number of (j, L) terms other than the self  */
@@ -510,8 +512,9 @@ int orc_pair_AU(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2,
                             continue;
                         }
                         double dx = xi - xj + m0 * L0, dy = yi - yj + m1 * L1, dz = zi - zj + m2 * L2;
-                        double r = sqrt(dx * dx + dy * dy + dz * dz);
-                        if (rc > 0.0 && r > rc) continue;
+                        double r2 = dx * dx + dy * dy + dz * dz;
+                        if (rc > 0.0 && r2 > rc * rc * (1.0 + 1e-12)) continue;
+                        double r = sqrt(r2);
                         double p, rd;
                         kernel_pair(&s, Dmax, r, q[i], q[j], &p, &rd, &cl);
                         a += n[j] * p;
@@ -560,8 +563,9 @@ int orc_pair_brute(int Na, const int32_t *i0, const int32_t *i1, const int32_t *
                         double dx = i0[i] * h0 - i0[j] * h0 + m0 * L0;
                         double dy = i1[i] * h1 - i1[j] * h1 + m1 * L1;
                         double dz = i2[i] * h2 - i2[j] * h2 + m2 * L2;
-                        double r = sqrt(dx * dx + dy * dy + dz * dz);
-                        if (rc > 0.0 && r > rc) continue;
+                        double r2 = dx * dx + dy * dy + dz * dz;
+                        if (rc > 0.0 && r2 > rc * rc * (1.0 + 1e-12)) continue;
+                        double r = sqrt(r2);
                         double D = 0.5 * r * (q[i] + q[j]);
                         if (D > Dmax) {
                             double a1 = q[i] * r, a2 = q[j] * r;

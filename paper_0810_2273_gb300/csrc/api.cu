@@ -1,0 +1,933 @@
+// extern "C" entry points of libvdwdf (declared in include/vdwdf.h).
+//
+// A call validates its arguments on the host, takes scratch with
+// cudaMallocAsync on the caller's stream, runs
+//   gradient + q0  ->  trimming into brick order  ->  tile boxes  ->  pair kernel
+//   (-> potential assembly)  ->  reductions,
+// reads the counters back and frees the scratch on the same stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "table.h"
+
+struct vdwdf_table {
+    int nD, nd;
+    double Dmax;
+    std::vector<double> nodes;   // nD * nd, D outer
+    std::vector<double> coef64;  // (nD + 2) * (nd + 2), / 36
+    std::vector<float> coef32;
+    std::mutex mu;
+    std::map<int, std::pair<double *, float *>> dev;  // device id -> copies
+};
+
+namespace vdwdf {
+
+namespace {
+
+std::atomic<long long> g_launches{0};
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxImages = 64;
+
+int finish_table(vdwdf_table *t) {
+    const int S = t->nd + 2;
+    try {
+        t->coef64.assign(static_cast<size_t>(t->nD + 2) * S, 0.0);
+        t->coef32.assign(static_cast<size_t>(t->nD + 2) * S, 0.0f);
+    } catch (const std::bad_alloc &) {
+        return VDWDF_EALLOC;
+    }
+    spline_coefficients(t->nD, t->nd, t->nodes.data(), t->coef64.data());
+    for (size_t i = 0; i < t->coef64.size(); ++i) {
+        t->coef64[i] /= 36.0;
+        t->coef32[i] = static_cast<float>(t->coef64[i]);
+    }
+    return VDWDF_OK;
+}
+
+int table_on_device(const vdwdf_table *tc, double **d64, float **d32) {
+    vdwdf_table *t = const_cast<vdwdf_table *>(tc);
+    int dev = 0;
+    VDWDF_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(t->mu);
+    auto it = t->dev.find(dev);
+    if (it == t->dev.end()) {
+        double *a = nullptr;
+        float *b = nullptr;
+        const size_t n = t->coef64.size();
+        if (cudaMalloc(&a, n * sizeof(double)) != cudaSuccess) return VDWDF_EALLOC;
+        if (cudaMalloc(&b, n * sizeof(float)) != cudaSuccess) {
+            cudaFree(a);
+            return VDWDF_EALLOC;
+        }
+        VDWDF_CUDA_TRY(cudaMemcpy(a, t->coef64.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        VDWDF_CUDA_TRY(cudaMemcpy(b, t->coef32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+        it = t->dev.emplace(dev, std::make_pair(a, b)).first;
+    }
+    *d64 = it->second.first;
+    *d32 = it->second.second;
+    return VDWDF_OK;
+}
+
+// Morton order of the 4x4x4 bricks of a grid, cached per (device, dims).
+std::mutex g_brick_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<int *, int>> g_bricks;
+
+uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffff;
+    x = (x | x << 32) & 0x1f00000000ffffULL;
+    x = (x | x << 16) & 0x1f0000ff0000ffULL;
+    x = (x | x << 8) & 0x100f00f00f00f00fULL;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+    x = (x | x << 2) & 0x1249249249249249ULL;
+    return x;
+}
+
+int brick_order(const int dims[3], int **order, int *nb) {
+    int dev = 0;
+    VDWDF_CUDA_TRY(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, dims[0], dims[1], dims[2]);
+    std::lock_guard<std::mutex> lk(g_brick_mu);
+    auto it = g_bricks.find(key);
+    if (it == g_bricks.end()) {
+        const int bx = (dims[0] + kBrick - 1) / kBrick, by = (dims[1] + kBrick - 1) / kBrick,
+                  bz = (dims[2] + kBrick - 1) / kBrick;
+        const int n = bx * by * bz;
+        std::vector<std::pair<uint64_t, int>> keys(n);
+        for (int x = 0; x < bx; ++x)
+            for (int y = 0; y < by; ++y)
+                for (int z = 0; z < bz; ++z) {
+                    const int id = (x * by + y) * bz + z;
+                    keys[id] = {spread3(x) << 2 | spread3(y) << 1 | spread3(z), id};
+                }
+        std::sort(keys.begin(), keys.end());
+        std::vector<int> ord(n);
+        for (int i = 0; i < n; ++i) ord[i] = keys[i].second;
+        int *d = nullptr;
+        if (cudaMalloc(&d, sizeof(int) * n) != cudaSuccess) return VDWDF_EALLOC;
+        VDWDF_CUDA_TRY(cudaMemcpy(d, ord.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        it = g_bricks.emplace(key, std::make_pair(d, n)).first;
+    }
+    *order = it->second.first;
+    *nb = it->second.second;
+    return VDWDF_OK;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+// ---------------------------------------------------------------------------
+// argument checks and geometry
+// ---------------------------------------------------------------------------
+struct Geom {
+    int dims[3];
+    int per[3];
+    double L[3], h[3];
+    double dV;
+    long long N;
+    int M[3];
+    double rc;
+    bool use_cut;
+};
+
+int check_grid(const vdwdf_grid *g, Geom &G) {
+    if (!g) return VDWDF_EINVAL;
+    long long N = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (g->n[a] < 1 || g->n[a] > (1 << 20)) return VDWDF_EINVAL;
+        if (g->periodic[a] != 0 && g->periodic[a] != 1) return VDWDF_EINVAL;
+        N *= g->n[a];
+        for (int b = 0; b < 3; ++b) {
+            const double v = g->cell[a][b];
+            if (!std::isfinite(v)) return VDWDF_EINVAL;
+            if (a != b && v != 0.0) return VDWDF_EUNSUPPORTED;
+        }
+        if (!(g->cell[a][a] > 0.0)) return VDWDF_EINVAL;
+    }
+    if (N > (1LL << 31) - 1) return VDWDF_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        G.dims[a] = g->n[a];
+        G.per[a] = g->periodic[a];
+        G.L[a] = g->cell[a][a];
+        G.h[a] = G.L[a] / g->n[a];
+    }
+    G.N = N;
+    G.dV = G.L[0] * G.L[1] * G.L[2] / static_cast<double>(N);
+    return VDWDF_OK;
+}
+
+int check_cut(double n_cut, double r_cut, Geom &G) {
+    if (!(n_cut > 0.0) || !std::isfinite(n_cut)) return VDWDF_EINVAL;
+    if (std::isnan(r_cut) || std::isinf(r_cut)) return VDWDF_EINVAL;
+    const bool any_per = G.per[0] || G.per[1] || G.per[2];
+    if (any_per && !(r_cut > 0.0)) return VDWDF_EINVAL;
+    G.use_cut = r_cut > 0.0;
+    G.rc = G.use_cut ? r_cut : 0.0;
+    for (int a = 0; a < 3; ++a) {
+        G.M[a] = G.per[a] ? static_cast<int>(std::ceil(r_cut / G.L[a])) + 1 : 0;
+        if (G.M[a] > kMaxImages) return VDWDF_EINVAL;
+    }
+    return VDWDF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// scratch
+// ---------------------------------------------------------------------------
+struct Carve {
+    size_t off = 0;
+    template <typename T>
+    size_t take(size_t count) {
+        const size_t o = off;
+        off += (count * sizeof(T) + 255) & ~static_cast<size_t>(255);
+        return o;
+    }
+};
+
+struct Work {
+    unsigned char *base = nullptr;
+    double *q0 = nullptr, *qn = nullptr, *qg = nullptr;
+    int *cnt = nullptr, *off = nullptr, *slot = nullptr;
+    float4 *p32 = nullptr;
+    float *n32 = nullptr;
+    dvec4 *p64 = nullptr;
+    double *n64 = nullptr;
+    float4 *blo = nullptr, *bhi = nullptr;
+    double *A = nullptr, *U = nullptr;
+    Stats *stats = nullptr;
+    unsigned int *queue = nullptr;
+};
+
+size_t layout(const Geom &G, int nb, bool pot, bool fp64, Work *w, unsigned char *base) {
+    Carve c;
+    const size_t N = static_cast<size_t>(G.N);
+    const size_t tiles = (N + kJT - 1) / kJT;
+    const size_t o_q0 = c.take<double>(N);
+    const size_t o_qn = pot ? c.take<double>(N) : 0;
+    const size_t o_qg = pot ? c.take<double>(3 * N) : 0;
+    const size_t o_cnt = c.take<int>(nb);
+    const size_t o_off = c.take<int>(nb + 1);
+    const size_t o_slot = c.take<int>(N);
+    const size_t o_p32 = c.take<float4>(N);
+    const size_t o_n32 = c.take<float>(N);
+    const size_t o_p64 = fp64 ? c.take<dvec4>(N) : 0;
+    const size_t o_n64 = c.take<double>(N);
+    const size_t o_blo = c.take<float4>(tiles);
+    const size_t o_bhi = c.take<float4>(tiles);
+    const size_t o_A = pot ? c.take<double>(N) : 0;
+    const size_t o_U = pot ? c.take<double>(N) : 0;
+    const size_t o_st = c.take<Stats>(1);
+    const size_t o_q = c.take<unsigned int>(1);
+    if (w && base) {
+        w->base = base;
+        w->q0 = reinterpret_cast<double *>(base + o_q0);
+        w->qn = pot ? reinterpret_cast<double *>(base + o_qn) : nullptr;
+        w->qg = pot ? reinterpret_cast<double *>(base + o_qg) : nullptr;
+        w->cnt = reinterpret_cast<int *>(base + o_cnt);
+        w->off = reinterpret_cast<int *>(base + o_off);
+        w->slot = reinterpret_cast<int *>(base + o_slot);
+        w->p32 = reinterpret_cast<float4 *>(base + o_p32);
+        w->n32 = reinterpret_cast<float *>(base + o_n32);
+        w->p64 = fp64 ? reinterpret_cast<dvec4 *>(base + o_p64) : nullptr;
+        w->n64 = reinterpret_cast<double *>(base + o_n64);
+        w->blo = reinterpret_cast<float4 *>(base + o_blo);
+        w->bhi = reinterpret_cast<float4 *>(base + o_bhi);
+        w->A = pot ? reinterpret_cast<double *>(base + o_A) : nullptr;
+        w->U = pot ? reinterpret_cast<double *>(base + o_U) : nullptr;
+        w->stats = reinterpret_cast<Stats *>(base + o_st);
+        w->queue = reinterpret_cast<unsigned int *>(base + o_q);
+    }
+    return c.off;
+}
+
+// Zero the counters; q0 minimum starts above every float.
+int reset_stats(Stats *s, cudaStream_t st) {
+    VDWDF_CUDA_TRY(cudaMemsetAsync(s, 0, sizeof(Stats), st));
+    VDWDF_CUDA_TRY(cudaMemsetAsync(&s->qmin_bits, 0xFF, sizeof(unsigned int), st));
+    return VDWDF_OK;
+}
+
+// gradient, q0, trimming and tiles of one problem into w
+int prepare(const Geom &G, const double *n_dev, const double *grad_dev, double n_cut, bool pot,
+            Work &w, cudaStream_t st) {
+    int *order = nullptr, nb = 0;
+    int rc = brick_order(G.dims, &order, &nb);
+    if (rc) return rc;
+    rc = reset_stats(w.stats, st);
+    if (rc) return rc;
+    rc = launch_grad_q0(G.dims, G.h, n_dev, grad_dev, w.q0, w.qn, w.qg, st);
+    if (rc) return rc;
+    return launch_compact(G.dims, n_dev, n_cut, w.q0, order, nb, w.cnt, w.off, pot ? w.slot : nullptr,
+                          w.p32, w.n32, w.p64, w.n64, w.blo, w.bhi, w.stats, st);
+}
+
+void fill_params(const Geom &G, const Work &w, PairParams &pp) {
+    for (int a = 0; a < 3; ++a) {
+        pp.h2[a] = G.h[a] * G.h[a];
+        pp.dims[a] = G.dims[a];
+        pp.M[a] = G.M[a];
+    }
+    pp.rc2 = G.rc * G.rc * (1.0 + 1e-12);  // inclusive cutoff, rounding ties inside
+    pp.use_cut = G.use_cut ? 1 : 0;
+    pp.p32 = w.p32;
+    pp.n32 = w.n32;
+    pp.p64 = w.p64;
+    pp.n64 = w.n64;
+    pp.blo = w.blo;
+    pp.bhi = w.bhi;
+    pp.A = w.A;
+    pp.U = w.U;
+    pp.stats = w.stats;
+}
+
+struct Launch {
+    int threads = 512;
+    int nctas = 1;
+    int jt = 64;
+    int ks0 = 0, ksn = 0;
+};
+
+// Opt-in shared memory per block on this device, less 1 KiB for static arrays.
+int smem_budget() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+        v = kMaxSmemBytes;
+    return std::min(v, kMaxSmemBytes) - 1024;
+}
+
+int smem_rows_available(int S) {
+    const int base = pair_smem_bytes(VDWDF_FP32, 0, S);
+    return std::max(0, (smem_budget() - base) / (S * static_cast<int>(sizeof(float))));
+}
+
+int ctas_per_sm(int precision, bool pot, int threads, int ksn, int S) {
+    (void)pot;
+    if (precision == VDWDF_FP32) return 1;  // the resident table band takes the shared memory
+    (void)ksn;
+    (void)S;
+    return std::max(1, 1024 / threads);
+}
+
+void fill_shared(const vdwdf_table *t, const double *d64, const float *d32, const Launch &ln,
+                 unsigned int *queue, unsigned int max_iters, PairShared &sh) {
+    sh.tab64 = d64;
+    sh.tab32 = d32;
+    sh.S = t->nd + 2;
+    sh.nD = t->nD;
+    sh.nd = t->nd;
+    const double hD = t->Dmax / (t->nD - 1);
+    sh.cD = 0.5 / hD;
+    sh.cd = static_cast<double>(t->nd);
+    sh.C_asym = 12.0 * std::pow(4.0 * kPi / 9.0, 3);
+    sh.ks0 = ln.ks0;
+    sh.ksn = ln.ksn;
+    sh.jtiles_per_item = ln.jt;
+    sh.item_limit = 0xFFFFFFFFu;
+    sh.max_iters = max_iters;
+    sh.queue = queue;
+}
+
+Launch choose_launch(int precision, bool pot, const vdwdf_tuning *tu, const vdwdf_table *t,
+                     long long n_active) {
+    Launch ln;
+    const int S = t->nd + 2;
+    if (tu && (tu->threads == 256 || tu->threads == 512 || tu->threads == 1024)) ln.threads = tu->threads;
+    const int sms = sm_count();
+    ln.nctas = sms * ctas_per_sm(precision, pot, ln.threads, 0, S);
+    int ipsm = (tu && tu->items_per_sm > 0) ? tu->items_per_sm : 24;
+    const long long nI = (n_active + ln.threads - 1) / ln.threads;
+    const long long nJ = (n_active + kJT - 1) / kJT;
+    const long long want = static_cast<long long>(ipsm) * sms;
+    long long C = std::max<long long>(1, (want + std::max<long long>(nI, 1) - 1) / std::max<long long>(nI, 1));
+    C = std::min<long long>(C, std::max<long long>(nJ, 1));
+    ln.jt = static_cast<int>(std::max<long long>(1, (nJ + C - 1) / C));
+    if (precision == VDWDF_FP32) {
+        const int avail = smem_rows_available(S);
+        int rows = std::min(avail, t->nD + 2);
+        if (tu && tu->smem_rows < 0) rows = 0;
+        if (tu && tu->smem_rows > 0) rows = std::min(rows, tu->smem_rows);
+        int r0 = (tu && tu->smem_row0 > 0) ? tu->smem_row0 : 0;
+        r0 = std::min(r0, t->nD + 2 - rows);
+        ln.ks0 = std::max(0, r0);
+        ln.ksn = rows;
+    }
+    return ln;
+}
+
+struct Timer {
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool ok = false;
+    Timer() {
+        ok = true;
+        for (auto &x : e)
+            if (cudaEventCreate(&x) != cudaSuccess) ok = false;
+    }
+    ~Timer() {
+        for (auto &x : e)
+            if (x) cudaEventDestroy(x);
+    }
+    void mark(int i, cudaStream_t st) {
+        if (ok) cudaEventRecord(e[i], st);
+    }
+    float ms(int a, int b) {
+        float v = 0.0f;
+        if (ok && cudaEventElapsedTime(&v, e[a], e[b]) == cudaSuccess) return v;
+        return 0.0f;
+    }
+};
+
+void fill_result(const Stats &s, const Geom &G, const vdwdf_table *t, vdwdf_result *out) {
+    out->E = 0.5 * G.dV * G.dV * s.E_pair;
+    out->E_diag = 0.5 * G.dV * G.dV * s.n2sum * t->nodes[0];
+    out->n_active = s.n_active;
+    out->pairs = static_cast<int64_t>(s.pairs);
+    out->pairs_evaluated = static_cast<int64_t>(s.evals);
+    out->n_clamped = static_cast<int64_t>(s.clamped);
+    float fmin, fmax;
+    std::memcpy(&fmin, &s.qmin_bits, 4);
+    std::memcpy(&fmax, &s.qmax_bits, 4);
+    out->q0_min = s.n_active > 0 ? fmin : 0.0;
+    out->q0_max = s.n_active > 0 ? fmax : 0.0;
+}
+
+// Single problem, energy or potential.
+int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
+               double r_cut, const vdwdf_table *table, int precision, const vdwdf_tuning *tu,
+               bool pot, double *v_dev, double *A_grid, double *U_grid, vdwdf_result *out,
+               void *stream) {
+    Geom G;
+    int rc = check_grid(grid, G);
+    if (rc) return rc;
+    rc = check_cut(n_cut, r_cut, G);
+    if (rc) return rc;
+    if (!n_dev) return VDWDF_EINVAL;
+    if (pot && !v_dev && !A_grid && !U_grid) return VDWDF_EINVAL;
+    if (!table) return VDWDF_ENOTABLE;
+    if (precision != VDWDF_FP32 && precision != VDWDF_FP64) return VDWDF_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long launches0 = g_launches.load();
+    double *d64 = nullptr;
+    float *d32 = nullptr;
+    rc = table_on_device(table, &d64, &d32);
+    if (rc) return rc;
+    int *order = nullptr, nb = 0;
+    rc = brick_order(G.dims, &order, &nb);
+    if (rc) return rc;
+    const bool fp64 = precision == VDWDF_FP64;
+    const size_t bytes = layout(G, nb, pot, fp64, nullptr, nullptr);
+    unsigned char *base = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&base), bytes, st) != cudaSuccess) return VDWDF_EALLOC;
+    Work w;
+    layout(G, nb, pot, fp64, &w, base);
+    Timer tm;
+    Stats hs;
+    std::memset(&hs, 0, sizeof(hs));
+    auto body = [&]() -> int {
+        tm.mark(0, st);
+        int r = prepare(G, n_dev, grad_dev, n_cut, pot, w, st);
+        if (r) return r;
+        VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+        VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+        tm.mark(1, st);
+        if (pot) {
+            VDWDF_CUDA_TRY(cudaMemsetAsync(w.A, 0, sizeof(double) * G.N, st));
+            VDWDF_CUDA_TRY(cudaMemsetAsync(w.U, 0, sizeof(double) * G.N, st));
+        }
+        if (hs.n_active > 0) {
+            Launch ln = choose_launch(precision, pot, tu, table, hs.n_active);
+            VDWDF_CUDA_TRY(cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st));
+            PairLaunch pl;
+            std::memset(&pl, 0, sizeof(pl));
+            const long long nI = (hs.n_active + ln.threads - 1) / ln.threads;
+            const long long nJ = (hs.n_active + kJT - 1) / kJT;
+            const long long items = nI * ((nJ + ln.jt - 1) / ln.jt);
+            fill_shared(table, d64, d32, ln, w.queue, static_cast<unsigned int>(std::min<long long>(items + 2, 0xFFFFFFF0LL)), pl.sh);
+            pl.ninst = 1;
+            fill_params(G, w, pl.inst[0]);
+            r = launch_pair(precision, pot, ln.threads, pl, ln.nctas, st);
+            if (r) return r;
+        }
+        tm.mark(2, st);
+        if (pot) {
+            r = launch_assemble(G.dims, G.h, G.dV, w.slot, w.A, w.U, w.qn, w.qg, v_dev, A_grid, U_grid, st);
+            if (r) return r;
+            r = launch_energy_from_A(static_cast<int>(G.N), w.A, w.n64, w.stats, st);
+            if (r) return r;
+        }
+        tm.mark(3, st);
+        VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+        VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+        return VDWDF_OK;
+    };
+    rc = body();
+    cudaFreeAsync(base, st);
+    if (rc == VDWDF_OK && hs.guard_trips) rc = VDWDF_ETIMEOUT;
+    if (rc == VDWDF_OK && out) {
+        std::memset(out, 0, sizeof(*out));
+        fill_result(hs, G, table, out);
+        out->ms_prep = tm.ms(0, 1);
+        out->ms_pairs = tm.ms(1, 2);
+        out->ms_post = tm.ms(2, 3);
+        out->launches = static_cast<int32_t>(g_launches.load() - launches0);
+    }
+    if (rc == VDWDF_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            note_cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+            rc = VDWDF_ECUDA;
+        }
+    }
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// batched energies: one persistent pair launch per kMaxInst instances,
+// recorded into a CUDA graph and replayed for the same inputs
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+    std::vector<Geom> geo;
+    std::vector<Work> work;
+    std::vector<unsigned char *> bufs;
+    unsigned int *queues = nullptr;  // one per pair launch
+    cudaGraphExec_t exec = nullptr;
+    int device = 0;
+    int launches_per_replay = 0;
+    ~BatchPlan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (auto *b : bufs) cudaFree(b);
+        if (queues) cudaFree(queues);
+    }
+};
+
+std::mutex g_batch_mu;
+std::map<std::vector<uintptr_t>, BatchPlan *> g_batches;
+
+int record_batch(BatchPlan &bp, int ninst, const double *const *n_dev, double n_cut,
+                 const vdwdf_table *table, int precision, const vdwdf_tuning *tu, double *d64,
+                 float *d32, cudaStream_t st) {
+    long long nmax = 0, nsum = 0;
+    for (int k = 0; k < ninst; ++k) {
+        nmax = std::max(nmax, bp.geo[k].N);
+        nsum += bp.geo[k].N;
+    }
+    const int ngroups = (ninst + kMaxInst - 1) / kMaxInst;
+    for (int k = 0; k < ninst; ++k) {
+        int rc = prepare(bp.geo[k], n_dev[k], nullptr, n_cut, false, bp.work[k], st);
+        if (rc) return rc;
+    }
+    for (int g = 0; g < ngroups; ++g) {
+        const int k0 = g * kMaxInst, k1 = std::min(ninst, k0 + kMaxInst);
+        long long gsum = 0;
+        for (int k = k0; k < k1; ++k) gsum += bp.geo[k].N;
+        Launch ln = choose_launch(precision, false, tu, table, std::max<long long>(1, gsum / (k1 - k0)));
+        VDWDF_CUDA_TRY(cudaMemsetAsync(bp.queues + g, 0, sizeof(unsigned int), st));
+        PairLaunch pl;
+        std::memset(&pl, 0, sizeof(pl));
+        long long items = 0;
+        for (int k = k0; k < k1; ++k) {
+            const long long N = bp.geo[k].N;
+            items += ((N + ln.threads - 1) / ln.threads) * (((N + kJT - 1) / kJT + ln.jt - 1) / ln.jt);
+        }
+        fill_shared(table, d64, d32, ln, bp.queues + g,
+                    static_cast<unsigned int>(std::min<long long>(items + 2, 0xFFFFFFF0LL)), pl.sh);
+        pl.ninst = k1 - k0;
+        for (int k = k0; k < k1; ++k) fill_params(bp.geo[k], bp.work[k], pl.inst[k - k0]);
+        int rc = launch_pair(precision, false, ln.threads, pl, ln.nctas, st);
+        if (rc) return rc;
+    }
+    (void)nmax;
+    (void)nsum;
+    return VDWDF_OK;
+}
+
+}  // namespace
+
+void note_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+    if (std::getenv("VDWDF_VERBOSE"))
+        std::fprintf(stderr, "vdwdf: %s failed: %s (%s:%d)\n", what, cudaGetErrorString(e), file, line);
+}
+
+void count_launches(int n) { g_launches.fetch_add(n); }
+
+}  // namespace vdwdf
+
+using namespace vdwdf;
+
+extern "C" {
+
+const char *vdwdf_strerror(int s) {
+    switch (s) {
+        case VDWDF_OK: return "ok";
+        case VDWDF_EINVAL: return "invalid argument";
+        case VDWDF_EUNSUPPORTED: return "unsupported input (non-orthorhombic cell)";
+        case VDWDF_ECUDA: return "CUDA runtime error";
+        case VDWDF_EALLOC: return "allocation failed";
+        case VDWDF_ETIMEOUT: return "device work loop hit its iteration cap";
+        case VDWDF_ENOTABLE: return "missing or mismatched kernel table";
+        default: return "unknown status";
+    }
+}
+
+int vdwdf_version(void) { return VDWDF_VERSION; }
+
+int64_t vdwdf_launch_count(void) { return g_launches.load(); }
+
+int vdwdf_table_build(int nD, double Dmax, int ndelta, int quad_level, double *phi_nodes_out,
+                      vdwdf_table **out) {
+    if (!out || nD < 4 || ndelta < 4 || !(Dmax > 0.0) || !std::isfinite(Dmax) || quad_level < 0 ||
+        quad_level > 2 || static_cast<long long>(nD) * ndelta > (1LL << 26))
+        return VDWDF_EINVAL;
+    vdwdf_table *t = new (std::nothrow) vdwdf_table;
+    if (!t) return VDWDF_EALLOC;
+    t->nD = nD;
+    t->nd = ndelta;
+    t->Dmax = Dmax;
+    try {
+        t->nodes.assign(static_cast<size_t>(nD) * ndelta, 0.0);
+    } catch (const std::bad_alloc &) {
+        delete t;
+        return VDWDF_EALLOC;
+    }
+    if (build_phi_nodes(nD, Dmax, ndelta, quad_level, t->nodes.data()) != 0) {
+        delete t;
+        return VDWDF_EALLOC;
+    }
+    int rc = finish_table(t);
+    if (rc) {
+        delete t;
+        return rc;
+    }
+    if (phi_nodes_out) std::memcpy(phi_nodes_out, t->nodes.data(), sizeof(double) * t->nodes.size());
+    *out = t;
+    return VDWDF_OK;
+}
+
+int vdwdf_table_from_nodes(int nD, double Dmax, int ndelta, const double *phi_nodes, vdwdf_table **out) {
+    if (!out || !phi_nodes || nD < 4 || ndelta < 4 || !(Dmax > 0.0) || !std::isfinite(Dmax) ||
+        static_cast<long long>(nD) * ndelta > (1LL << 26))
+        return VDWDF_EINVAL;
+    for (long long i = 0; i < static_cast<long long>(nD) * ndelta; ++i)
+        if (!std::isfinite(phi_nodes[i])) return VDWDF_EINVAL;
+    vdwdf_table *t = new (std::nothrow) vdwdf_table;
+    if (!t) return VDWDF_EALLOC;
+    t->nD = nD;
+    t->nd = ndelta;
+    t->Dmax = Dmax;
+    try {
+        t->nodes.assign(phi_nodes, phi_nodes + static_cast<size_t>(nD) * ndelta);
+    } catch (const std::bad_alloc &) {
+        delete t;
+        return VDWDF_EALLOC;
+    }
+    int rc = finish_table(t);
+    if (rc) {
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return VDWDF_OK;
+}
+
+int vdwdf_table_nodes(const vdwdf_table *t, double *phi_nodes_out) {
+    if (!t || !phi_nodes_out) return VDWDF_EINVAL;
+    std::memcpy(phi_nodes_out, t->nodes.data(), sizeof(double) * t->nodes.size());
+    return VDWDF_OK;
+}
+
+int vdwdf_table_info(const vdwdf_table *t, int *nD, double *Dmax, int *ndelta) {
+    if (!t) return VDWDF_EINVAL;
+    if (nD) *nD = t->nD;
+    if (Dmax) *Dmax = t->Dmax;
+    if (ndelta) *ndelta = t->nd;
+    return VDWDF_OK;
+}
+
+void vdwdf_table_free(vdwdf_table *t) {
+    if (!t) return;
+    int cur = 0;
+    const bool have = cudaGetDevice(&cur) == cudaSuccess;
+    for (auto &kv : t->dev) {
+        if (cudaSetDevice(kv.first) == cudaSuccess) {
+            cudaFree(kv.second.first);
+            cudaFree(kv.second.second);
+        }
+    }
+    if (have) cudaSetDevice(cur);
+    delete t;
+}
+
+int vdwdf_kernel_eval(const vdwdf_table *t, int precision, int64_t npts, const double *r_dev,
+                      const double *qi_dev, const double *qj_dev, double *phi_dev, double *rdphi_dev,
+                      void *cuda_stream) {
+    if (!t) return VDWDF_ENOTABLE;
+    if (npts < 0 || (npts > 0 && (!r_dev || !qi_dev || !qj_dev || !phi_dev || !rdphi_dev)))
+        return VDWDF_EINVAL;
+    if (precision != VDWDF_FP32 && precision != VDWDF_FP64) return VDWDF_EINVAL;
+    if (npts == 0) return VDWDF_OK;
+    double *d64 = nullptr;
+    float *d32 = nullptr;
+    int rc = table_on_device(t, &d64, &d32);
+    if (rc) return rc;
+    Launch ln;
+    PairShared sh;
+    std::memset(&sh, 0, sizeof(sh));
+    fill_shared(t, d64, d32, ln, nullptr, 0, sh);
+    return launch_kernel_eval(precision, sh, npts, r_dev, qi_dev, qj_dev, phi_dev, rdphi_dev,
+                              static_cast<cudaStream_t>(cuda_stream));
+}
+
+int vdwdf_q0(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
+             double *q0_dev, double *dq0dn_dev, double *dq0dg_dev, void *cuda_stream) {
+    (void)n_cut;
+    Geom G;
+    int rc = check_grid(grid, G);
+    if (rc) return rc;
+    if (!n_dev || !q0_dev) return VDWDF_EINVAL;
+    return launch_grad_q0(G.dims, G.h, n_dev, grad_dev, q0_dev, dq0dn_dev, dq0dg_dev,
+                          static_cast<cudaStream_t>(cuda_stream));
+}
+
+int vdwdf_energy(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
+                 double r_cut, const vdwdf_table *table, int precision, const vdwdf_tuning *tuning,
+                 vdwdf_result *out, void *cuda_stream) {
+    return run_single(grid, n_dev, grad_dev, n_cut, r_cut, table, precision, tuning, false, nullptr,
+                      nullptr, nullptr, out, cuda_stream);
+}
+
+int vdwdf_potential(const vdwdf_grid *grid, const double *n_dev, double n_cut, double r_cut,
+                    const vdwdf_table *table, int precision, const vdwdf_tuning *tuning, double *v_dev,
+                    double *A_dev, double *U_dev, vdwdf_result *out, void *cuda_stream) {
+    return run_single(grid, n_dev, nullptr, n_cut, r_cut, table, precision, tuning, true, v_dev, A_dev,
+                      U_dev, out, cuda_stream);
+}
+
+int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const *n_dev, double n_cut,
+                         double r_cut, const vdwdf_table *table, int precision,
+                         const vdwdf_tuning *tuning, double *E_out, vdwdf_result *out,
+                         void *cuda_stream) {
+    if (ninst < 1 || ninst > 4096 || !grids || !n_dev || !E_out) return VDWDF_EINVAL;
+    if (!table) return VDWDF_ENOTABLE;
+    if (precision != VDWDF_FP32 && precision != VDWDF_FP64) return VDWDF_EINVAL;
+    std::vector<Geom> geo(ninst);
+    for (int k = 0; k < ninst; ++k) {
+        int rc = check_grid(&grids[k], geo[k]);
+        if (rc) return rc;
+        rc = check_cut(n_cut, r_cut, geo[k]);
+        if (rc) return rc;
+        if (!n_dev[k]) return VDWDF_EINVAL;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    double *d64 = nullptr;
+    float *d32 = nullptr;
+    int rc = table_on_device(table, &d64, &d32);
+    if (rc) return rc;
+    int dev = 0;
+    VDWDF_CUDA_TRY(cudaGetDevice(&dev));
+    // signature of the recorded graph: inputs, shapes, cutoffs, table, precision, tuning
+    std::vector<uintptr_t> key;
+    key.push_back(static_cast<uintptr_t>(dev));
+    key.push_back(static_cast<uintptr_t>(ninst));
+    key.push_back(reinterpret_cast<uintptr_t>(table));
+    key.push_back(static_cast<uintptr_t>(precision));
+    uint64_t bits;
+    std::memcpy(&bits, &n_cut, 8);
+    key.push_back(static_cast<uintptr_t>(bits));
+    std::memcpy(&bits, &r_cut, 8);
+    key.push_back(static_cast<uintptr_t>(bits));
+    if (tuning) {
+        key.push_back(static_cast<uintptr_t>(tuning->threads));
+        key.push_back(static_cast<uintptr_t>(tuning->items_per_sm));
+        key.push_back(static_cast<uintptr_t>(static_cast<uint32_t>(tuning->smem_rows)));
+        key.push_back(static_cast<uintptr_t>(static_cast<uint32_t>(tuning->smem_row0)));
+    }
+    for (int k = 0; k < ninst; ++k) {
+        key.push_back(reinterpret_cast<uintptr_t>(n_dev[k]));
+        for (int a = 0; a < 3; ++a) {
+            key.push_back(static_cast<uintptr_t>(grids[k].n[a]));
+            key.push_back(static_cast<uintptr_t>(grids[k].periodic[a]));
+            std::memcpy(&bits, &grids[k].cell[a][a], 8);
+            key.push_back(static_cast<uintptr_t>(bits));
+        }
+    }
+    const long long launches0 = g_launches.load();
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    BatchPlan *bp = nullptr;
+    auto it = g_batches.find(key);
+    if (it != g_batches.end()) {
+        bp = it->second;
+    } else {
+        bp = new (std::nothrow) BatchPlan;
+        if (!bp) return VDWDF_EALLOC;
+        bp->device = dev;
+        bp->geo = geo;
+        bp->work.resize(ninst);
+        const int ngroups = (ninst + kMaxInst - 1) / kMaxInst;
+        for (int k = 0; k < ninst; ++k) {
+            int *order = nullptr, nb = 0;
+            rc = brick_order(geo[k].dims, &order, &nb);
+            if (rc) {
+                delete bp;
+                return rc;
+            }
+            const size_t bytes = layout(geo[k], nb, false, precision == VDWDF_FP64, nullptr, nullptr);
+            unsigned char *b = nullptr;
+            if (cudaMalloc(&b, bytes) != cudaSuccess) {
+                delete bp;
+                return VDWDF_EALLOC;
+            }
+            bp->bufs.push_back(b);
+            layout(geo[k], nb, false, precision == VDWDF_FP64, &bp->work[k], b);
+        }
+        if (cudaMalloc(&bp->queues, sizeof(unsigned int) * ngroups) != cudaSuccess) {
+            delete bp;
+            return VDWDF_EALLOC;
+        }
+        // record the whole batch into a graph on a private stream
+        cudaStream_t cs = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            delete bp;
+            return VDWDF_ECUDA;
+        }
+        const long long l0 = g_launches.load();
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = record_batch(*bp, ninst, n_dev, n_cut, table, precision, tuning, d64, d32, cs);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        if (e == cudaSuccess && rc == VDWDF_OK) e = cudaGraphInstantiate(&bp->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        bp->launches_per_replay = static_cast<int>(g_launches.load() - l0);
+        g_launches.fetch_sub(bp->launches_per_replay);  // recorded, not launched
+        if (e != cudaSuccess || rc != VDWDF_OK) {
+            if (e != cudaSuccess) note_cuda_error(e, "graph capture", __FILE__, __LINE__);
+            delete bp;
+            return rc != VDWDF_OK ? rc : VDWDF_ECUDA;
+        }
+        g_batches[key] = bp;
+    }
+    Timer tm;
+    tm.mark(0, st);
+    VDWDF_CUDA_TRY(cudaGraphLaunch(bp->exec, st));
+    count_launches(bp->launches_per_replay);
+    tm.mark(1, st);
+    std::vector<Stats> hs(ninst);
+    for (int k = 0; k < ninst; ++k)
+        VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs[k], bp->work[k].stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+    VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+    int status = VDWDF_OK;
+    vdwdf_result tot;
+    std::memset(&tot, 0, sizeof(tot));
+    for (int k = 0; k < ninst; ++k) {
+        vdwdf_result r;
+        fill_result(hs[k], bp->geo[k], table, &r);
+        E_out[k] = r.E;
+        tot.E += r.E;
+        tot.E_diag += r.E_diag;
+        tot.n_active += r.n_active;
+        tot.pairs += r.pairs;
+        tot.pairs_evaluated += r.pairs_evaluated;
+        tot.n_clamped += r.n_clamped;
+        if (hs[k].guard_trips) status = VDWDF_ETIMEOUT;
+    }
+    if (out) {
+        *out = tot;
+        out->ms_pairs = tm.ms(0, 1);
+        out->launches = static_cast<int32_t>(g_launches.load() - launches0);
+    }
+    return status;
+}
+
+int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, double r_cut,
+                   const vdwdf_table *table, int precision, vdwdf_tuning *best, void *cuda_stream) {
+    if (!best) return VDWDF_EINVAL;
+    Geom G;
+    int rc = check_grid(grid, G);
+    if (rc) return rc;
+    rc = check_cut(n_cut, r_cut, G);
+    if (rc) return rc;
+    if (!n_dev) return VDWDF_EINVAL;
+    if (!table) return VDWDF_ENOTABLE;
+    if (precision != VDWDF_FP32 && precision != VDWDF_FP64) return VDWDF_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    double *d64 = nullptr;
+    float *d32 = nullptr;
+    rc = table_on_device(table, &d64, &d32);
+    if (rc) return rc;
+    int *order = nullptr, nb = 0;
+    rc = brick_order(G.dims, &order, &nb);
+    if (rc) return rc;
+    const bool fp64 = precision == VDWDF_FP64;
+    const size_t bytes = layout(G, nb, false, fp64, nullptr, nullptr);
+    unsigned char *base = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&base), bytes, st) != cudaSuccess) return VDWDF_EALLOC;
+    Work w;
+    layout(G, nb, false, fp64, &w, base);
+    rc = prepare(G, n_dev, nullptr, n_cut, false, w, st);
+    Stats hs;
+    std::memset(&hs, 0, sizeof(hs));
+    if (rc == VDWDF_OK && cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = VDWDF_ECUDA;
+    if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
+    vdwdf_tuning cand[6] = {{256, 24, 0, 0}, {512, 24, 0, 0}, {1024, 24, 0, 0},
+                            {512, 8, 0, 0},  {512, 64, 0, 0}, {512, 24, -1, 0}};
+    double best_rate = -1.0;
+    vdwdf_tuning choice = {512, 24, 0, 0};
+    Timer tm;
+    for (int ci = 0; ci < 6 && rc == VDWDF_OK && hs.n_active > 0; ++ci) {
+        if (fp64 && cand[ci].smem_rows != 0) continue;
+        Launch ln = choose_launch(precision, false, &cand[ci], table, hs.n_active);
+        for (int rep = 0; rep < 2 && rc == VDWDF_OK; ++rep) {
+            if (cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st) != cudaSuccess) rc = VDWDF_ECUDA;
+            Stats zero;
+            std::memset(&zero, 0, sizeof(zero));
+            zero.n_active = hs.n_active;
+            if (rc == VDWDF_OK &&
+                cudaMemcpyAsync(w.stats, &zero, sizeof(Stats), cudaMemcpyHostToDevice, st) != cudaSuccess)
+                rc = VDWDF_ECUDA;
+            PairLaunch pl;
+            std::memset(&pl, 0, sizeof(pl));
+            fill_shared(table, d64, d32, ln, w.queue, 0xFFFFFFF0u, pl.sh);
+            pl.sh.item_limit = static_cast<unsigned int>(4 * ln.nctas);
+            pl.ninst = 1;
+            fill_params(G, w, pl.inst[0]);
+            tm.mark(0, st);
+            if (rc == VDWDF_OK) rc = launch_pair(precision, false, ln.threads, pl, ln.nctas, st);
+            tm.mark(1, st);
+            Stats out;
+            if (rc == VDWDF_OK &&
+                cudaMemcpyAsync(&out, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                rc = VDWDF_ECUDA;
+            if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
+            const double ms = tm.ms(0, 1);
+            if (rc == VDWDF_OK && rep == 1 && ms > 0.0) {
+                const double rate = static_cast<double>(out.evals) / ms;
+                if (rate > best_rate) {
+                    best_rate = rate;
+                    choice = cand[ci];
+                }
+            }
+        }
+    }
+    cudaFreeAsync(base, st);
+    if (rc == VDWDF_OK) *best = choice;
+    return rc;
+}
+
+}  // extern "C"

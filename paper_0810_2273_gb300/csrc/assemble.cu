@@ -1,0 +1,106 @@
+// Assembly of the nonlocal potential on the grid from the per-point pair sums
+// (the adjoint of the double sum of paper section 2 with the active mask of
+// section 3 frozen):
+//   dE/dn_m = dV^2 [chi_m (A_m + U_m dq0/dn_m) + sum_a (G_a^T w_a)_m],
+//   w_a = chi U dq0/dg_a,
+// where G_a is the periodic 4th-order central-difference stencil along axis a.
+// G_a is antisymmetric, so G_a^T w = -G_a w and
+//   v_m = dE/dn_m / dV = dV [chi_m (A_m + U_m dq0/dn_m) - sum_a (G_a w_a)_m].
+// Also E = 1/2 dV^2 sum_i n_i A_i.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace vdwdf {
+
+namespace {
+
+__device__ __forceinline__ int wrap(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+__global__ void k_assemble(int n0, int n1, int n2, double ih0, double ih1, double ih2, double dV,
+                           const int *__restrict__ slot, const double *__restrict__ A,
+                           const double *__restrict__ U, const double *__restrict__ qn,
+                           const double *__restrict__ qg, double *__restrict__ v,
+                           double *__restrict__ Ag, double *__restrict__ Ug) {
+    const long long N = static_cast<long long>(n0) * n1 * n2;
+    for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < N;
+         m += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(m % n2);
+        const int b = static_cast<int>((m / n2) % n1);
+        const int a = static_cast<int>(m / (static_cast<long long>(n1) * n2));
+        const long long sa = static_cast<long long>(n1) * n2;
+        // w_ax at a neighbour index (0 at inactive points)
+        auto w = [&](long long mm, int ax) {
+            const int s = slot[mm];
+            return s >= 0 ? U[s] * qg[ax * N + mm] : 0.0;
+        };
+        auto ia = [&](int aa) { return static_cast<long long>(wrap(aa, n0)) * sa + static_cast<long long>(b) * n2 + c; };
+        auto ib = [&](int bb) { return static_cast<long long>(a) * sa + static_cast<long long>(wrap(bb, n1)) * n2 + c; };
+        auto ic = [&](int cc) { return static_cast<long long>(a) * sa + static_cast<long long>(b) * n2 + wrap(cc, n2); };
+        const double div =
+            (8.0 * (w(ia(a + 1), 0) - w(ia(a - 1), 0)) - (w(ia(a + 2), 0) - w(ia(a - 2), 0))) * (ih0 / 12.0) +
+            (8.0 * (w(ib(b + 1), 1) - w(ib(b - 1), 1)) - (w(ib(b + 2), 1) - w(ib(b - 2), 1))) * (ih1 / 12.0) +
+            (8.0 * (w(ic(c + 1), 2) - w(ic(c - 1), 2)) - (w(ic(c + 2), 2) - w(ic(c - 2), 2))) * (ih2 / 12.0);
+        const int s = slot[m];
+        double loc = 0.0, av = 0.0, uv = 0.0;
+        if (s >= 0) {
+            av = A[s];
+            uv = U[s];
+            loc = av + uv * qn[m];
+        }
+        if (v) v[m] = dV * (loc - div);
+        if (Ag) Ag[m] = av;
+        if (Ug) Ug[m] = uv;
+    }
+}
+
+__global__ void k_energy_from_A(int n_max, const double *__restrict__ A, const double *__restrict__ n64,
+                                Stats *stats) {
+    const int na = min(stats->n_active, n_max);
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < na; i += gridDim.x * blockDim.x)
+        s += n64[i] * A[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) t += ws[k];
+        atomicAdd(&stats->E_pair, t);
+    }
+}
+
+}  // namespace
+
+int launch_assemble(const int dims[3], const double h[3], double dV, const int *slot,
+                    const double *A, const double *U, const double *dq0dn, const double *dq0dg,
+                    double *v, double *A_grid, double *U_grid, cudaStream_t st) {
+    const long long N = static_cast<long long>(dims[0]) * dims[1] * dims[2];
+    const int bs = 256;
+    long long nb = (N + bs - 1) / bs;
+    if (nb > 1 << 20) nb = 1 << 20;
+    k_assemble<<<static_cast<int>(nb), bs, 0, st>>>(dims[0], dims[1], dims[2], 1.0 / h[0], 1.0 / h[1],
+                                                     1.0 / h[2], dV, slot, A, U, dq0dn, dq0dg, v,
+                                                     A_grid, U_grid);
+    count_launches(1);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
+}
+
+int launch_energy_from_A(int n_max, const double *A, const double *n64, Stats *stats,
+                         cudaStream_t st) {
+    int nb = (n_max + 255) / 256;
+    if (nb > 2048) nb = 2048;
+    if (nb < 1) nb = 1;
+    k_energy_from_A<<<nb, 256, 0, st>>>(n_max, A, n64, stats);
+    count_launches(1);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
+}
+
+}  // namespace vdwdf

@@ -1,0 +1,100 @@
+// Internal declarations shared by the libvdwdf translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vdwdf.h"
+
+namespace vdwdf {
+
+#define VDWDF_CUDA_TRY(expr)                                                   \
+    do {                                                                       \
+        cudaError_t err__ = (expr);                                            \
+        if (err__ != cudaSuccess) {                                            \
+            ::vdwdf::note_cuda_error(err__, #expr, __FILE__, __LINE__);        \
+            return VDWDF_ECUDA;                                                \
+        }                                                                      \
+    } while (0)
+
+void note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+void count_launches(int n);
+
+constexpr int kJT = 256;                // points per staged j tile and per bounding-box tile
+constexpr int kBrick = 4;               // 4 x 4 x 4 grid bricks order the active list
+constexpr int kMaxSmemBytes = 232448;   // 227 KiB opt-in shared memory per block (cc 10.x)
+constexpr int kMaxInst = 24;            // instances per pair-kernel launch
+
+// FP64 point record (x, y, z in grid index units, q0).
+struct __align__(32) dvec4 {
+    double x, y, z, w;
+};
+
+// Device-side counters of one instance (zeroed before use).
+struct Stats {
+    double E_pair;             // sum over ordered pairs of n_i n_j phi (self term included)
+    double n2sum;              // sum over active points of n^2
+    unsigned long long pairs;  // ordered pair interactions other than the self term
+    unsigned long long evals;  // pair evaluations done
+    unsigned long long clamped;
+    unsigned int guard_trips;  // work loops that hit their iteration cap
+    unsigned int qmin_bits, qmax_bits;  // q0 range of active points (FP32 bits; q0 > 0)
+    int n_active;
+};
+
+// Per-instance inputs of the pair kernel.
+struct PairParams {
+    double h2[3];        // squared grid spacings (r^2 = sum h2_a d_a^2, d in index units)
+    double rc2;          // squared cutoff times (1 + 1e-12): inside iff r^2 <= rc2
+    int dims[3];
+    int M[3];            // max |image index| per axis (0: not periodic)
+    int use_cut;
+    const float4 *p32;   // active points: x, y, z (index units), q0
+    const float *n32;
+    const dvec4 *p64;
+    const double *n64;
+    const float4 *blo, *bhi;  // bounding boxes of kJT tiles (index units)
+    double *A, *U;       // potential mode: per active point, accumulated
+    Stats *stats;
+};
+
+// Inputs shared by all instances of a launch.
+struct PairShared {
+    const double *tab64;  // (nD + 2) x (nd + 2) B-spline coefficients / 36, D outer
+    const float *tab32;
+    int S;                // row stride (nd + 2)
+    int nD, nd;
+    double cD, cd;        // tD = r (q_i + q_j) cD,  td = |q_i - q_j|/(q_i + q_j) cd
+    double C_asym;
+    int ks0, ksn;         // FP32: table rows [ks0, ks0 + ksn) resident in shared memory
+    int jtiles_per_item;  // j tiles per work item
+    unsigned int item_limit;  // process only the first item_limit items (autotuning)
+    unsigned int max_iters;   // cap on the work loop of one CTA
+    unsigned int *queue;      // work-queue head (zeroed before launch)
+};
+
+struct PairLaunch {
+    PairShared sh;
+    int ninst;
+    PairParams inst[kMaxInst];
+};
+
+int launch_grad_q0(const int dims[3], const double h[3], const double *n, const double *grad_in,
+                   double *q0, double *dq0dn, double *dq0dg, cudaStream_t st);
+int launch_compact(const int dims[3], const double *n, double n_cut, const double *q0,
+                   const int *brick_order, int nbricks, int *brick_cnt, int *brick_off, int *slot,
+                   float4 *p32, float *n32, dvec4 *p64, double *n64, float4 *blo, float4 *bhi,
+                   Stats *stats, cudaStream_t st);
+int launch_pair(int precision, bool potential, int threads, const PairLaunch &pl, int nctas,
+                cudaStream_t st);
+int pair_smem_bytes(int precision, int ksn, int S);
+int launch_assemble(const int dims[3], const double h[3], double dV, const int *slot,
+                    const double *A, const double *U, const double *dq0dn, const double *dq0dg,
+                    double *v, double *A_grid, double *U_grid, cudaStream_t st);
+int launch_energy_from_A(int n_max, const double *A, const double *n64, Stats *stats,
+                         cudaStream_t st);
+int launch_kernel_eval(int precision, const PairShared &sh, int64_t npts, const double *r,
+                       const double *qi, const double *qj, double *phi, double *rdphi,
+                       cudaStream_t st);
+
+}  // namespace vdwdf

@@ -1,0 +1,56 @@
+"""Run one standard workload through the library and print per-call timings.
+
+    python -m paper_0810_2273_gb300.run_case --workload xe_monolayer \
+        [--dims 24 42 60] [--mode potential|energy] [--precision fp32|fp64] [--repeat 3]
+
+Workloads are the seeded densities of ``paper_0810_2273_gb300.inputs``
+(kr_dimer, xe_monolayer, molecule24, slab_adsorbate); --dims regrids the
+same cell.  The kernel table is built on the host (quadrature level 1) or
+loaded from --table (an .npz written by Table.save).
+"""
+import argparse
+import json
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--workload", default="xe_monolayer",
+                    choices=["kr_dimer", "xe_monolayer", "molecule24", "slab_adsorbate"])
+    ap.add_argument("--dims", type=int, nargs=3, default=None)
+    ap.add_argument("--mode", default="potential", choices=["potential", "energy"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--table", default=None)
+    ap.add_argument("--quad-level", type=int, default=1)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    import paper_0810_2273_gb300 as V
+    from paper_0810_2273_gb300 import build, inputs
+
+    build.build()
+    T = V.Table.load(a.table) if a.table else V.Table.build(400, 30.0, 200, a.quad_level)
+    maker = getattr(inputs, a.workload)
+    w = maker(tuple(a.dims)) if a.dims else maker()
+    dev = torch.device("cuda:0")
+    n = torch.from_numpy(w["density"]).to(dev)
+    args = (w["lengths"], w["periodic"], w["n_cut"], w["r_cut"], T)
+    for k in range(a.repeat):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if a.mode == "potential":
+            E, _, res = V.potential(n, *args, precision=a.precision)
+        else:
+            E, res = V.energy(n, *args, precision=a.precision)
+        torch.cuda.synchronize()
+        res = dict(res)
+        res.update(call=k, E=E, wall_ms=1e3 * (time.perf_counter() - t0), workload=a.workload,
+                   dims=list(n.shape), mode=a.mode, precision=a.precision,
+                   pairs_per_s=res["pairs"] / max(res["ms_pairs"] * 1e-3, 1e-12))
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

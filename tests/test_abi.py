@@ -1,0 +1,129 @@
+"""The C-ABI library: loads without a GPU, exports what include/vdwdf.h declares,
+rejects bad arguments on the host, and its host-side kernel table agrees with
+the oracle's independent quadrature of Dion eq. (14)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "vdwdf.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vdwdf_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_0810_2273_gb300 import _native, build
+    build.build()
+    return _native
+
+
+def test_library_exports_every_declared_symbol(native):
+    lib = native.load()
+    names = _declared_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(native.PROTOTYPES), set(names) ^ set(native.PROTOTYPES)
+    assert lib.vdwdf_version() == 10000
+    for s in (0, -1, -2, -3, -4, -5, -6):
+        assert lib.vdwdf_strerror(s)
+
+
+def test_struct_layouts_match_header(native, tmp_path):
+    """ctypes structs vs the C compiler's layout of include/vdwdf.h."""
+    import subprocess
+    fields = {"vdwdf_grid": native.vdwdf_grid, "vdwdf_result": native.vdwdf_result,
+              "vdwdf_tuning": native.vdwdf_tuning}
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "vdwdf.h"', "int main(void) {"]
+    for s, cls in fields.items():
+        src.append('printf("%s size %%zu\\n", sizeof(%s));' % (s, s))
+        for f, _ in cls._fields_:
+            src.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (s, f, s, f))
+    src.append("return 0; }")
+    c = os.path.join(tmp_path, "layout.c")
+    exe = os.path.join(tmp_path, "layout")
+    open(c, "w").write("\n".join(src))
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        s, f, v = line.split()
+        got = ctypes.sizeof(fields[s]) if f == "size" else getattr(fields[s], f).offset
+        assert got == int(v), line
+
+
+def test_host_side_argument_errors(native):
+    """Invalid inputs are rejected before any device work (no GPU needed)."""
+    lib = native.load()
+    h = ctypes.c_void_p()
+    assert lib.vdwdf_table_build(2, 30.0, 200, 1, None, ctypes.byref(h)) == -1
+    assert lib.vdwdf_table_build(400, -1.0, 200, 1, None, ctypes.byref(h)) == -1
+    assert lib.vdwdf_table_build(400, 30.0, 200, 7, None, ctypes.byref(h)) == -1
+    nodes = np.zeros((4, 4))
+    nodes[1, 1] = np.inf
+    assert lib.vdwdf_table_from_nodes(4, 30.0, 4, nodes.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)) == -1
+    g = native.vdwdf_grid()
+    for a in range(3):
+        g.cell[a][a] = 10.0
+        g.n[a] = 8
+    res = native.vdwdf_result()
+    # null density pointer
+    assert lib.vdwdf_energy(ctypes.byref(g), None, None, 1e-6, 0.0, ctypes.c_void_p(1), 0, None,
+                            ctypes.byref(res), None) == -1
+    # no table
+    assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, None, 0, None,
+                            ctypes.byref(res), None) == -6
+    # periodic without a cutoff
+    g.periodic[0] = 1
+    assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1), 0,
+                            None, ctypes.byref(res), None) == -1
+    g.periodic[0] = 0
+    # non-positive density cutoff, bad precision
+    assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 0.0, 0.0, ctypes.c_void_p(1), 0,
+                            None, ctypes.byref(res), None) == -1
+    assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1), 5,
+                            None, ctypes.byref(res), None) == -1
+    # non-orthorhombic cell
+    g.cell[0][1] = 1.0
+    assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1), 0,
+                            None, ctypes.byref(res), None) == -2
+    # batched: bad count
+    assert lib.vdwdf_energy_batched(0, None, None, 1e-6, 0.0, ctypes.c_void_p(1), 0, None, None, None,
+                                    None) == -1
+
+
+def test_table_build_matches_oracle_quadrature(oracle_mod):
+    """Library table (its own quadrature: octave panels, pi/4-aligned panels, truncation
+    at 63.5 pi with an integration-by-parts tail) vs the oracle's reference quadrature
+    (ratio-1.5 log panels, unit-pi panels, truncation at 255.5 pi, no tail term)."""
+    from paper_0810_2273_gb300 import Table
+    T = Table.build(13, 30.0, 8, 1)
+    nodes = T.nodes
+    D = 30.0 * np.arange(13) / 12
+    dl = np.arange(8) / 8
+    DD, LL = np.meshgrid(D[1:], dl, indexing="ij")
+    ref = oracle_mod.phi((DD * (1 + LL)).ravel(), (DD * (1 - LL)).ravel(),
+                         oracle_mod.QUAD_REFERENCE).reshape(DD.shape)
+    assert np.max(np.abs(nodes[1:] - ref)) < 5e-12
+    assert np.allclose(nodes[0], (4 * nodes[1] - nodes[2]) / 3, rtol=1e-15, atol=0)
+    assert T.info() == (13, 30.0, 8)
+
+
+def test_table_roundtrip_from_nodes(tmp_path):
+    from paper_0810_2273_gb300 import Table
+    rng = np.random.default_rng(0)
+    nodes = rng.normal(size=(9, 6))
+    T = Table.from_nodes(nodes, 12.0)
+    assert np.array_equal(T.nodes, nodes)
+    p = os.path.join(tmp_path, "t.npz")
+    T.save(p)
+    T2 = Table.load(p)
+    assert np.array_equal(T2.nodes, nodes) and T2.info() == (9, 12.0, 6)

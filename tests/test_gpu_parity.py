@@ -1,0 +1,195 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle on the same seeded
+inputs.  Tolerances: E relative 1e-10 (FP64 path), 1e-6 (FP32 path); v max-norm
+relative 1e-10 (FP64), 1e-5 (FP32); integer counts exact."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0810_2273_gb300 as V
+    return V
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def gtable(V, oracle_table):
+    return V.Table.from_nodes(oracle_table, 30.0)
+
+
+def _t(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+
+
+def _problem(oracle_mod, spline, w):
+    return oracle_mod.Problem(w["density"], w["lengths"], w["periodic"], w["n_cut"], w["r_cut"], spline)
+
+
+def _relerr(a, b):
+    return abs(a - b) / abs(b)
+
+
+def test_kernel_eval_matches_oracle(V, dev, gtable, oracle_spline):
+    """Interpolation + asymptote branch in isolation, incl. the last cells and clamping."""
+    rng = np.random.default_rng(3)
+    n = 20000
+    r = rng.uniform(0.0, 25.0, n)
+    qi = 10 ** rng.uniform(-0.7, 0.9, n)
+    qj = 10 ** rng.uniform(-0.7, 0.9, n)
+    # exact end nodes and a few clamped deltas
+    r[:4] = [0.0, 30.0 / 2.0, 60.0 / 4.0, 1e-3]
+    qi[:4] = [1.0, 1.0, 2.0, 1.0]
+    qj[:4] = [1.0, 1.0, 2.0, 1.0]
+    qi[4:8] = [8.0, 9.0, 7.5, 8.0]
+    qj[4:8] = [0.01, 0.02, 0.015, 0.0101]
+    r[4:8] = [0.5, 0.3, 0.2, 1.0]
+    p_o, rd_o, _ = oracle_spline.kernel(r, qi, qj)
+    p64, rd64 = V.kernel_eval(gtable, _t(r, dev), _t(qi, dev), _t(qj, dev), "fp64")
+    p32, rd32 = V.kernel_eval(gtable, _t(r, dev), _t(qi, dev), _t(qj, dev), "fp32")
+    p64, rd64, p32, rd32 = (x.cpu().numpy() for x in (p64, rd64, p32, rd32))
+    sc = np.abs(p_o) + 1e-12
+    assert np.max(np.abs(p64 - p_o) / sc) < 1e-11
+    scr = np.abs(rd_o) + 1e-12 * np.max(np.abs(rd_o))   # absolute floor where r dphi/dd1 = 0
+    assert np.max(np.abs(rd64 - rd_o) / scr) < 1e-9
+    # FP32: relative to the local value, with an absolute floor near the zero crossings
+    big = np.max(np.abs(p_o))
+    assert np.max(np.abs(p32 - p_o) / (np.abs(p_o) + 1e-5 * big)) < 1e-5
+    assert np.max(np.abs(rd32 - rd_o) / (np.abs(rd_o) + 1e-5 * np.max(np.abs(rd_o)))) < 1e-4
+
+
+def test_q0_matches_oracle(V, dev, oracle_mod):
+    rng = np.random.default_rng(5)
+    n = 10 ** rng.uniform(-6, 0.5, size=(10, 13, 7))
+    L = (5.0, 6.5, 3.5)
+    h = [l / d for l, d in zip(L, n.shape)]
+    g = oracle_mod.gradient(n, h)
+    q, qn, qg = oracle_mod.q0(n, g)
+    gq, gqn, gqg = V.q0(_t(n, dev), L)
+    for a, b in ((gq, q), (gqn, qn), (gqg, qg)):
+        a = a.cpu().numpy()
+        assert np.max(np.abs(a - b) / (np.abs(b) + 1e-300)) < 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-6)])
+def test_energy_kr_dimer(V, dev, gtable, oracle_mod, oracle_spline, prec, tol):
+    """Rare-gas dimer, 24x18x18, open cell, all 7,776 points active."""
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.kr_dimer()
+    e = _problem(oracle_mod, oracle_spline, w).energy()
+    E, res = V.energy(_t(w["density"], dev), w["lengths"], w["periodic"], w["n_cut"], w["r_cut"],
+                      gtable, prec)
+    assert _relerr(E, e["E"]) < tol, (E, e["E"])
+    assert _relerr(res["E_diag"], e["E_diag"]) < 1e-12
+    assert res["pairs"] == e["pairs"] == 7776 * 7775
+    assert res["n_active"] == 7776
+    if prec == "fp64":
+        assert res["n_clamped"] == e["clamped"]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-6)])
+def test_energy_periodic_monolayer_small(V, dev, gtable, oracle_mod, oracle_spline, prec, tol):
+    """Monolayer cell on a coarse 12x21x30 grid, periodic x, y, 20 bohr cutoff:
+    spans several tiles with a ragged last tile; pair counts exact."""
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.xe_monolayer((12, 21, 30))
+    e = _problem(oracle_mod, oracle_spline, w).energy()
+    E, res = V.energy(_t(w["density"], dev), w["lengths"], w["periodic"], w["n_cut"], w["r_cut"],
+                      gtable, prec)
+    assert res["n_active"] % 256 != 0
+    assert _relerr(E, e["E"]) < tol, (E, e["E"])
+    assert res["pairs"] == e["pairs"]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_potential_small(V, dev, gtable, oracle_mod, oracle_spline, prec, tol):
+    """E and v on a 20^3 molecule grid and on a periodic slab, whole grid vs the oracle."""
+    from paper_0810_2273_gb300 import inputs
+    for w in (inputs.molecule24((20, 20, 20)), inputs.xe_monolayer((10, 18, 24))):
+        P = _problem(oracle_mod, oracle_spline, w)
+        e = P.energy()
+        vo = P.potential(e["A"], e["U"])
+        E, v, res, A, U = V.potential(_t(w["density"], dev), w["lengths"], w["periodic"], w["n_cut"],
+                                      w["r_cut"], gtable, prec, want_AU=True)
+        v = v.cpu().numpy()
+        assert _relerr(E, e["E"]) < (tol if prec == "fp64" else 1e-6), (w["name"], E, e["E"])
+        assert np.max(np.abs(v - vo)) < tol * np.max(np.abs(vo)), w["name"]
+        flat = w["density"].ravel() >= w["n_cut"]
+        Ag = A.cpu().numpy().ravel()[flat]
+        Ug = U.cpu().numpy().ravel()[flat]
+        assert np.max(np.abs(Ag - e["A"])) < tol * np.max(np.abs(e["A"]))
+        assert np.max(np.abs(Ug - e["U"])) < tol * np.max(np.abs(e["U"]))
+        assert res["pairs"] == e["pairs"]
+
+
+def test_edge_cases(V, dev, gtable, oracle_mod, oracle_spline):
+    """No active point; one active point; grid sides not multiples of 4; huge cutoff."""
+    rng = np.random.default_rng(8)
+    L = (3.5, 4.2, 5.4)
+    n = rng.uniform(0.01, 0.5, size=(5, 7, 9))
+    for prec in ("fp64", "fp32"):
+        E, res = V.energy(_t(n, dev), L, (0, 0, 0), 10.0, 0.0, gtable, prec)
+        assert E == 0.0 and res["n_active"] == 0 and res["pairs"] == 0
+        one = np.full((5, 7, 9), 1e-3)
+        one[2, 3, 4] = 0.8
+        E, res = V.energy(_t(one, dev), L, (0, 0, 0), 0.1, 0.0, gtable, prec)
+        ref = 0.5 * (np.prod(L) / one.size) ** 2 * 0.64 * oracle_spline.f[0, 0]
+        assert abs(E - ref) < 1e-12 * abs(ref) and res["pairs"] == 0
+        P = oracle_mod.Problem(n, L, (0, 0, 0), 0.2, 0.0, oracle_spline)
+        e = P.energy()
+        E, res = V.energy(_t(n, dev), L, (0, 0, 0), 0.2, 0.0, gtable, prec)
+        assert _relerr(E, e["E"]) < (1e-10 if prec == "fp64" else 1e-6)
+        assert res["pairs"] == e["pairs"]
+        Pp = oracle_mod.Problem(n, L, (1, 1, 1), 0.2, 6.0, oracle_spline)
+        ep = Pp.energy()
+        E, res = V.energy(_t(n, dev), L, (1, 1, 1), 0.2, 6.0, gtable, prec)
+        assert _relerr(E, ep["E"]) < (1e-10 if prec == "fp64" else 1e-6)
+        assert res["pairs"] == ep["pairs"]
+
+
+def test_batched_matches_single(V, dev, gtable):
+    """Several uneven densities in one graph-captured launch equal one-at-a-time calls,
+    also on replay with changed density values."""
+    import torch
+    from paper_0810_2273_gb300 import inputs
+    ws = [inputs.kr_dimer((16, 12, 12)), inputs.kr_dimer((20, 15, 15)), inputs.molecule24((14, 14, 14))]
+    ns = [_t(w["density"], dev) for w in ws]
+    for prec, tol in (("fp64", 1e-12), ("fp32", 1e-6)):
+        Es, _ = V.energy_batched(ns, [w["lengths"] for w in ws], [w["periodic"] for w in ws], 1e-6, 0.0,
+                                 gtable, prec)
+        for w, nt, Eb in zip(ws, ns, Es):
+            E1, _ = V.energy(nt, w["lengths"], w["periodic"], 1e-6, 0.0, gtable, "fp64")
+            assert _relerr(Eb, E1) < tol
+        with torch.no_grad():
+            ns[1].mul_(1.1)
+        Es2, _ = V.energy_batched(ns, [w["lengths"] for w in ws], [w["periodic"] for w in ws], 1e-6, 0.0,
+                                  gtable, prec)
+        E1, _ = V.energy(ns[1], ws[1]["lengths"], ws[1]["periodic"], 1e-6, 0.0, gtable, "fp64")
+        assert _relerr(Es2[1], E1) < tol and _relerr(Es2[0], Es[0]) < 1e-14
+        with torch.no_grad():
+            ns[1].div_(1.1)
+
+
+def test_autograd_function(V, dev, gtable):
+    import torch
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.kr_dimer((16, 12, 12))
+    n = _t(w["density"], dev).requires_grad_(True)
+    spec = dict(lengths=w["lengths"], periodic=w["periodic"], n_cut=w["n_cut"], r_cut=w["r_cut"],
+                table=gtable, precision="fp64")
+    E = V.nonlocal_energy(n, spec)
+    E.backward()
+    _, v, _ = V.potential(n.detach(), w["lengths"], w["periodic"], w["n_cut"], w["r_cut"], gtable, "fp64")
+    dV = np.prod(w["lengths"]) / n.numel()
+    assert torch.allclose(n.grad, dV * v, rtol=1e-14, atol=0)
