@@ -28,11 +28,13 @@ sys.path.insert(0, ROOT)
 METRIC = "vdW-DF pair interactions/s (E_nl+v_nl), FP32 vs FP64 path at ≤1e-6 rel err"
 UNIT = "pair interactions/s"
 WORKLOAD = "xe_monolayer 48x84x120 periodic-xy r_cut=20 n_cut=1e-6 (E_nl + v_nl)"
-# FP32-pipe operations per pair interaction of the fused E + v pass, table branch,
-# counted from the formulation (geometry, r, D, delta, cell split, B-spline weights
-# and their derivatives, 4x4 combine for phi, phi_D, phi_delta, chain rule,
-# accumulation); shared-memory loads and MUFU operations are not in this count.
-OPS_PER_PAIR_EV = 117
+# FP32-pipe operations per ordered pair interaction of the fused E + v pass, table
+# branch, counted from the formulation: one evaluation serves the pair in both
+# orders (123 operations per unordered pair: geometry, r, D, delta, cell split,
+# B-spline weights and their derivatives, 4x4 combine for phi, phi_D, phi_delta,
+# chain rule for both d1 and d2, accumulation on both sides); shared-memory loads
+# and MUFU operations are not in this count.
+OPS_PER_PAIR_EV = 62
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 

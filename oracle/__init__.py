@@ -56,14 +56,14 @@ def lib():
         L.orc_phi_table.restype = _i
         L.orc_phi_table.argtypes = [_i, _d, _i, _p, _d, _d, _i, _i, _i]
         L.orc_spline_prepare.restype = _i
-        L.orc_spline_prepare.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p]
+        L.orc_spline_prepare.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _p, _p]
         L.orc_spline_eval_many.restype = _i
         L.orc_spline_eval_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p]
         L.orc_kernel_many.restype = _i
-        L.orc_kernel_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p]
+        L.orc_kernel_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p]
         L.orc_pair_AU.restype = _i
         L.orc_pair_AU.argtypes = ([_i, _p, _p, _p, _p, _p, _i, _i, _i, _d, _d, _d, _i, _i, _i, _d,
-                                   _i, _d, _i, _d, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p])
+                                   _i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p])
         L.orc_pair_brute.restype = _i
         L.orc_pair_brute.argtypes = ([_i, _p, _p, _p, _p, _p, _i, _i, _i, _d, _d, _d, _i, _i, _i,
                                       _d, _d, _d, _d, _d, _i, _i, _i, _p])
@@ -156,7 +156,8 @@ class Spline:
     """Tensor-product cubic spline through the node table (M form).
 
     Boundary conditions: zero slope at D = 0 and delta = 0, zero curvature at
-    the last node of each axis.  ``kernel`` adds the D > Dmax asymptote.
+    the last node of each axis.  ``kernel`` adds the D > Dmax branch: eq. (17)
+    times rho(delta), the 1-D spline through phi(Dmax, delta_l) / phi17(Dmax, delta_l).
     """
 
     def __init__(self, nodes, Dmax=30.0):
@@ -168,14 +169,20 @@ class Spline:
         self.fDD = np.zeros_like(self.f)
         self.fdd = np.zeros_like(self.f)
         self.fDDdd = np.zeros_like(self.f)
+        self.rho = np.zeros(self.nd)
+        self.rhoM = np.zeros(self.nd)
         rc = lib().orc_spline_prepare(self.nD, self.hD, self.nd, self.hd, _ptr(self.f),
-                                      _ptr(self.fDD), _ptr(self.fdd), _ptr(self.fDDdd))
+                                      _ptr(self.fDD), _ptr(self.fdd), _ptr(self.fDDdd),
+                                      _ptr(self.rho), _ptr(self.rhoM))
         if rc != 0:
             raise RuntimeError("orc_spline_prepare failed (%d)" % rc)
 
     def _args(self):
         return (self.nD, self.hD, self.nd, self.hd, _ptr(self.f), _ptr(self.fDD),
                 _ptr(self.fdd), _ptr(self.fDDdd))
+
+    def _kargs(self):
+        return self._args() + (_ptr(self.rho), _ptr(self.rhoM))
 
     def eval(self, D, dl):
         """Spline value and partials (phi, dphi/dD, dphi/ddelta) inside the table."""
@@ -194,7 +201,7 @@ class Spline:
         r, qi, qj = (_f64(x.ravel()) for x in np.broadcast_arrays(r, qi, qj))
         p = np.zeros_like(r)
         rd = np.zeros_like(r)
-        ncl = lib().orc_kernel_many(*self._args(), len(r), _ptr(r), _ptr(qi), _ptr(qj), _ptr(p), _ptr(rd))
+        ncl = lib().orc_kernel_many(*self._kargs(), len(r), _ptr(r), _ptr(qi), _ptr(qj), _ptr(p), _ptr(rd))
         return p, rd, ncl
 
 
@@ -285,7 +292,7 @@ class Problem:
         s = self.spline
         rc = lib().orc_pair_AU(self.n_active, _ptr(self.i0), _ptr(self.i1), _ptr(self.i2),
                                _ptr(self.na), _ptr(self.qa), *self.dims, *self.lengths,
-                               *self.periodic, self.rc, *s._args(), len(qidx), _ptr(qidx),
+                               *self.periodic, self.rc, *s._kargs(), len(qidx), _ptr(qidx),
                                _ptr(A), _ptr(U), _ptr(npairs), _ptr(ncl))
         if rc != 0:
             raise RuntimeError("orc_pair_AU failed (%d)" % rc)

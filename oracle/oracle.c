@@ -339,9 +339,11 @@ static void spline_M_1d(int N, double h, const double *f, int fs, double *M, int
     for (int i = n - 2; i >= 0; --i) M[ms * i] = dp[i] - cp[i] * M[ms * (i + 1)];
 }
 
-/* f: nD x nd nodes (row-major, D outer).  Outputs fDD, fdd, fDDdd same shape. */
+/* f: nD x nd nodes (row-major, D outer).  Outputs fDD, fdd, fDDdd same shape,
+ * and rho, rhoM (nd): the ratio of the last row to eq. (17) at D = Dmax and its
+ * second derivatives along delta (see kernel_pair). */
 int orc_spline_prepare(int nD, double hD, int nd, double hd, const double *f,
-                       double *fDD, double *fdd, double *fDDdd)
+                       double *fDD, double *fdd, double *fDDdd, double *rho, double *rhoM)
 {
     if (nD < 3 || nd < 3) return -1;
     int nmax = nD > nd ? nD : nd;
@@ -351,6 +353,14 @@ int orc_spline_prepare(int nD, double hD, int nd, double hd, const double *f,
     for (int l = 0; l < nd; ++l) spline_M_1d(nD, hD, f + l, nd, fDD + l, nd, cp, dp);
     for (int k = 0; k < nD; ++k) spline_M_1d(nd, hd, f + (size_t)k * nd, 1, fdd + (size_t)k * nd, 1, cp, dp);
     for (int k = 0; k < nD; ++k) spline_M_1d(nd, hd, fDD + (size_t)k * nd, 1, fDDdd + (size_t)k * nd, 1, cp, dp);
+    const double C = 12.0 * pow(4.0 * M_PI / 9.0, 3);
+    const double Dmax = (nD - 1) * hD;
+    for (int l = 0; l < nd; ++l) {
+        double d1 = Dmax * (1.0 + l * hd), d2 = Dmax * (1.0 - l * hd);
+        double a17 = -C / (d1 * d1 * d2 * d2 * (d1 * d1 + d2 * d2));
+        rho[l] = f[(size_t)(nD - 1) * nd + l] / a17;
+    }
+    spline_M_1d(nd, hd, rho, 1, rhoM, 1, cp, dp);
     free(cp); free(dp);
     return 0;
 }
@@ -359,11 +369,26 @@ typedef struct {
     int nD, nd;
     double hD, hd;
     const double *f, *fDD, *fdd, *fDDdd;
+    const double *rho, *rhoM;  /* beyond-table normalisation (see kernel_pair) */
 } orc_spline;
 
-/* S(D, delta) and its partials, D in [0, (nD-1) hD], delta in [0, (nd-1) hd]. */
-static void spline_eval(const orc_spline *s, double D, double dl,
-                        double *phi, double *phiD, double *phid)
+/* 1-D cubic spline in delta (M form) through y at the delta nodes: value and slope. */
+static void spline1_eval(int nd, double hd, const double *y, const double *M, double dl,
+                         double *v, double *dv)
+{
+    double td = dl / hd;
+    int l = (int)floor(td);
+    if (l > nd - 2) l = nd - 2;
+    if (l < 0) l = 0;
+    double u = td - l, A = 1.0 - u, B = u;
+    *v = A * y[l] + B * y[l + 1] + ((A * A * A - A) * M[l] + (B * B * B - B) * M[l + 1]) * hd * hd / 6.0;
+    *dv = (y[l + 1] - y[l]) / hd + (-(3.0 * A * A - 1.0) * M[l] + (3.0 * B * B - 1.0) * M[l + 1]) * hd / 6.0;
+}
+
+/* S(D, delta), its partials and the mixed partial, D in [0, (nD-1) hD],
+ * delta in [0, (nd-1) hd]. */
+static void spline_eval2(const orc_spline *s, double D, double dl,
+                         double *phi, double *phiD, double *phid, double *phiDd)
 {
     double tD = D / s->hD, td = dl / s->hd;
     int k = (int)floor(tD), l = (int)floor(td);
@@ -386,7 +411,7 @@ static void spline_eval(const orc_spline *s, double D, double dl,
     double dbe[2] = {-1.0 / hd, 1.0 / hd};
     double det[2] = {-(3.0 * (1.0 - u) * (1.0 - u) - 1.0) * hd / 6.0,
                      (3.0 * u * u - 1.0) * hd / 6.0};
-    double p = 0.0, pD = 0.0, pd = 0.0;
+    double p = 0.0, pD = 0.0, pd = 0.0, pDd = 0.0;
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) {
             size_t o = (size_t)(k + i) * s->nd + (l + j);
@@ -394,10 +419,18 @@ static void spline_eval(const orc_spline *s, double D, double dl,
             p += al[i] * be[j] * F + ga[i] * be[j] * FDD + al[i] * et[j] * Fdd + ga[i] * et[j] * FDDdd;
             pD += dal[i] * be[j] * F + dga[i] * be[j] * FDD + dal[i] * et[j] * Fdd + dga[i] * et[j] * FDDdd;
             pd += al[i] * dbe[j] * F + ga[i] * dbe[j] * FDD + al[i] * det[j] * Fdd + ga[i] * det[j] * FDDdd;
+            pDd += dal[i] * dbe[j] * F + dga[i] * dbe[j] * FDD + dal[i] * det[j] * Fdd + dga[i] * det[j] * FDDdd;
         }
     *phi = p;
     *phiD = pD;
     *phid = pd;
+    if (phiDd) *phiDd = pDd;
+}
+
+static void spline_eval(const orc_spline *s, double D, double dl,
+                        double *phi, double *phiD, double *phid)
+{
+    spline_eval2(s, D, dl, phi, phiD, phid, NULL);
 }
 
 int orc_spline_eval_many(int nD, double hD, int nd, double hd, const double *f,
@@ -405,19 +438,26 @@ int orc_spline_eval_many(int nD, double hD, int nd, double hd, const double *f,
                          int npts, const double *D, const double *dl,
                          double *phi, double *phiD, double *phid)
 {
-    orc_spline s = {nD, nd, hD, hd, f, fDD, fdd, fDDdd};
+    orc_spline s = {nD, nd, hD, hd, f, fDD, fdd, fDDdd, NULL, NULL};
     for (int p = 0; p < npts; ++p) spline_eval(&s, D[p], dl[p], &phi[p], &phiD[p], &phid[p]);
     return 0;
 }
 
 /* ---------------------------------------------------------------------- */
 /* The kernel as the double sum uses it (section 2):                        */
-/*   D <= Dmax: the spline of the node table, delta clamped to the last     */
-/*              delta node (then d phi / d delta = 0);                      */
-/*   D >  Dmax: Dion eq. (17), phi = -C / (d1^2 d2^2 (d1^2 + d2^2)),        */
-/*              C = 12 (4 pi / 9)^3, d1 = D (1 + delta), d2 = D (1 - delta).*/
+/*   D <= Dmax: the spline of the node table; above the last delta node   */
+/*              (delta > 0.995 for 200 nodes) its natural continuation,     */
+/*              linear in delta with the end slope (zero curvature there),  */
+/*              so phi stays twice differentiable in delta;                */
+/*   D >  Dmax: Dion eq. (17), phi17 = -C / (d1^2 d2^2 (d1^2 + d2^2)),      */
+/*              C = 12 (4 pi / 9)^3, d1 = D (1 + delta), d2 = D (1 - delta),*/
+/*              times rho(delta), the cubic spline (same end conditions as  */
+/*              the table) through phi(Dmax, delta_l) / phi17(Dmax, delta_l).*/
+/* Reading: eq. (17) needs both d1 and d2 large, so at large delta it is off */
+/* by tens of percent at D = Dmax; rho (= 1 where it is accurate) makes phi  */
+/* continuous across Dmax, so that E is a continuous function of n.         */
 /* Returns phi, and r * dphi/dd1 for the pair (d1 = q_i r, d2 = q_j r),     */
-/* with signed ds = (q_i - q_j)/(q_i + q_j) and                             */
+/* with signed ds = (q_i - q_j)/(q_i + q_j), dds/dd1 = (1 - ds)/(2 D):      */
 /*   dphi/dd1 = 1/2 phi_D + (1 - ds)/(2 D) phi_ds.                          */
 /* ---------------------------------------------------------------------- */
 static void kernel_pair(const orc_spline *s, double Dmax, double r, double qi, double qj,
@@ -428,24 +468,27 @@ static void kernel_pair(const orc_spline *s, double Dmax, double r, double qi, d
     double D = 0.5 * r * sq;
     double ds = (qi - qj) / sq;
     double dl = fabs(ds);
+    double sgn = (ds > 0.0) ? 1.0 : ((ds < 0.0) ? -1.0 : 0.0);
+    double dlast = (s->nd - 1) * s->hd;
+    double ext = 0.0;   /* distance beyond the last delta node */
+    if (dl > dlast) { ext = dl - dlast; dl = dlast; *clamped += 1; }
     if (D > Dmax) {
         double d1 = qi * r, d2 = qj * r;
         double d12 = d1 * d1, d22 = d2 * d2;
-        double p = -C / (d12 * d22 * (d12 + d22));
-        *phi = p;
-        double dp1 = -p * (2.0 / d1 + 2.0 * d1 / (d12 + d22));
-        *rdphi1 = r * dp1;
+        double p17 = -C / (d12 * d22 * (d12 + d22));
+        double dp17 = -p17 * (2.0 / d1 + 2.0 * d1 / (d12 + d22));
+        double rho, drho;
+        spline1_eval(s->nd, s->hd, s->rho, s->rhoM, dl, &rho, &drho);
+        rho += drho * ext;
+        *phi = rho * p17;
+        *rdphi1 = r * (rho * dp17 + p17 * drho * sgn * (1.0 - ds) / (2.0 * D));
         return;
     }
-    double dlast = (s->nd - 1) * s->hd;
-    int cl = 0;
-    if (dl > dlast) { dl = dlast; cl = 1; }
-    double p, pD, pd;
-    spline_eval(s, D, dl, &p, &pD, &pd);
-    if (cl) pd = 0.0;
-    *clamped += cl;
+    double p, pD, pd, pDd;
+    spline_eval2(s, D, dl, &p, &pD, &pd, &pDd);
+    p += pd * ext;      /* the continuation: S(D, last) + S_delta(D, last) ext */
+    pD += pDd * ext;
     *phi = p;
-    double sgn = (ds > 0.0) ? 1.0 : ((ds < 0.0) ? -1.0 : 0.0);
     if (D > 0.0)
         *rdphi1 = r * (0.5 * pD + (1.0 - ds) / (2.0 * D) * sgn * pd);
     else
@@ -454,10 +497,11 @@ static void kernel_pair(const orc_spline *s, double Dmax, double r, double qi, d
 
 int orc_kernel_many(int nD, double hD, int nd, double hd, const double *f,
                     const double *fDD, const double *fdd, const double *fDDdd,
+                    const double *rho, const double *rhoM,
                     int npts, const double *r, const double *qi, const double *qj,
                     double *phi, double *rdphi1)
 {
-    orc_spline s = {nD, nd, hD, hd, f, fDD, fdd, fDDdd};
+    orc_spline s = {nD, nd, hD, hd, f, fDD, fdd, fDDdd, rho, rhoM};
     double Dmax = (nD - 1) * hD;
     int cl = 0;
     for (int p = 0; p < npts; ++p) kernel_pair(&s, Dmax, r[p], qi[p], qj[p], &phi[p], &rdphi1[p], &cl);
@@ -484,11 +528,12 @@ int orc_pair_AU(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2,
                 int per0, int per1, int per2, double rc,
                 int nD, double hD, int nd, double hd, const double *f,
                 const double *fDD, const double *fdd, const double *fDDdd,
+                const double *rho, const double *rhoM,
                 int nq, const int32_t *qidx, double *A, double *U,
                 int64_t *npairs, int64_t *nclamp)
 {
     if ((per0 || per1 || per2) && !(rc > 0.0)) return -1;
-    orc_spline s = {nD, nd, hD, hd, f, fDD, fdd, fDDdd};
+    orc_spline s = {nD, nd, hD, hd, f, fDD, fdd, fDDdd, rho, rhoM};
     double Dmax = (nD - 1) * hD;
     int M0 = per0 ? (int)ceil(rc / L0) + 1 : 0;
     int M1 = per1 ? (int)ceil(rc / L1) + 1 : 0;
@@ -531,8 +576,8 @@ int orc_pair_AU(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2,
 }
 
 /* Brute force of the same sum with phi from direct quadrature of eq. (14)
- * at every pair (no table, no spline); D > Dmax still takes eq. (17) and the
- * self term uses phi00 given by the caller.  Returns sum_i n_i A_i. */
+ * at every pair (no table, no spline, no asymptote); the self term uses phi00
+ * given by the caller.  Returns sum_i n_i A_i. */
 int orc_pair_brute(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2,
                    const double *n, const double *q,
                    int n0, int n1, int n2, double L0, double L1, double L2,
@@ -541,7 +586,7 @@ int orc_pair_brute(int Na, const int32_t *i0, const int32_t *i1, const int32_t *
                    double *sum_out)
 {
     if ((per0 || per1 || per2) && !(rc > 0.0)) return -1;
-    const double C = 12.0 * pow(4.0 * M_PI / 9.0, 3);
+    (void)Dmax;
     int M0 = per0 ? (int)ceil(rc / L0) + 1 : 0;
     int M1 = per1 ? (int)ceil(rc / L1) + 1 : 0;
     int M2 = per2 ? (int)ceil(rc / L2) + 1 : 0;
@@ -552,7 +597,7 @@ int orc_pair_brute(int Na, const int32_t *i0, const int32_t *i1, const int32_t *
     double *d2 = (double *)malloc(sizeof(double) * cap);
     double *wt = (double *)malloc(sizeof(double) * cap);
     if (!d1 || !d2 || !wt) { free(d1); free(d2); free(wt); return -2; }
-    double asym = 0.0, self = 0.0;
+    double self = 0.0;
     for (int i = 0; i < Na; ++i) {
         self += n[i] * n[i] * phi00;
         for (int j = 0; j < Na; ++j)
@@ -566,12 +611,6 @@ int orc_pair_brute(int Na, const int32_t *i0, const int32_t *i1, const int32_t *
                         double r2 = dx * dx + dy * dy + dz * dz;
                         if (rc > 0.0 && r2 > rc * rc * (1.0 + 1e-12)) continue;
                         double r = sqrt(r2);
-                        double D = 0.5 * r * (q[i] + q[j]);
-                        if (D > Dmax) {
-                            double a1 = q[i] * r, a2 = q[j] * r;
-                            asym += n[i] * n[j] * (-C / (a1 * a1 * a2 * a2 * (a1 * a1 + a2 * a2)));
-                            continue;
-                        }
                         if (cnt == cap) {
                             cap *= 2;
                             double *t1 = (double *)realloc(d1, sizeof(double) * cap);
@@ -594,7 +633,7 @@ int orc_pair_brute(int Na, const int32_t *i0, const int32_t *i1, const int32_t *
     int rc2 = orc_phi_many((int)cnt, d1, d2, ph, a_min, log_ratio, n_log, m_half, n_osc);
     double tab = 0.0;
     for (size_t p = 0; p < cnt; ++p) tab += wt[p] * ph[p];
-    *sum_out = self + tab + asym;
+    *sum_out = self + tab;
     free(d1); free(d2); free(wt); free(ph);
     return rc2;
 }

@@ -40,17 +40,21 @@ std::atomic<long long> g_launches{0};
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxImages = 64;
 
+// Device layout of the coefficients: (nD + 2) x (nd + 2) bicubic coefficients / 36,
+// then nd + 2 coefficients / 6 of the beyond-table normalisation rho(delta).
 int finish_table(vdwdf_table *t) {
     const int S = t->nd + 2;
+    const size_t main = static_cast<size_t>(t->nD + 2) * S;
     try {
-        t->coef64.assign(static_cast<size_t>(t->nD + 2) * S, 0.0);
-        t->coef32.assign(static_cast<size_t>(t->nD + 2) * S, 0.0f);
+        t->coef64.assign(main + S, 0.0);
+        t->coef32.assign(main + S, 0.0f);
     } catch (const std::bad_alloc &) {
         return VDWDF_EALLOC;
     }
     spline_coefficients(t->nD, t->nd, t->nodes.data(), t->coef64.data());
+    rho_coefficients(t->nD, t->Dmax, t->nd, t->nodes.data(), t->coef64.data() + main);
     for (size_t i = 0; i < t->coef64.size(); ++i) {
-        t->coef64[i] /= 36.0;
+        t->coef64[i] /= (i < main) ? 36.0 : 6.0;
         t->coef32[i] = static_cast<float>(t->coef64[i]);
     }
     return VDWDF_OK;
@@ -215,7 +219,7 @@ struct Work {
 size_t layout(const Geom &G, int nb, bool pot, bool fp64, Work *w, unsigned char *base) {
     Carve c;
     const size_t N = static_cast<size_t>(G.N);
-    const size_t tiles = (N + kJT - 1) / kJT;
+    const size_t tiles = (N + kTile - 1) / kTile;
     const size_t o_q0 = c.take<double>(N);
     const size_t o_qn = pot ? c.take<double>(N) : 0;
     const size_t o_qg = pot ? c.take<double>(3 * N) : 0;
@@ -310,8 +314,8 @@ int smem_budget() {
     return std::min(v, kMaxSmemBytes) - 1024;
 }
 
-int smem_rows_available(int S) {
-    const int base = pair_smem_bytes(VDWDF_FP32, 0, S);
+int smem_rows_available(int threads, int S) {
+    const int base = pair_smem_bytes(VDWDF_FP32, threads, 0, S);
     return std::max(0, (smem_budget() - base) / (S * static_cast<int>(sizeof(float))));
 }
 
@@ -340,6 +344,8 @@ void fill_shared(const vdwdf_table *t, const double *d64, const float *d32, cons
     sh.item_limit = 0xFFFFFFFFu;
     sh.max_iters = max_iters;
     sh.queue = queue;
+    sh.item_E = nullptr;
+    sh.item_cap = 0;
 }
 
 Launch choose_launch(int precision, bool pot, const vdwdf_tuning *tu, const vdwdf_table *t,
@@ -349,15 +355,16 @@ Launch choose_launch(int precision, bool pot, const vdwdf_tuning *tu, const vdwd
     if (tu && (tu->threads == 256 || tu->threads == 512 || tu->threads == 1024)) ln.threads = tu->threads;
     const int sms = sm_count();
     ln.nctas = sms * ctas_per_sm(precision, pot, ln.threads, 0, S);
-    int ipsm = (tu && tu->items_per_sm > 0) ? tu->items_per_sm : 24;
-    const long long nI = (n_active + ln.threads - 1) / ln.threads;
-    const long long nJ = (n_active + kJT - 1) / kJT;
-    const long long want = static_cast<long long>(ipsm) * sms;
-    long long C = std::max<long long>(1, (want + std::max<long long>(nI, 1) - 1) / std::max<long long>(nI, 1));
-    C = std::min<long long>(C, std::max<long long>(nJ, 1));
-    ln.jt = static_cast<int>(std::max<long long>(1, (nJ + C - 1) / C));
+    // work items are (tile of kTile i points) x (jt j tiles); aim at ipsm items per
+    // warp slot so that the dynamic queue balances uneven (culled) items
+    int ipsm = (tu && tu->items_per_sm > 0) ? tu->items_per_sm : 64;
+    const long long nT = std::max<long long>(1, (n_active + kTile - 1) / kTile);
+    const long long want = static_cast<long long>(ipsm) * sms * (ln.threads / 32);
+    long long C = std::max<long long>(1, (want + nT - 1) / nT);
+    C = std::min<long long>(C, nT);
+    ln.jt = static_cast<int>(std::max<long long>(1, (nT + C - 1) / C));
     if (precision == VDWDF_FP32) {
-        const int avail = smem_rows_available(S);
+        const int avail = smem_rows_available(ln.threads, S);
         int rows = std::min(avail, t->nD + 2);
         if (tu && tu->smem_rows < 0) rows = 0;
         if (tu && tu->smem_rows > 0) rows = std::min(rows, tu->smem_rows);
@@ -437,6 +444,7 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
     Timer tm;
     Stats hs;
     std::memset(&hs, 0, sizeof(hs));
+    double *item_buf = nullptr;
     auto body = [&]() -> int {
         tm.mark(0, st);
         int r = prepare(G, n_dev, grad_dev, n_cut, pot, w, st);
@@ -453,13 +461,21 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
             VDWDF_CUDA_TRY(cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st));
             PairLaunch pl;
             std::memset(&pl, 0, sizeof(pl));
-            const long long nI = (hs.n_active + ln.threads - 1) / ln.threads;
-            const long long nJ = (hs.n_active + kJT - 1) / kJT;
-            const long long items = nI * ((nJ + ln.jt - 1) / ln.jt);
-            fill_shared(table, d64, d32, ln, w.queue, static_cast<unsigned int>(std::min<long long>(items + 2, 0xFFFFFFF0LL)), pl.sh);
+            const long long items = pair_items(hs.n_active, ln.jt);
+            if (items > 0xFFFFFFF0LL) return VDWDF_EINVAL;
+            fill_shared(table, d64, d32, ln, w.queue, static_cast<unsigned int>(items + 2), pl.sh);
+            if (!pot) {
+                // one energy partial per work item, summed afterwards in a fixed order
+                if (cudaMallocAsync(reinterpret_cast<void **>(&item_buf), sizeof(double) * items, st) != cudaSuccess)
+                    return VDWDF_EALLOC;
+                pl.sh.item_E = item_buf;
+                pl.sh.item_cap = static_cast<unsigned int>(items);
+            }
             pl.ninst = 1;
             fill_params(G, w, pl.inst[0]);
             r = launch_pair(precision, pot, ln.threads, pl, ln.nctas, st);
+            if (r) return r;
+            r = launch_reduce_items(pl, st);
             if (r) return r;
         }
         tm.mark(2, st);
@@ -475,6 +491,7 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
         return VDWDF_OK;
     };
     rc = body();
+    if (item_buf) cudaFreeAsync(item_buf, st);
     cudaFreeAsync(base, st);
     if (rc == VDWDF_OK && hs.guard_trips) rc = VDWDF_ETIMEOUT;
     if (rc == VDWDF_OK && out) {
@@ -504,12 +521,15 @@ struct BatchPlan {
     std::vector<Work> work;
     std::vector<unsigned char *> bufs;
     unsigned int *queues = nullptr;  // one per pair launch
+    std::vector<double *> item_bufs; // energy partials per work item, one buffer per launch
+    std::vector<long long> item_caps;
     cudaGraphExec_t exec = nullptr;
     int device = 0;
     int launches_per_replay = 0;
     ~BatchPlan() {
         if (exec) cudaGraphExecDestroy(exec);
         for (auto *b : bufs) cudaFree(b);
+        for (auto *b : item_bufs) cudaFree(b);
         if (queues) cudaFree(queues);
     }
 };
@@ -539,15 +559,16 @@ int record_batch(BatchPlan &bp, int ninst, const double *const *n_dev, double n_
         PairLaunch pl;
         std::memset(&pl, 0, sizeof(pl));
         long long items = 0;
-        for (int k = k0; k < k1; ++k) {
-            const long long N = bp.geo[k].N;
-            items += ((N + ln.threads - 1) / ln.threads) * (((N + kJT - 1) / kJT + ln.jt - 1) / ln.jt);
-        }
-        fill_shared(table, d64, d32, ln, bp.queues + g,
-                    static_cast<unsigned int>(std::min<long long>(items + 2, 0xFFFFFFF0LL)), pl.sh);
+        for (int k = k0; k < k1; ++k) items += pair_items(bp.geo[k].N, ln.jt);
+        if (items > 0xFFFFFFF0LL) return VDWDF_EINVAL;
+        fill_shared(table, d64, d32, ln, bp.queues + g, static_cast<unsigned int>(items + 2), pl.sh);
+        pl.sh.item_E = bp.item_bufs[g];
+        pl.sh.item_cap = static_cast<unsigned int>(bp.item_caps[g]);
         pl.ninst = k1 - k0;
         for (int k = k0; k < k1; ++k) fill_params(bp.geo[k], bp.work[k], pl.inst[k - k0]);
         int rc = launch_pair(precision, false, ln.threads, pl, ln.nctas, st);
+        if (rc) return rc;
+        rc = launch_reduce_items(pl, st);
         if (rc) return rc;
     }
     (void)nmax;
@@ -796,6 +817,21 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
         if (cudaMalloc(&bp->queues, sizeof(unsigned int) * ngroups) != cudaSuccess) {
             delete bp;
             return VDWDF_EALLOC;
+        }
+        for (int g = 0; g < ngroups; ++g) {
+            const int k0 = g * kMaxInst, k1 = std::min(ninst, k0 + kMaxInst);
+            long long gsum = 0;
+            for (int k = k0; k < k1; ++k) gsum += geo[k].N;
+            const Launch ln = choose_launch(precision, false, tuning, table, std::max<long long>(1, gsum / (k1 - k0)));
+            long long items = 0;
+            for (int k = k0; k < k1; ++k) items += pair_items(geo[k].N, ln.jt);
+            double *b = nullptr;
+            if (cudaMalloc(&b, sizeof(double) * std::max<long long>(items, 1)) != cudaSuccess) {
+                delete bp;
+                return VDWDF_EALLOC;
+            }
+            bp->item_bufs.push_back(b);
+            bp->item_caps.push_back(items);
         }
         // record the whole batch into a graph on a private stream
         cudaStream_t cs = nullptr;

@@ -20,7 +20,7 @@ namespace vdwdf {
 void note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 void count_launches(int n);
 
-constexpr int kJT = 256;                // points per staged j tile and per bounding-box tile
+constexpr int kTile = 32;               // points per tile: one warp's i set, one staged j tile
 constexpr int kBrick = 4;               // 4 x 4 x 4 grid bricks order the active list
 constexpr int kMaxSmemBytes = 232448;   // 227 KiB opt-in shared memory per block (cc 10.x)
 constexpr int kMaxInst = 24;            // instances per pair-kernel launch
@@ -53,15 +53,15 @@ struct PairParams {
     const float *n32;
     const dvec4 *p64;
     const double *n64;
-    const float4 *blo, *bhi;  // bounding boxes of kJT tiles (index units)
+    const float4 *blo, *bhi;  // bounding boxes of kTile-point tiles (index units)
     double *A, *U;       // potential mode: per active point, accumulated
     Stats *stats;
 };
 
 // Inputs shared by all instances of a launch.
 struct PairShared {
-    const double *tab64;  // (nD + 2) x (nd + 2) B-spline coefficients / 36, D outer
-    const float *tab32;
+    const double *tab64;  // (nD + 2) x (nd + 2) B-spline coefficients / 36, D outer,
+    const float *tab32;   // then nd + 2 coefficients / 6 of rho(delta) (beyond-table scale)
     int S;                // row stride (nd + 2)
     int nD, nd;
     double cD, cd;        // tD = r (q_i + q_j) cD,  td = |q_i - q_j|/(q_i + q_j) cd
@@ -71,6 +71,8 @@ struct PairShared {
     unsigned int item_limit;  // process only the first item_limit items (autotuning)
     unsigned int max_iters;   // cap on the work loop of one CTA
     unsigned int *queue;      // work-queue head (zeroed before launch)
+    double *item_E;           // energy mode: one partial sum per work item (then reduced in
+    unsigned int item_cap;    // a fixed order, so that E is reproducible bit for bit)
 };
 
 struct PairLaunch {
@@ -87,7 +89,15 @@ int launch_compact(const int dims[3], const double *n, double n_cut, const doubl
                    Stats *stats, cudaStream_t st);
 int launch_pair(int precision, bool potential, int threads, const PairLaunch &pl, int nctas,
                 cudaStream_t st);
-int pair_smem_bytes(int precision, int ksn, int S);
+int pair_smem_bytes(int precision, int threads, int ksn, int S);
+// Sum the energy-mode item partials of every instance in a fixed order into its
+// Stats::E_pair (one block per instance).
+int launch_reduce_items(const PairLaunch &pl, cudaStream_t st);
+// Work items of an instance with n_active points and jt j tiles per item.
+__host__ __device__ inline long long pair_items(long long n_active, int jt) {
+    const long long nT = (n_active + kTile - 1) / kTile;
+    return nT * ((nT + jt - 1) / jt);
+}
 int launch_assemble(const int dims[3], const double h[3], double dV, const int *slot,
                     const double *A, const double *U, const double *dq0dn, const double *dq0dg,
                     double *v, double *A_grid, double *U_grid, cudaStream_t st);

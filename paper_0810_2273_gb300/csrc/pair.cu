@@ -4,22 +4,26 @@
 // For active points i, j and image vectors L (periodic axes),
 //   r = |r_i - r_j + L|,  D = r (q_i + q_j)/2,  delta = |q_i - q_j|/(q_i + q_j),
 //   phi = bicubic B-spline of the node table at (D, delta)         if D <= Dmax,
-//   phi = -C / (d1^2 d2^2 (d1^2 + d2^2)), d1 = q_i r, d2 = q_j r     otherwise
-// (section 2: the kernel "can be redefined to depend on two quantities D and
-// delta"; Dion eq. 17 for large D).  Energy mode sums each unordered pair once
-// with weight 2 (phi is symmetric in i, j); potential mode gives, per point,
+//   phi = rho(delta) phi17,  phi17 = -C / (d1^2 d2^2 (d1^2 + d2^2))   otherwise,
+// d1 = q_i r, d2 = q_j r (section 2: the kernel "can be redefined to depend on two
+// quantities D and delta"; Dion eq. 17 for large D, scaled by the cubic spline
+// rho of phi(Dmax, delta) / phi17(Dmax, delta) so that phi is continuous at Dmax).
+// Energy mode sums each unordered pair once with weight 2 (phi is symmetric in
+// i, j); potential mode gives, per point,
 //   A_i = sum_{j,L} n_j phi,   U_i = n_i sum_{j,L} n_j r dphi/dd1,
-//   r dphi/dd1 = r/2 phi_D + (1 - ds)/(q_i + q_j) phi_ds,  ds = (q_i - q_j)/(q_i + q_j)
-// on the table branch and -2 phi (1/q_i + q_i/(q_i^2 + q_j^2)) on the asymptote.
+//   r dphi/dd1 = r/2 phi_D + (1 - ds)/(q_i + q_j) phi_ds,  ds = (q_i - q_j)/(q_i + q_j),
+// and beyond the table rho r dphi17/dd1 + phi17 (1 - ds)/(q_i + q_j) rho_ds with
+// r dphi17/dd1 = -2 phi17 (1/q_i + q_i/(q_i^2 + q_j^2)).
 //
-// Work decomposition: persistent CTAs pull work items (instance, i tile,
-// range of j tiles) from one queue in global memory; each thread owns one i;
-// j tiles of kJT points are staged in shared memory and read as broadcasts;
-// the FP32 path keeps a band of B-spline rows resident in shared memory and
-// reads it with explicit shared-memory loads, other rows from L2.  Periodic
-// images of a j tile are culled against the i tile by bounding boxes.  FP32
-// partial sums over one (j tile, image) are folded into FP64 accumulators.
-// The work loop is bounded (max_iters); nothing waits on another CTA.
+// Work decomposition: persistent CTAs keep a band of B-spline rows resident in
+// shared memory (FP32 path, staged once).  Each warp then works on its own:
+// it pulls work items (instance, tile of kTile i points, range of j tiles) from
+// one queue in global memory, culls every (j tile, image) against its i tile
+// by bounding boxes, stages surviving j tiles in a private shared-memory
+// buffer (warp-synchronous, no block barrier), and runs the pair loop with
+// each lane owning one i and the j points read as broadcasts.  FP32 partial
+// sums over one j tile are folded into FP64 accumulators.  The work loop is
+// bounded (max_iters); nothing waits on another warp or CTA.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -68,8 +72,7 @@ __device__ __forceinline__ int floor_split(double x, double &frac) {
     return static_cast<int>(f);
 }
 
-// Cubic B-spline weights times 6 (the table holds coefficients / 36) and their
-// t-derivatives times 6.
+// Cubic B-spline weights times 6 and their t-derivatives times 6.
 template <typename R>
 __device__ __forceinline__ void bw(R t, R w[4]) {
     const R t2 = t * t, t3 = t2 * t, s = R(1) - t;
@@ -125,7 +128,8 @@ struct Consts {
 
 template <typename R>
 struct Table {
-    const R *g;      // whole coefficient table in global memory, row stride S
+    const R *g;      // bicubic coefficients / 36 in global memory, row stride S
+    const R *rho;    // rho(delta) coefficients / 6 (after the bicubic block)
     uint32_t s;      // shared-memory address of the resident band (FP32), same stride
     int k0, kn;      // band rows [k0, k0 + kn)
     int S;
@@ -153,57 +157,75 @@ __device__ __forceinline__ void interp(const Table<R> &tb, int k, int l, const R
     combine<POT, R>(c, wD, dwD, wd, dwd, p, pt, pu);
 }
 
-// One pair: phi and (POT) r dphi/dd1; counts a clamped delta.
+// One pair: phi and (POT) r dphi/dd1, r dphi/dd2; counts a clamped delta.
+// With ds = (q_i - q_j)/(q_i + q_j): dds/dd1 = (1 - ds)/(2D), dds/dd2 = -(1 + ds)/(2D).
 template <bool POT, typename R>
 __device__ __forceinline__ void pair_phi(R r2, R qi, R qj, R inv_qi, R qi2, const Consts<R> &K,
-                                         const Table<R> &tb, R &phi, R &rd, unsigned &ncl) {
+                                         const Table<R> &tb, R &phi, R &rd, R &rd2, unsigned &ncl) {
     const R r = rlen(r2);
     const R sq = qi + qj;
     const R dq = qi - qj;
     const R isq = recip(sq);
+    // delta cell; beyond the last node the spline continues linearly with its end
+    // slope (it has zero curvature there): the weights become w(u) + e w'(u), e the
+    // distance past the node in cells.  No index leaves the table.
+    const R dl = fabs(dq) * isq;
+    const R td0 = dl * K.cd;
+    const bool cl = td0 > K.tdmax;
+    ncl += cl ? 1u : 0u;
+    R td = fmin(fmax(td0, R(0)), K.tdclamp);
+    R u;
+    int l = floor_split(td, u);
+    if (sizeof(R) == 8 && l > K.lmax) {  // FP64 keeps the exact end node: last cell at u = 1
+        l = K.lmax;
+        u = td - R(l);
+    }
+    R wd[4], dwd[4];
+    bw<R>(u, wd);
+    if (POT || cl) bdw<R>(u, dwd);
+    if (cl) {
+        const R e = td0 - td;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) wd[n] += e * dwd[n];
+    }
+    const R sgn1 = dq > R(0) ? (R(1) - dl) : -(R(1) + dl);   // sign(ds) (1 - ds)
+    const R sgn2 = dq > R(0) ? (R(1) + dl) : -(R(1) - dl);   // sign(ds) (1 + ds)
     R tD = r * sq * K.cD;
-    // the table is read only for 0 <= tD <= nD - 1 (also false for NaN); delta is
-    // clamped into [0, last node] so that no index leaves the table
+    // the table is read only for 0 <= tD <= nD - 1 (false for NaN as well)
     if (tD >= R(0) && tD <= K.tDmax) {
         tD = fmin(tD, K.tDclamp);
-        const R dl = fabs(dq) * isq;
-        R td = dl * K.cd;
-        const bool cl = td > K.tdmax;
-        ncl += cl ? 1u : 0u;
-        td = fmin(fmax(td, R(0)), K.tdclamp);
-        R t, u;
+        R t;
         int k = floor_split(tD, t);
-        int l = floor_split(td, u);
-        if (sizeof(R) == 8) {  // FP64 keeps the exact end nodes: last cell at t = 1
-            if (k > K.kmax) {
-                k = K.kmax;
-                t = tD - R(k);
-            }
-            if (l > K.lmax) {
-                l = K.lmax;
-                u = td - R(l);
-            }
+        if (sizeof(R) == 8 && k > K.kmax) {
+            k = K.kmax;
+            t = tD - R(k);
         }
-        R wD[4], wd[4], dwD[4], dwd[4];
+        R wD[4], dwD[4];
         bw<R>(t, wD);
-        bw<R>(u, wd);
-        if (POT) {
-            bdw<R>(t, dwD);
-            bdw<R>(u, dwd);
-        }
+        if (POT) bdw<R>(t, dwD);
         R pt = 0, pu = 0;
         interp<POT, R>(tb, k, l, wD, dwD, wd, dwd, phi, pt, pu);
         if (POT) {
-            const R sgn1 = dq > R(0) ? (R(1) - dl) : -(R(1) + dl);
-            pu = cl ? R(0) : pu;
-            rd = r * K.cD * pt + isq * K.cd * sgn1 * pu;
+            const R a = r * K.cD * pt, b = isq * K.cd * pu;
+            rd = a + b * sgn1;
+            rd2 = a - b * sgn2;
         }
     } else {
         const R r4 = r2 * r2;
         const R qj2 = qj * qj;
         const R s2 = qi2 + qj2;
-        phi = -K.C * recip(r4 * r2 * qi2 * qj2 * s2);
-        if (POT) rd = R(-2) * phi * (inv_qi + qi * recip(s2));
+        const R p17 = -K.C * recip(r4 * r2 * qi2 * qj2 * s2);
+        const R *rc = tb.rho + l;
+        const R c0 = __ldg(rc), c1 = __ldg(rc + 1), c2 = __ldg(rc + 2), c3 = __ldg(rc + 3);
+        const R rho = wd[0] * c0 + wd[1] * c1 + wd[2] * c2 + wd[3] * c3;
+        phi = rho * p17;
+        if (POT) {
+            const R drho = dwd[0] * c0 + dwd[1] * c1 + dwd[2] * c2 + dwd[3] * c3;
+            const R is2 = recip(s2);
+            const R b = p17 * isq * K.cd * drho;
+            rd = rho * (R(-2) * p17 * (inv_qi + qi * is2)) + b * sgn1;
+            rd2 = rho * (R(-2) * p17 * (recip(qj) + qj * is2)) - b * sgn2;
+        }
     }
 }
 
@@ -226,45 +248,21 @@ __device__ void make_consts(const PairShared &sh, Consts<R> &K) {
     K.lmax = sh.nd - 2;
 }
 
-__device__ __forceinline__ void fold(float &a32, double &a64) {
-    a64 += static_cast<double>(a32);
-    a32 = 0.0f;
-}
-__device__ __forceinline__ void fold(double &a, double &a64) {
-    a64 += a;
-    a = 0.0;
+template <typename R>
+__device__ void make_table(const PairShared &sh, Table<R> &tb) {
+    tb.S = sh.S;
+    tb.g = sizeof(R) == 4 ? reinterpret_cast<const R *>(sh.tab32) : reinterpret_cast<const R *>(sh.tab64);
+    tb.rho = tb.g + static_cast<size_t>(sh.nD + 2) * sh.S;
+    tb.s = 0;
+    tb.k0 = 0;
+    tb.kn = 0;
 }
 
-// Sum over the block; result valid in thread 0.  All threads must call it.
 template <typename T>
-__device__ __forceinline__ T block_sum(T v, T *red) {
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    T s = T(0);
-    if (threadIdx.x < 32) {
-        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : T(0);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    }
-    return s;
-}
-
-// Squared distance between the i box and the j box shifted by image m.
-__device__ __forceinline__ float box_gap2(const float ilo[3], const float ihi[3], const float jl[3],
-                                          const float jh[3], const int m[3], const int dims[3],
-                                          const float h2[3]) {
-    float d2 = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float s = static_cast<float>(m[a] * dims[a]);
-        const float g = fmaxf(0.0f, fmaxf(ilo[a] - jh[a] + s, jl[a] - ihi[a] - s));
-        d2 += h2[a] * g * g;
-    }
-    return d2;
+    return v;
 }
 
 // Spherical cutoff, inclusive: a pair is inside iff r^2 <= rc2 (the host folds a
@@ -286,75 +284,119 @@ __device__ __forceinline__ bool beyond(double r2, double, double, double, const 
     return r2 > c.rc2d;
 }
 
+// Squared distance between the i box and the j box shifted by image m.
+__device__ __forceinline__ float box_gap2(const float ilo[3], const float ihi[3], const float jl[3],
+                                          const float jh[3], const int m[3], const int dims[3],
+                                          const float h2[3]) {
+    float d2 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float s = static_cast<float>(m[a] * dims[a]);
+        const float g = fmaxf(0.0f, fmaxf(ilo[a] - jh[a] + s, jl[a] - ihi[a] - s));
+        d2 += h2[a] * g * g;
+    }
+    return d2;
+}
+
+// Per-warp running totals, flushed to the instance's counters when the warp
+// moves to another instance and at exit (lane 0 holds the warp's total).
+struct WarpTotals {
+    double E;
+    unsigned long long pairs, evals, clamped;
+    int inst;
+};
+
+__device__ __forceinline__ void flush(WarpTotals &t, const PairLaunch &pl, bool energy) {
+    const double E = warp_sum(t.E);
+    const unsigned long long pairs = warp_sum(t.pairs), clamped = warp_sum(t.clamped);
+    if (t.inst >= 0 && (threadIdx.x & 31) == 0) {
+        Stats *s = pl.inst[t.inst].stats;
+        if (energy && E != 0.0) atomicAdd(&s->E_pair, E);
+        if (pairs) atomicAdd(&s->pairs, pairs);
+        if (t.evals) atomicAdd(&s->evals, t.evals);
+        if (clamped) atomicAdd(&s->clamped, clamped);
+    }
+    t.E = 0.0;
+    t.pairs = t.evals = t.clamped = 0;
+}
+
 // MODE 0: energy (unordered pairs), MODE 1: potential (A, U per point).
 template <typename R, int MODE, int NT>
 __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaunch pl) {
     constexpr bool POT = (MODE == 1);
+    constexpr int NW = NT / 32;
     using P = typename PT<R>::P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    P *sp = reinterpret_cast<P *>(smem_raw);
-    R *sn = reinterpret_cast<R *>(smem_raw + sizeof(P) * kJT);
-    double *red = reinterpret_cast<double *>(smem_raw + (sizeof(P) + sizeof(R)) * kJT);
-    unsigned long long *redu = reinterpret_cast<unsigned long long *>(red + 32);
-    __shared__ unsigned int s_item;
     __shared__ unsigned int s_prefix[kMaxInst + 1];
     __shared__ int s_C[kMaxInst];
 
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    P *sp = reinterpret_cast<P *>(smem_raw) + warp * kTile;
+    R *sn = reinterpret_cast<R *>(smem_raw + sizeof(P) * kTile * NW) + warp * kTile;
+
     const PairShared &sh = pl.sh;
     Table<R> tb;
-    tb.S = sh.S;
+    make_table<R>(sh, tb);
     Consts<R> K;
     make_consts<R>(sh, K);
     if constexpr (sizeof(R) == 4) {
-        tb.g = reinterpret_cast<const R *>(sh.tab32);
-        float *band = reinterpret_cast<float *>(smem_raw + (sizeof(P) + sizeof(R)) * kJT + 64 * sizeof(double));
+        float *band = reinterpret_cast<float *>(smem_raw + (sizeof(P) + sizeof(R)) * kTile * NW);
         tb.s = static_cast<uint32_t>(__cvta_generic_to_shared(band));
         tb.k0 = sh.ks0;
         tb.kn = sh.ksn;
         const int nb = sh.ksn * sh.S;
         const float *src = sh.tab32 + static_cast<size_t>(sh.ks0) * sh.S;
         for (int e = threadIdx.x; e < nb; e += NT) band[e] = __ldg(src + e);
-    } else {
-        tb.g = reinterpret_cast<const R *>(sh.tab64);
-        tb.s = 0;
-        tb.k0 = 0;
-        tb.kn = 0;
     }
     // work items per instance: (i tiles) x (chunks of jtiles_per_item j tiles)
     if (threadIdx.x == 0) {
         unsigned int acc = 0;
         for (int k = 0; k < pl.ninst; ++k) {
             const int na = pl.inst[k].stats->n_active;
-            const int nI = (na + NT - 1) / NT;
-            const int nJ = (na + kJT - 1) / kJT;
-            const int C = max(1, (nJ + sh.jtiles_per_item - 1) / sh.jtiles_per_item);
+            const int nT = (na + kTile - 1) / kTile;
+            const int C = max(1, (nT + sh.jtiles_per_item - 1) / sh.jtiles_per_item);
             s_prefix[k] = acc;
             s_C[k] = C;
-            acc += static_cast<unsigned int>(nI) * static_cast<unsigned int>(C);
+            acc += static_cast<unsigned int>(pair_items(na, sh.jtiles_per_item));
         }
         s_prefix[pl.ninst] = acc;
     }
-    __syncthreads();
+    __syncthreads();  // the only block barrier: table band and item counts ready
     const unsigned int n_items = min(s_prefix[pl.ninst], sh.item_limit);
+
+    WarpTotals tot;
+    tot.E = 0.0;
+    tot.pairs = tot.evals = tot.clamped = 0;
+    tot.inst = -1;
 
     for (unsigned int iter = 0;; ++iter) {
         if (iter >= sh.max_iters) {
-            if (threadIdx.x == 0) atomicAdd(&pl.inst[0].stats->guard_trips, 1u);
+            if (lane == 0) atomicAdd(&pl.inst[0].stats->guard_trips, 1u);
             break;
         }
-        if (threadIdx.x == 0) s_item = atomicAdd(sh.queue, 1u);
-        __syncthreads();
-        const unsigned int item = s_item;
-        __syncthreads();
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(sh.queue, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
         int k = 0;
         while (k + 1 < pl.ninst && item >= s_prefix[k + 1]) ++k;
+        if (k != tot.inst) {
+            flush(tot, pl, !POT);
+            tot.inst = k;
+        }
         const PairParams &pp = pl.inst[k];
         const unsigned int local = item - s_prefix[k];
         const int C = s_C[k];
         const int I = static_cast<int>(local / C), c = static_cast<int>(local % C);
         const int n_act = pp.stats->n_active;
-        const int nJ = (n_act + kJT - 1) / kJT;
+        const int nT = (n_act + kTile - 1) / kTile;
+        const int Js = I;  // i <-> j folded: j tiles from the i tile on
+        const int J0 = Js + c * sh.jtiles_per_item;
+        const int J1 = min(nT, J0 + sh.jtiles_per_item);
+        if (J0 >= J1) {
+            if (!POT && lane == 0 && sh.item_E && item < sh.item_cap) sh.item_E[item] = 0.0;
+            continue;
+        }
 
         R h2[3];
         float h2f[3], rcm[3];
@@ -380,9 +422,9 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
         const P *pts = PT<R>::pts(pp);
         const R *nsrc = PT<R>::ns(pp);
 
-        const int ig = I * NT + static_cast<int>(threadIdx.x);
+        const int ig = I * kTile + lane;
         const bool act = ig < n_act;
-        const int ni_act = min(NT, n_act - I * NT);
+        const int ni_act = min(kTile, n_act - I * kTile);
         R xi = 0, yi = 0, zi = 0, qi = 1, ni = 0;
         if (act) {
             const P pi = PT<R>::load(pts, ig);
@@ -393,27 +435,13 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
             ni = __ldg(nsrc + ig);
         }
         const R inv_qi = R(1) / qi, qi2 = qi * qi;
-        float ilo[3] = {3e38f, 3e38f, 3e38f}, ihi[3] = {-3e38f, -3e38f, -3e38f};
-        for (int s = 0; s < NT / kJT; ++s) {
-            const int t = I * (NT / kJT) + s;
-            if (t * kJT < n_act) {
-                const float4 lo = __ldg(pp.blo + t), hi = __ldg(pp.bhi + t);
-                ilo[0] = fminf(ilo[0], lo.x);
-                ilo[1] = fminf(ilo[1], lo.y);
-                ilo[2] = fminf(ilo[2], lo.z);
-                ihi[0] = fmaxf(ihi[0], hi.x);
-                ihi[1] = fmaxf(ihi[1], hi.y);
-                ihi[2] = fmaxf(ihi[2], hi.z);
-            }
-        }
-        const int Js = POT ? 0 : (I * NT) / kJT;
-        const int J0 = Js + c * sh.jtiles_per_item;
-        const int J1 = min(nJ, J0 + sh.jtiles_per_item);
+        const float4 ib0 = __ldg(pp.blo + I), ib1 = __ldg(pp.bhi + I);
+        const float ilo[3] = {ib0.x, ib0.y, ib0.z}, ihi[3] = {ib1.x, ib1.y, ib1.z};
         double A64 = 0.0, U64 = 0.0;
-        unsigned long long cnt = 0, nclamp = 0, evals = 0;
+        unsigned int cnt = 0, nclamp = 0;
         for (int J = J0; J < J1; ++J) {
-            const int jb = J * kJT;
-            const int jn = min(kJT, n_act - jb);
+            const int jb = J * kTile;
+            const int jn = min(kTile, n_act - jb);
             const float4 jlo = __ldg(pp.blo + J), jhi = __ldg(pp.bhi + J);
             const float jl[3] = {jlo.x, jlo.y, jlo.z}, jh[3] = {jhi.x, jhi.y, jhi.z};
             int mlo[3], mhi[3];
@@ -436,12 +464,17 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
                         any = !use_cut || box_gap2(ilo, ihi, jl, jh, mm, dims, h2f) <= rc2_box;
                     }
             if (!any) continue;
-            if (static_cast<int>(threadIdx.x) < jn) {
-                sp[threadIdx.x] = PT<R>::load(pts, jb + threadIdx.x);
-                sn[threadIdx.x] = __ldg(nsrc + jb + threadIdx.x);
+            __syncwarp();
+            if (lane < jn) {
+                sp[lane] = PT<R>::load(pts, jb + lane);
+                sn[lane] = __ldg(nsrc + jb + lane);
             }
-            __syncthreads();
-            const bool overlap = !POT && (jb < (I + 1) * NT);
+            __syncwarp();
+            R a_acc = 0, u_acc = 0;  // i side (this lane's i)
+            R ja = 0, ju = 0;        // j side: lane L collects j = jb + L
+            // weights: off-diagonal tiles count every pair for i and for j; in the
+            // diagonal tile j > i counts for both, j == i (self and self-images) for i only
+            const bool diag = (J == I);
             for (int m0 = mlo[0]; m0 <= mhi[0]; ++m0)
                 for (int m1 = mlo[1]; m1 <= mhi[1]; ++m1)
                     for (int m2 = mlo[2]; m2 <= mhi[2]; ++m2) {
@@ -450,83 +483,92 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
                         const R xs = xi + static_cast<R>(m0 * dims[0]);
                         const R ys = yi + static_cast<R>(m1 * dims[1]);
                         const R zs = zi + static_cast<R>(m2 * dims[2]);
-                        R a_acc = 0, u_acc = 0;
-                        unsigned int c32 = 0, cl32 = 0;
-                        evals += static_cast<unsigned long long>(jn) * static_cast<unsigned long long>(ni_act);
-                        if (overlap) {
-                            // per-pair weights: 2 (j > i), 1 (j == i), 0 (j < i)
-                            for (int jj = 0; jj < jn; ++jj) {
-                                const P pj = sp[jj];
-                                const R nj = sn[jj];
-                                const R dx = xs - pj.x, dy = ys - pj.y, dz = zs - pj.z;
-                                const R r2 = h2[0] * (dx * dx) + h2[1] * (dy * dy) + h2[2] * (dz * dz);
-                                const int jg = jb + jj;
-                                const R wgt = (jg > ig) ? R(2) : ((jg == ig) ? R(1) : R(0));
-                                if (wgt == R(0) || (use_cut && beyond(r2, dx, dy, dz, cut))) continue;
-                                R phi, rd;
-                                unsigned ncl = 0;
-                                pair_phi<false, R>(r2, qi, pj.w, inv_qi, qi2, K, tb, phi, rd, ncl);
-                                a_acc += wgt * nj * phi;
-                                c32 += (r2 > R(0)) ? static_cast<unsigned>(wgt) : 0u;
-                                cl32 += ncl * static_cast<unsigned>(wgt);
-                            }
-                            if (act) {
-                                fold(a_acc, A64);
-                                cnt += c32;
-                                nclamp += cl32;
-                            }
-                        } else {
+                        tot.evals += static_cast<unsigned long long>(jn) * static_cast<unsigned long long>(ni_act);
 #pragma unroll 2
-                            for (int jj = 0; jj < jn; ++jj) {
-                                const P pj = sp[jj];
-                                const R nj = sn[jj];
-                                const R dx = xs - pj.x, dy = ys - pj.y, dz = zs - pj.z;
-                                const R r2 = h2[0] * (dx * dx) + h2[1] * (dy * dy) + h2[2] * (dz * dz);
-                                if (use_cut && beyond(r2, dx, dy, dz, cut)) continue;
-                                R phi, rd = 0;
+                        for (int jj = 0; jj < jn; ++jj) {
+                            const P pj = sp[jj];
+                            const R nj = sn[jj];
+                            const R dx = xs - pj.x, dy = ys - pj.y, dz = zs - pj.z;
+                            const R r2 = h2[0] * (dx * dx) + h2[1] * (dy * dy) + h2[2] * (dz * dz);
+                            const bool both = !diag || jj > lane;
+                            const bool inside = act && (both || jj == lane) && !(use_cut && beyond(r2, dx, dy, dz, cut));
+                            R cA = 0, cU = 0;
+                            if (inside) {
+                                R phi, rd = 0, rd2 = 0;
                                 unsigned ncl = 0;
-                                pair_phi<POT, R>(r2, qi, pj.w, inv_qi, qi2, K, tb, phi, rd, ncl);
-                                a_acc += nj * phi;
-                                if (POT) u_acc += nj * rd;
-                                c32 += (r2 > R(0)) ? 1u : 0u;
-                                cl32 += ncl;
-                            }
-                            if (act) {
+                                pair_phi<POT, R>(r2, qi, pj.w, inv_qi, qi2, K, tb, phi, rd, rd2, ncl);
+                                const unsigned wt = both ? 2u : 1u;  // ordered pairs represented
                                 if (POT) {
-                                    fold(a_acc, A64);
-                                    fold(u_acc, U64);
-                                    cnt += c32;
-                                    nclamp += cl32;
+                                    a_acc += nj * phi;
+                                    u_acc += nj * rd;
+                                    if (both) {
+                                        cA = ni * phi;
+                                        cU = ni * rd2;
+                                    }
                                 } else {
-                                    double t = 0.0;
-                                    fold(a_acc, t);
-                                    A64 += 2.0 * t;
-                                    cnt += 2ull * c32;
-                                    nclamp += 2ull * cl32;
+                                    a_acc += static_cast<R>(wt) * nj * phi;
+                                }
+                                cnt += (r2 > R(0)) ? wt : 0u;
+                                nclamp += ncl * wt;
+                            }
+                            if (POT && __any_sync(0xffffffffu, cA != R(0) || cU != R(0))) {
+                                cA = warp_sum(cA);
+                                cU = warp_sum(cU);
+                                if (lane == jj) {
+                                    ja += cA;
+                                    ju += cU;
                                 }
                             }
                         }
                     }
-            __syncthreads();
-        }
-        if (POT) {
-            if (act) {
-                atomicAdd(pp.A + ig, A64);
-                atomicAdd(pp.U + ig, static_cast<double>(ni) * U64);
+            A64 += static_cast<double>(a_acc);
+            U64 += static_cast<double>(u_acc);
+            if (POT && lane < jn) {
+                if (ja != R(0)) atomicAdd(pp.A + jb + lane, static_cast<double>(ja));
+                if (ju != R(0)) atomicAdd(pp.U + jb + lane, static_cast<double>(sn[lane]) * static_cast<double>(ju));
             }
-        } else {
-            const double e = act ? static_cast<double>(ni) * A64 : 0.0;
-            const double es = block_sum<double>(e, red);
-            if (threadIdx.x == 0) atomicAdd(&pp.stats->E_pair, es);
         }
-        const unsigned long long cs = block_sum<unsigned long long>(act ? cnt : 0ull, redu);
-        if (threadIdx.x == 0) atomicAdd(&pp.stats->pairs, cs);
-        const unsigned long long cl = block_sum<unsigned long long>(act ? nclamp : 0ull, redu);
-        if (threadIdx.x == 0) {
-            atomicAdd(&pp.stats->clamped, cl);
-            atomicAdd(&pp.stats->evals, evals);
+        if (act) {
+            if (POT) {
+                if (A64 != 0.0) atomicAdd(pp.A + ig, A64);
+                if (U64 != 0.0) atomicAdd(pp.U + ig, static_cast<double>(ni) * U64);
+            }
+            tot.pairs += cnt;
+            tot.clamped += nclamp;
+        }
+        if (!POT) {
+            // the item's energy partial, summed over lanes in a fixed order
+            const double e = warp_sum(act ? static_cast<double>(ni) * A64 : 0.0);
+            if (lane == 0) {
+                if (sh.item_E && item < sh.item_cap)
+                    sh.item_E[item] = e;
+                else
+                    tot.E += e;
+            }
         }
     }
+    flush(tot, pl, !POT);
+}
+
+// Fixed-order sum of an instance's energy-mode item partials (block k: instance k).
+__global__ void k_reduce_items(const __grid_constant__ PairLaunch pl) {
+    const int k = blockIdx.x;
+    if (k >= pl.ninst) return;
+    unsigned int lo = 0;
+    for (int t = 0; t < k; ++t)
+        lo += static_cast<unsigned int>(pair_items(pl.inst[t].stats->n_active, pl.sh.jtiles_per_item));
+    const unsigned int n = static_cast<unsigned int>(pair_items(pl.inst[k].stats->n_active, pl.sh.jtiles_per_item));
+    const unsigned int hi = min(lo + n, pl.sh.item_cap);
+    double s = 0.0;
+    for (unsigned int i = lo + threadIdx.x; i < hi; i += blockDim.x) s += pl.sh.item_E[i];
+    __shared__ double part[256];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (static_cast<int>(threadIdx.x) < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&pl.inst[k].stats->E_pair, part[0]);
 }
 
 // The kernel at given (r, q_i, q_j), for isolated checks of the interpolation.
@@ -534,20 +576,16 @@ template <typename R>
 __global__ void k_kernel_eval(const PairShared sh, int64_t npts, const double *r,
                               const double *qi, const double *qj, double *phi, double *rd) {
     Table<R> tb;
-    tb.S = sh.S;
-    tb.g = sizeof(R) == 4 ? reinterpret_cast<const R *>(sh.tab32) : reinterpret_cast<const R *>(sh.tab64);
-    tb.s = 0;
-    tb.k0 = 0;
-    tb.kn = 0;
+    make_table<R>(sh, tb);
     Consts<R> K;
     make_consts<R>(sh, K);
     for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < npts;
          p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const R rr = static_cast<R>(r[p]);
         const R a = static_cast<R>(qi[p]), b = static_cast<R>(qj[p]);
-        R ph, rdv = 0;
+        R ph, rdv = 0, rd2 = 0;
         unsigned ncl = 0;
-        pair_phi<true, R>(rr * rr, a, b, R(1) / a, a * a, K, tb, ph, rdv, ncl);
+        pair_phi<true, R>(rr * rr, a, b, R(1) / a, a * a, K, tb, ph, rdv, rd2, ncl);
         phi[p] = static_cast<double>(ph);
         rd[p] = static_cast<double>(rdv);
     }
@@ -575,21 +613,29 @@ int launch_nt(int threads, const PairLaunch &pl, int nctas, size_t smem, cudaStr
 
 }  // namespace
 
-int pair_smem_bytes(int precision, int ksn, int S) {
+int pair_smem_bytes(int precision, int threads, int ksn, int S) {
     const size_t pt = precision == VDWDF_FP64 ? sizeof(dvec4) + sizeof(double) : sizeof(float4) + sizeof(float);
-    size_t b = pt * kJT + 64 * sizeof(double);
+    size_t b = pt * kTile * static_cast<size_t>(threads / 32);
     if (precision != VDWDF_FP64) b += static_cast<size_t>(ksn) * S * sizeof(float);
     return static_cast<int>(b);
 }
 
 int launch_pair(int precision, bool potential, int threads, const PairLaunch &pl, int nctas,
                 cudaStream_t st) {
-    const size_t smem = static_cast<size_t>(pair_smem_bytes(precision, pl.sh.ksn, pl.sh.S));
+    const size_t smem = static_cast<size_t>(pair_smem_bytes(precision, threads, pl.sh.ksn, pl.sh.S));
     if (precision == VDWDF_FP64)
         return potential ? launch_nt<double, 1>(threads, pl, nctas, smem, st)
                          : launch_nt<double, 0>(threads, pl, nctas, smem, st);
     return potential ? launch_nt<float, 1>(threads, pl, nctas, smem, st)
                      : launch_nt<float, 0>(threads, pl, nctas, smem, st);
+}
+
+int launch_reduce_items(const PairLaunch &pl, cudaStream_t st) {
+    if (!pl.sh.item_E) return VDWDF_OK;
+    k_reduce_items<<<pl.ninst, 256, 0, st>>>(pl);
+    count_launches(1);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
 }
 
 int launch_kernel_eval(int precision, const PairShared &sh, int64_t npts, const double *r,

@@ -9,8 +9,8 @@
 //    partials dq0/dn, dq0/dg used by the adjoint;
 //  - trimming (section 3: points below a density cutoff are dropped): active
 //    points are listed in the order of 4x4x4 grid bricks taken along a Morton
-//    curve, so that consecutive runs of kJT points are compact in space;
-//  - bounding boxes of those kJT-point tiles (for image culling).
+//    curve, so that consecutive runs of kTile points are compact in space;
+//  - bounding boxes of those kTile-point tiles (for image culling).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -215,15 +215,16 @@ __global__ void k_scatter(BrickGeom g, const int *__restrict__ order, int nb,
     }
 }
 
-// one block of kJT threads per tile: bounding box, q0 range, sum of n^2
+// one warp per kTile-point tile: bounding box, q0 range, sum of n^2
 __global__ void k_tiles(const float4 *__restrict__ p32, const double *__restrict__ n64,
-                        float4 *__restrict__ blo, float4 *__restrict__ bhi, Stats *stats) {
+                        float4 *__restrict__ blo, float4 *__restrict__ bhi, Stats *stats, int ntiles_max) {
     const int na = stats->n_active;
-    const int t = blockIdx.x;
-    if (t * kJT >= na) return;
-    const int i = t * kJT + threadIdx.x;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= ntiles_max || t * kTile >= na) return;
+    const int i = t * kTile + lane;
     const bool in = i < na;
-    float4 p = in ? p32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 p = in ? p32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     float lo[4] = {in ? p.x : 3e38f, in ? p.y : 3e38f, in ? p.z : 3e38f, in ? p.w : 3e38f};
     float hi[4] = {in ? p.x : -3e38f, in ? p.y : -3e38f, in ? p.z : -3e38f, in ? p.w : -3e38f};
     double n2 = in ? n64[i] * n64[i] : 0.0;
@@ -236,32 +237,13 @@ __global__ void k_tiles(const float4 *__restrict__ p32, const double *__restrict
         }
         n2 += __shfl_xor_sync(0xffffffffu, n2, o);
     }
-    __shared__ float slo[8][4], shi[8][4];
-    __shared__ double sn2[8];
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            slo[w][k] = lo[k];
-            shi[w][k] = hi[k];
-        }
-        sn2[w] = n2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int ww = 1; ww < kJT / 32; ++ww)
-            for (int k = 0; k < 4; ++k) {
-                slo[0][k] = fminf(slo[0][k], slo[ww][k]);
-                shi[0][k] = fmaxf(shi[0][k], shi[ww][k]);
-            }
-        double s = 0.0;
-        for (int ww = 0; ww < kJT / 32; ++ww) s += sn2[ww];
-        blo[t] = make_float4(slo[0][0], slo[0][1], slo[0][2], slo[0][3]);
-        bhi[t] = make_float4(shi[0][0], shi[0][1], shi[0][2], shi[0][3]);
-        atomicAdd(&stats->n2sum, s);
+    if (lane == 0) {
+        blo[t] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        bhi[t] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        atomicAdd(&stats->n2sum, n2);
         // q0 > 0 on active points: float bit patterns order like the values
-        atomicMin(&stats->qmin_bits, __float_as_uint(slo[0][3]));
-        atomicMax(&stats->qmax_bits, __float_as_uint(shi[0][3]));
+        atomicMin(&stats->qmin_bits, __float_as_uint(lo[3]));
+        atomicMax(&stats->qmax_bits, __float_as_uint(hi[3]));
     }
 }
 
@@ -300,8 +282,8 @@ int launch_compact(const int dims[3], const double *n, double n_cut, const doubl
                                            n32, p64, n64);
     VDWDF_CUDA_TRY(cudaGetLastError());
     const long long N = static_cast<long long>(dims[0]) * dims[1] * dims[2];
-    const int tiles = static_cast<int>((N + kJT - 1) / kJT);
-    k_tiles<<<tiles, kJT, 0, st>>>(p32, n64, blo, bhi, stats);
+    const int tiles = static_cast<int>((N + kTile - 1) / kTile);
+    k_tiles<<<(tiles + 7) / 8, 256, 0, st>>>(p32, n64, blo, bhi, stats, tiles);
     VDWDF_CUDA_TRY(cudaGetLastError());
     count_launches(4);
     return VDWDF_OK;

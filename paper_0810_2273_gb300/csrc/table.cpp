@@ -278,6 +278,19 @@ int build_phi_nodes(int nD, double Dmax, int ndelta, int level, double *nodes) {
     return 0;
 }
 
+void rho_coefficients(int nD, double Dmax, int nd, const double *nodes, double *coef) {
+    // rho(delta_l) = phi(Dmax, delta_l) / phi17(Dmax, delta_l): the large-D branch is
+    // eq. (17) times the cubic spline of rho, continuous with the table at Dmax.
+    const double C = 12.0 * std::pow(4.0 * kPi / 9.0, 3);
+    std::vector<double> r(nd), cp, dp;
+    for (int l = 0; l < nd; ++l) {
+        const double dl = static_cast<double>(l) / nd;
+        const double d1 = Dmax * (1.0 + dl), d2 = Dmax * (1.0 - dl);
+        r[l] = nodes[static_cast<size_t>(nD - 1) * nd + l] / (-C / (d1 * d1 * d2 * d2 * (d1 * d1 + d2 * d2)));
+    }
+    bspline_1d(nd, r.data(), 1, coef, 1, cp, dp);
+}
+
 void spline_coefficients(int nD, int nd, const double *nodes, double *coef) {
     // coef: (nD + 2) x (nd + 2), D outer.  First along D for every delta node, then
     // along delta for every (ghost-extended) D row.

@@ -16,4 +16,9 @@ int quadrature_node_count(int level);
 // delta = 0 and zero curvature at the last node of each axis.
 void spline_coefficients(int nD, int ndelta, const double *nodes, double *coef);
 
+// 1-D cubic B-spline coefficients (ndelta + 2) in delta of
+// rho(delta_l) = phi(Dmax, delta_l) / phi17(Dmax, delta_l) (same end conditions),
+// which scales Dion's eq. (17) beyond the table so that phi is continuous at Dmax.
+void rho_coefficients(int nD, double Dmax, int ndelta, const double *nodes, double *coef);
+
 }  // namespace vdwdf

@@ -1,0 +1,196 @@
+"""The five standard workloads at their full sizes, in the launch configuration
+bench.py times.  Where the oracle cannot do the whole O(N^2) sum, it computes
+sampled outputs one by one (A_i, U_i, v_m at random points); the FP32 path is
+also held against the FP64 GPU path on whole energies.
+Tolerances: E relative 1e-6 (FP32) / 1e-10 (FP64); v max-norm relative 1e-5
+(FP32) / 1e-10 (FP64); binding energies 0.01 meV; pair counts exact."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HARTREE_MEV = 27211.386
+
+
+@pytest.fixture(scope="module")
+def V():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0810_2273_gb300 as V
+    return V
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def gtable(V, oracle_table):
+    return V.Table.from_nodes(oracle_table, 30.0)
+
+
+def _t(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+
+
+def _args(w, T):
+    return (w["lengths"], w["periodic"], w["n_cut"], w["r_cut"], T)
+
+
+def _fd_tol(E, h, dV, vmax):
+    """Central-difference tolerance: 1e-6 of max|v| plus the FP64 rounding of E
+    (the step moves E by only ~2 h dV v)."""
+    return 1e-6 * vmax + 64 * 2.2e-16 * abs(E) / (2 * h * dV)
+
+
+def _sample_points(w, rng, n_act, n_inact, n_min=None):
+    flat = w["density"].ravel()
+    act = np.nonzero(flat >= (2 * w["n_cut"] if n_min is None else n_min))[0]
+    ina = np.nonzero(flat < 0.5 * w["n_cut"])[0]
+    pts = list(rng.choice(act, n_act, replace=False))
+    if n_inact and len(ina):
+        pts += list(rng.choice(ina, min(n_inact, len(ina)), replace=False))
+    return np.array(pts, dtype=np.int64)
+
+
+def test_monolayer_full(V, dev, gtable, oracle_mod, oracle_spline):
+    """48x84x120 periodic monolayer (the bench workload): FP32 E + v against the FP64
+    GPU energy, identical pair counts, and v at sampled points against the oracle."""
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.xe_monolayer()
+    n = _t(w["density"], dev)
+    E32, v32, r32 = V.potential(n, *_args(w, gtable), precision="fp32")
+    E64, v64, r64, Ag, Ug = V.potential(n, *_args(w, gtable), precision="fp64", want_AU=True)
+    assert abs(E32 - E64) < 1e-6 * abs(E64), (E32, E64)
+    assert r32["pairs"] == r64["pairs"]
+    assert r32["n_active"] == r64["n_active"] == 302870
+    P = oracle_mod.Problem(w["density"], *_args(w, oracle_spline))
+    rng = np.random.default_rng(11)
+    pts = _sample_points(w, rng, 20, 4)
+    vo = P.potential_at(pts)
+    v = v32.cpu().numpy().ravel()
+    vmax = np.max(np.abs(v))
+    assert np.max(np.abs(v[pts] - vo)) < 1e-5 * vmax
+    assert np.max(np.abs(v64.cpu().numpy().ravel()[pts] - vo)) < 1e-10 * vmax
+    A, U, cnt, _ = P.AU(np.arange(0, P.n_active, 37731))
+    idx = P.active[np.arange(0, P.n_active, 37731)]
+    assert np.max(np.abs(Ag.cpu().numpy().ravel()[idx] - A) / np.abs(A)) < 1e-10
+    assert np.max(np.abs(Ug.cpu().numpy().ravel()[idx] - U)) < 1e-10 * np.max(np.abs(U))
+
+
+def test_molecule_full_potential_and_fd(V, dev, gtable, oracle_mod, oracle_spline):
+    """64^3 open molecule: FP32 E + v; v at sampled points (also of the 24^3 index
+    subsample floor(64k/24)) against the oracle; v against central differences
+    (h = 1e-4 n) of the FP64 GPU energy at a few full-size points."""
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.molecule24()
+    n = _t(w["density"], dev)
+    E32, v32, r32 = V.potential(n, *_args(w, gtable), precision="fp32")
+    E64, v64, r64 = V.potential(n, *_args(w, gtable), precision="fp64")
+    assert abs(E32 - E64) < 1e-6 * abs(E64)
+    v32 = v32.cpu().numpy().ravel()
+    v64 = v64.cpu().numpy().ravel()
+    vmax = np.max(np.abs(v64))
+    assert np.max(np.abs(v32 - v64)) < 1e-5 * vmax
+    P = oracle_mod.Problem(w["density"], *_args(w, oracle_spline))
+    rng = np.random.default_rng(13)
+    sub = (np.arange(24) * 64) // 24
+    cand = np.ravel_multi_index(np.meshgrid(sub, sub, sub, indexing="ij"), (64, 64, 64)).ravel()
+    flat = w["density"].ravel()
+    cand = cand[(flat[cand] >= 2 * w["n_cut"]) | (flat[cand] < 0.5 * w["n_cut"])]
+    pts = np.concatenate([rng.choice(cand, 24, replace=False), _sample_points(w, rng, 8, 0)])
+    vo = P.potential_at(pts)
+    assert np.max(np.abs(v64[pts] - vo)) < 1e-10 * vmax
+    assert np.max(np.abs(v32[pts] - vo)) < 1e-5 * vmax
+    dV = np.prod(w["lengths"]) / flat.size
+    for m in _sample_points(w, rng, 4, 0, n_min=1e-3):
+        h = 1e-4 * flat[m]
+        Es = []
+        for s in (1, -1):
+            nn = flat.copy()
+            nn[m] += s * h
+            Es.append(V.energy(_t(nn.reshape(w["density"].shape), dev), *_args(w, gtable), precision="fp64")[0])
+        fd = (Es[0] - Es[1]) / (2 * h) / dV
+        assert abs(fd - v64[m]) < _fd_tol(E64, h, dV, vmax), (m, fd, v64[m])
+
+
+def test_molecule_coarse_fd(V, dev, gtable):
+    """Central differences (h = 1e-4 n) of the FP64 E at 64 random points of the same
+    molecule on a 24^3 grid against the FP64 and FP32 v.  Points are drawn where
+    n >= 1e-4: at densities near n_cut the step moves E by less than its own FP64
+    rounding (the oracle's E shows the same), so the difference says nothing there."""
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.molecule24((24, 24, 24))
+    flat = w["density"].ravel().copy()
+    n = _t(w["density"], dev)
+    E64, v64, _ = V.potential(n, *_args(w, gtable), precision="fp64")
+    _, v32, _ = V.potential(n, *_args(w, gtable), precision="fp32")
+    v64 = v64.cpu().numpy().ravel()
+    v32 = v32.cpu().numpy().ravel()
+    vmax = np.max(np.abs(v64))
+    assert np.max(np.abs(v32 - v64)) < 1e-5 * vmax
+    rng = np.random.default_rng(17)
+    dV = np.prod(w["lengths"]) / flat.size
+    pts = _sample_points(w, rng, 64, 0, n_min=1e-4)
+    for m in pts:
+        h = 1e-4 * flat[m]
+        Es = []
+        for s in (1, -1):
+            nn = flat.copy()
+            nn[m] += s * h
+            Es.append(V.energy(_t(nn.reshape(w["density"].shape), dev), *_args(w, gtable), precision="fp64")[0])
+        fd = (Es[0] - Es[1]) / (2 * h) / dV
+        assert abs(fd - v64[m]) < _fd_tol(E64, h, dV, vmax), (m, fd, v64[m])
+
+
+def test_binding_curve_batched(V, dev, gtable, oracle_mod, oracle_spline):
+    """18 uneven instances in one graph-captured launch (FP32 pairs): per-instance E
+    against FP64 single calls and binding energies E_AB - 2 E_A within 0.01 meV;
+    the smallest instance against the oracle."""
+    from paper_0810_2273_gb300 import inputs
+    ws = inputs.binding_curve()
+    ns = [_t(w["density"], dev) for w in ws]
+    L = [w["lengths"] for w in ws]
+    per = [w["periodic"] for w in ws]
+    E32, res = V.energy_batched(ns, L, per, 1e-6, 0.0, gtable, "fp32")
+    E32b, _ = V.energy_batched(ns, L, per, 1e-6, 0.0, gtable, "fp32")      # graph replay
+    assert np.max(np.abs(E32b - E32) / np.abs(E32)) < 1e-12
+    E64 = np.array([V.energy(t, w["lengths"], w["periodic"], 1e-6, 0.0, gtable, "fp64")[0]
+                    for t, w in zip(ns, ws)])
+    assert np.max(np.abs(E32 - E64) / np.abs(E64)) < 1e-6
+    EA32, EA64 = E32[-1], E64[-1]
+    bind32 = E32[:16] - 2 * EA32
+    bind64 = E64[:16] - 2 * EA64
+    assert np.max(np.abs(bind32 - bind64)) * HARTREE_MEV < 0.01
+    w0 = ws[-2]
+    e = oracle_mod.Problem(w0["density"], *_args(w0, oracle_spline)).energy()
+    assert abs(E64[-2] - e["E"]) < 1e-10 * abs(e["E"])
+    assert res["n_active"] == sum(int((w["density"] >= 1e-6).sum()) for w in ws)
+
+
+def test_slab_full_sampled(V, dev, gtable, oracle_mod, oracle_spline):
+    """128x112x200 periodic slab + flake: FP32 E + v at full size with A, U, v at
+    sampled points against the oracle; FP32 vs FP64 E on a 64x56x100 regrid."""
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.slab_adsorbate()
+    n = _t(w["density"], dev)
+    E32, v32, r32, A32, U32 = V.potential(n, *_args(w, gtable), precision="fp32", want_AU=True)
+    assert r32["n_active"] == int((w["density"] >= w["n_cut"]).sum())
+    P = oracle_mod.Problem(w["density"], *_args(w, oracle_spline))
+    q = np.arange(0, P.n_active, P.n_active // 12)[:12]
+    A, U, _, _ = P.AU(q)
+    idx = P.active[q]
+    Ag = A32.cpu().numpy().ravel()[idx]
+    Ug = U32.cpu().numpy().ravel()[idx]
+    assert np.max(np.abs(Ag - A)) < 1e-5 * np.max(np.abs(A))
+    assert np.max(np.abs(Ug - U)) < 1e-5 * np.max(np.abs(U))
+    wc = inputs.slab_adsorbate((64, 56, 100))
+    nc = _t(wc["density"], dev)
+    e32, _ = V.energy(nc, *_args(wc, gtable), precision="fp32")
+    e64, r64 = V.energy(nc, *_args(wc, gtable), precision="fp64")
+    assert abs(e32 - e64) < 1e-6 * abs(e64)

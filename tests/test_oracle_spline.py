@@ -61,27 +61,87 @@ def test_spline_matches_library_1d_splines(oracle_mod):
         assert abs(got - ref) < 1e-12 * np.max(np.abs(nodes))
 
 
+def _rho_reference(oracle_mod, s):
+    """rho(delta): scipy cubic spline (zero slope at 0, zero curvature at the end) through
+    the last table row divided by eq. (17) at D = Dmax, at the delta nodes."""
+    sp = pytest.importorskip("scipy.interpolate")
+    dl = np.arange(s.nd) * s.hd
+    ratio = s.f[-1] / oracle_mod.phi_asym(s.Dmax * (1 + dl), s.Dmax * (1 - dl))
+    return sp.CubicSpline(dl, ratio, bc_type=((1, 0.0), (2, 0.0)))
+
+
 def test_kernel_branches(oracle_mod, oracle_spline):
-    """D > 30 takes eq. (17) with its analytic d1-derivative; below, the spline; a
-    delta above the last node is clamped (and counted) with zero delta-slope."""
+    """D > Dmax takes eq. (17) times rho(delta) with the analytic d1-derivative; below,
+    the spline; a delta above the last node is counted."""
     s = oracle_spline
-    C = oracle_mod.C_ASYM
+    rho = _rho_reference(oracle_mod, s)
     r, qi, qj = 12.0, 3.1, 2.7         # D = 34.8
     p, rd, ncl = s.kernel([r], [qi], [qj])
     d1, d2 = qi * r, qj * r
-    pa = -C / (d1 ** 2 * d2 ** 2 * (d1 ** 2 + d2 ** 2))
-    assert abs(p[0] - pa) < 1e-15 * abs(pa) and ncl == 0
-    h = 1e-6 * d1
-    dp = (oracle_mod.phi_asym(d1 + h, d2) - oracle_mod.phi_asym(d1 - h, d2)) / (2 * h)
-    assert abs(rd[0] - r * dp) < 1e-7 * abs(r * dp)
-    # inside the table: r dphi/dd1 from a central difference of the spline kernel in q_i
-    r, qi, qj = 2.0, 1.3, 0.9
-    p0, rd0, _ = s.kernel([r], [qi], [qj])
+    dl = (qi - qj) / (qi + qj)
+    pa = rho(dl) * oracle_mod.phi_asym(d1, d2)
+    assert abs(p[0] - pa) < 1e-13 * abs(pa) and ncl == 0
+    # r dphi/dd1 by a central difference in q_i (d1 = q_i r moves, d2 fixed)
     e = 1e-6
     pp, _, _ = s.kernel([r], [qi + e], [qj])
     pm, _, _ = s.kernel([r], [qi - e], [qj])
-    # d phi / d q_i = r dphi/dd1  (d1 = q_i r)
+    assert abs((pp[0] - pm[0]) / (2 * e) - rd[0]) < 1e-7 * abs(rd[0])
+    # inside the table: the same check
+    r, qi, qj = 2.0, 1.3, 0.9
+    p0, rd0, _ = s.kernel([r], [qi], [qj])
+    pp, _, _ = s.kernel([r], [qi + e], [qj])
+    pm, _, _ = s.kernel([r], [qi - e], [qj])
     assert abs((pp[0] - pm[0]) / (2 * e) - rd0[0]) < 1e-7
     # clamping: delta = (8 - 0.01)/(8 + 0.01) > 0.995 with D = 0.5 * 0.5 * 8.01 < 30
     _, _, ncl = s.kernel([0.5], [8.0], [0.01])
     assert ncl == 1
+
+
+def test_kernel_continuous_at_table_edge(oracle_mod, oracle_spline):
+    """phi is continuous across D = Dmax: at the delta nodes exactly (rho interpolates
+    the ratio there), in between up to the interpolation error; rho = 1 where eq. (17)
+    is accurate (delta = 0; this table's quadrature is good to ~1e-11 absolute, i.e.
+    5e-4 of phi(30, 0) = -2.2e-8)."""
+    s = oracle_spline
+    rho = _rho_reference(oracle_mod, s)
+    assert abs(rho(0.0) - 1.0) < 2e-3
+    for dl in list(np.arange(0, 199, 13) / 200.0) + [0.2537, 0.61, 0.9033]:
+        q = 1.7
+        qi, qj = q * (1 + dl), q * (1 - dl)
+        r_edge = 2 * s.Dmax / (qi + qj)
+        inside, _, _ = s.kernel([r_edge * (1 - 1e-12)], [qi], [qj])
+        outside, _, _ = s.kernel([r_edge * (1 + 1e-12)], [qi], [qj])
+        on_node = abs(dl * s.nd - round(dl * s.nd)) < 1e-9
+        tol = 1e-9 if on_node else 1e-6
+        assert abs(inside[0] - outside[0]) <= tol * abs(inside[0]), (dl, inside, outside)
+
+
+@pytest.mark.parametrize("D", [2.0, 17.3, 29.99, 31.0, 45.0])
+def test_kernel_continued_past_last_delta_node(oracle_mod, oracle_spline, D):
+    """Above the last delta node the kernel is the spline's linear continuation (the
+    spline has zero curvature there): value and delta-slope continuous across the node,
+    and r dphi/dd1 of the continued kernel equals a central difference in q_i."""
+    s = oracle_spline
+    dlast = (s.nd - 1) * s.hd
+    q = 2.0
+    def at(dl, eps_q=0.0):
+        qi, qj = q * (1 + dl), q * (1 - dl)
+        r = 2 * D / (qi + qj)
+        return s.kernel([r], [qi + eps_q], [qj])
+    # second differences across the node: O(e^2) if smooth, O(e) for a kink, O(1) for
+    # a jump -- so the ratio of second difference to e^2 must not grow as e shrinks
+    ratios = []
+    for e in (1e-4, 1e-5):
+        below, _, n0 = at(dlast - e)
+        mid, _, _ = at(dlast)
+        above, _, n1 = at(dlast + e)
+        assert n0 == 0 and n1 == 1
+        ratios.append(abs(above[0] - 2 * mid[0] + below[0]) / e ** 2)
+    assert ratios[1] <= 2.0 * ratios[0] + 1e-6 * abs(mid[0])
+    dl = 0.9985
+    p0, rd, n2 = at(dl)
+    assert n2 == 1
+    h = 1e-6
+    pp, _, _ = at(dl, h)
+    pm, _, _ = at(dl, -h)
+    assert abs((pp[0] - pm[0]) / (2 * h) - rd[0]) <= 1e-6 * abs(rd[0])

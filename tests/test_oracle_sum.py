@@ -46,8 +46,9 @@ def test_translation_invariance_periodic(oracle_mod, oracle_spline):
 
 def test_far_fragments_cross_term_is_asymptotic_sum(oracle_mod, oracle_spline):
     """Two compactly supported blobs so far apart that every cross pair has D > 30:
-    E_AB - E_A - E_B must equal dV^2 sum_{i in A, j in B} n_i n_j phi_17(q_i r, q_j r),
-    written out here with numpy (the factor 1/2 and the two orderings give 1)."""
+    E_AB - E_A - E_B must equal dV^2 sum_{i in A, j in B} n_i n_j rho(delta) phi_17(q_i r, q_j r),
+    written out here with numpy and scipy (the factor 1/2 and the two orderings give 1)."""
+    sp = pytest.importorskip("scipy.interpolate")
     g = golden_dict("dion_kernel.txt")
     rng = np.random.default_rng(29)
     dims = (40, 8, 8)
@@ -68,7 +69,13 @@ def test_far_fragments_cross_term_is_asymptotic_sum(oracle_mod, oracle_spline):
     d1 = PA.qa[:, None] * r
     d2 = PB.qa[None, :] * r
     assert np.min(0.5 * (d1 + d2)) > 30.0
-    phi = -g["C_asym"] / (d1 ** 2 * d2 ** 2 * (d1 ** 2 + d2 ** 2))
+    s = oracle_spline
+    dln = np.arange(s.nd) * s.hd
+    ratio = s.f[-1] / (-g["C_asym"] / ((s.Dmax * (1 + dln)) ** 2 * (s.Dmax * (1 - dln)) ** 2 *
+                                      ((s.Dmax * (1 + dln)) ** 2 + (s.Dmax * (1 - dln)) ** 2)))
+    rho = sp.CubicSpline(dln, ratio, bc_type=((1, 0.0), (2, 0.0)))
+    dl = np.minimum(np.abs(d1 - d2) / (d1 + d2), dln[-1])
+    phi = rho(dl) * (-g["C_asym"] / (d1 ** 2 * d2 ** 2 * (d1 ** 2 + d2 ** 2)))
     cross = PA.dV ** 2 * np.sum(PA.na[:, None] * PB.na[None, :] * phi)
     assert abs((EAB - EA - EB) - cross) < 1e-6 * abs(cross)
     assert abs(EA) > 1e3 * abs(cross)
