@@ -316,7 +316,7 @@ int smem_budget() {
 
 int smem_rows_available(int threads, int S) {
     const int base = pair_smem_bytes(VDWDF_FP32, threads, 0, S);
-    return std::max(0, (smem_budget() - base) / (S * static_cast<int>(sizeof(float))));
+    return std::max(0, (smem_budget() - base) / (band_stride(S) * static_cast<int>(sizeof(float))));
 }
 
 int ctas_per_sm(int precision, bool pot, int threads, int ksn, int S) {
@@ -352,7 +352,8 @@ Launch choose_launch(int precision, bool pot, const vdwdf_tuning *tu, const vdwd
                      long long n_active) {
     Launch ln;
     const int S = t->nd + 2;
-    if (tu && (tu->threads == 256 || tu->threads == 512 || tu->threads == 1024)) ln.threads = tu->threads;
+    if (tu && (tu->threads == 256 || tu->threads == 384 || tu->threads == 512 || tu->threads == 1024))
+        ln.threads = tu->threads;
     const int sms = sm_count();
     ln.nctas = sms * ctas_per_sm(precision, pot, ln.threads, 0, S);
     // work items are (tile of kTile i points) x (jt j tiles); aim at ipsm items per
@@ -921,12 +922,13 @@ int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, do
     if (rc == VDWDF_OK && cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = VDWDF_ECUDA;
     if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
-    vdwdf_tuning cand[6] = {{256, 24, 0, 0}, {512, 24, 0, 0}, {1024, 24, 0, 0},
-                            {512, 8, 0, 0},  {512, 64, 0, 0}, {512, 24, -1, 0}};
+    constexpr int kCand = 7;
+    vdwdf_tuning cand[kCand] = {{256, 24, 0, 0}, {384, 24, 0, 0}, {512, 24, 0, 0}, {1024, 24, 0, 0},
+                                {512, 8, 0, 0},  {512, 64, 0, 0}, {512, 24, -1, 0}};
     double best_rate = -1.0;
     vdwdf_tuning choice = {512, 24, 0, 0};
     Timer tm;
-    for (int ci = 0; ci < 6 && rc == VDWDF_OK && hs.n_active > 0; ++ci) {
+    for (int ci = 0; ci < kCand && rc == VDWDF_OK && hs.n_active > 0; ++ci) {
         if (fp64 && cand[ci].smem_rows != 0) continue;
         Launch ln = choose_launch(precision, false, &cand[ci], table, hs.n_active);
         for (int rep = 0; rep < 2 && rc == VDWDF_OK; ++rep) {

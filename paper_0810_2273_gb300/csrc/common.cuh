@@ -89,6 +89,9 @@ int launch_compact(const int dims[3], const double *n, double n_cut, const doubl
                    Stats *stats, cudaStream_t st);
 int launch_pair(int precision, bool potential, int threads, const PairLaunch &pl, int nctas,
                 cudaStream_t st);
+// Row stride of the shared-memory table band: odd, so that one column of
+// consecutive rows falls in distinct banks.
+__host__ __device__ inline int band_stride(int S) { return S | 1; }
 int pair_smem_bytes(int precision, int threads, int ksn, int S);
 // Sum the energy-mode item partials of every instance in a fixed order into its
 // Stats::E_pair (one block per instance).

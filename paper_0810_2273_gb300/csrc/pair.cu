@@ -19,9 +19,10 @@
 // shared memory (FP32 path, staged once).  Each warp then works on its own:
 // it pulls work items (instance, tile of kTile i points, range of j tiles) from
 // one queue in global memory, culls every (j tile, image) against its i tile
-// by bounding boxes, stages surviving j tiles in a private shared-memory
-// buffer (warp-synchronous, no block barrier), and runs the pair loop with
-// each lane owning one i and the j points read as broadcasts.  FP32 partial
+// by bounding boxes and then every (j point, image) against the i box, stages
+// surviving j tiles in a private shared-memory buffer (warp-synchronous, no
+// block barrier), and runs the pair loop with each lane owning one i, the j
+// points read as broadcasts and the images of a pair innermost.  FP32 partial
 // sums over one j tile are folded into FP64 accumulators.  The work loop is
 // bounded (max_iters); nothing waits on another warp or CTA.
 #include <cuda_runtime.h>
@@ -101,6 +102,49 @@ __device__ __forceinline__ float lds32(uint32_t a) {
     return v;
 }
 
+// Two FP32 values per instruction (sm_100-family packed FP32 arithmetic).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 add2_rm(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rm.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)),
+          "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+    return *reinterpret_cast<const float2 *>(&d);
+}
+
+// floor_split of two values at once (both non-negative and below 2^22)
+__device__ __forceinline__ float2 floor_split2(float2 x, int &k0, int &k1) {
+    const float2 b = add2_rm(x, f2(12582912.0f));
+    k0 = __float_as_int(b.x) - 0x4B400000;
+    k1 = __float_as_int(b.y) - 0x4B400000;
+    const float2 f = fma2(f2(-1.0f), f2(12582912.0f), b);  // floor(x), exact
+    return fma2(f, f2(-1.0f), x);                            // x - floor(x), exact
+}
+
+__device__ __forceinline__ void bw2(float2 t, float2 w[4]) {
+    const float2 t2 = mul2(t, t), t3 = mul2(t2, t), s = fma2(t, f2(-1.0f), f2(1.0f));
+    w[0] = mul2(mul2(s, s), s);
+    w[1] = fma2(f2(3.0f), t3, fma2(f2(-6.0f), t2, f2(4.0f)));
+    w[2] = fma2(f2(-3.0f), t3, fma2(f2(3.0f), t2, fma2(f2(3.0f), t, f2(1.0f))));
+    w[3] = t3;
+}
+__device__ __forceinline__ void bdw2(float2 t, float2 d[4]) {
+    const float2 t2 = mul2(t, t), s = fma2(t, f2(-1.0f), f2(1.0f));
+    d[0] = mul2(f2(-3.0f), mul2(s, s));
+    d[1] = fma2(f2(9.0f), t2, mul2(f2(-12.0f), t));
+    d[2] = fma2(f2(-9.0f), t2, fma2(f2(6.0f), t, f2(3.0f)));
+    d[3] = mul2(f2(3.0f), t2);
+}
+
+// The delta-derivative weights sum to zero, so sum_n dwd[n] c[n] is taken as
+// sum_{n>=1} dwd[n] (c[n] - c[0]): neighbouring coefficients differ little and
+// their differences are exact, which keeps the small derivative of an O(phi)
+// row free of the cancellation that would otherwise scale its error by the
+// number of delta cells.
 template <bool POT, typename R>
 __device__ __forceinline__ void combine(const R c[4][4], const R wD[4], const R dwD[4],
                                         const R wd[4], const R dwd[4], R &phi, R &pt, R &pu) {
@@ -110,7 +154,8 @@ __device__ __forceinline__ void combine(const R c[4][4], const R wD[4], const R 
         const R row = wd[0] * c[m][0] + wd[1] * c[m][1] + wd[2] * c[m][2] + wd[3] * c[m][3];
         p += wD[m] * row;
         if (POT) {
-            const R drow = dwd[0] * c[m][0] + dwd[1] * c[m][1] + dwd[2] * c[m][2] + dwd[3] * c[m][3];
+            const R drow = dwd[1] * (c[m][1] - c[m][0]) + dwd[2] * (c[m][2] - c[m][0]) +
+                           dwd[3] * (c[m][3] - c[m][0]);
             a += dwD[m] * row;
             b += wD[m] * drow;
         }
@@ -130,9 +175,9 @@ template <typename R>
 struct Table {
     const R *g;      // bicubic coefficients / 36 in global memory, row stride S
     const R *rho;    // rho(delta) coefficients / 6 (after the bicubic block)
-    uint32_t s;      // shared-memory address of the resident band (FP32), same stride
+    uint32_t s;      // shared-memory address of the resident band (FP32), row stride SB
     int k0, kn;      // band rows [k0, k0 + kn)
-    int S;
+    int S, SB;
 };
 
 template <bool POT, typename R>
@@ -141,8 +186,8 @@ __device__ __forceinline__ void interp(const Table<R> &tb, int k, int l, const R
                                        R &pu) {
     R c[4][4];
     if (sizeof(R) == 4 && k >= tb.k0 && k + 4 <= tb.k0 + tb.kn) {
-        const uint32_t a0 = tb.s + 4u * static_cast<uint32_t>((k - tb.k0) * tb.S + l);
-        const uint32_t rs = 4u * static_cast<uint32_t>(tb.S);
+        const uint32_t a0 = tb.s + 4u * static_cast<uint32_t>((k - tb.k0) * tb.SB + l);
+        const uint32_t rs = 4u * static_cast<uint32_t>(tb.SB);
 #pragma unroll
         for (int m = 0; m < 4; ++m)
 #pragma unroll
@@ -157,40 +202,54 @@ __device__ __forceinline__ void interp(const Table<R> &tb, int k, int l, const R
     combine<POT, R>(c, wD, dwD, wd, dwd, p, pt, pu);
 }
 
-// One pair: phi and (POT) r dphi/dd1, r dphi/dd2; counts a clamped delta.
+// The delta-dependent part of a pair, shared by all its periodic images: the
+// delta cell and weights, and the signs of d(delta)/dd1, d(delta)/dd2.
 // With ds = (q_i - q_j)/(q_i + q_j): dds/dd1 = (1 - ds)/(2D), dds/dd2 = -(1 + ds)/(2D).
+template <typename R>
+struct Delta {
+    R sq, isq, sgn1, sgn2;
+    R wd[4], dwd[4];
+    int l;
+    bool cl;  // delta beyond the last node (weights continued linearly)
+};
+
 template <bool POT, typename R>
-__device__ __forceinline__ void pair_phi(R r2, R qi, R qj, R inv_qi, R qi2, const Consts<R> &K,
-                                         const Table<R> &tb, R &phi, R &rd, R &rd2, unsigned &ncl) {
-    const R r = rlen(r2);
-    const R sq = qi + qj;
+__device__ __forceinline__ void delta_part(R qi, R qj, const Consts<R> &K, Delta<R> &d) {
+    d.sq = qi + qj;
     const R dq = qi - qj;
-    const R isq = recip(sq);
-    // delta cell; beyond the last node the spline continues linearly with its end
-    // slope (it has zero curvature there): the weights become w(u) + e w'(u), e the
-    // distance past the node in cells.  No index leaves the table.
-    const R dl = fabs(dq) * isq;
+    d.isq = recip(d.sq);
+    // beyond the last node the spline continues linearly with its end slope (it has
+    // zero curvature there): the weights become w(u) + e w'(u), e the distance past
+    // the node in cells.  No index leaves the table.
+    const R dl = fabs(dq) * d.isq;
     const R td0 = dl * K.cd;
-    const bool cl = td0 > K.tdmax;
-    ncl += cl ? 1u : 0u;
-    R td = fmin(fmax(td0, R(0)), K.tdclamp);
+    d.cl = td0 > K.tdmax;
+    const R td = fmin(fmax(td0, R(0)), K.tdclamp);
     R u;
     int l = floor_split(td, u);
     if (sizeof(R) == 8 && l > K.lmax) {  // FP64 keeps the exact end node: last cell at u = 1
         l = K.lmax;
         u = td - R(l);
     }
-    R wd[4], dwd[4];
-    bw<R>(u, wd);
-    if (POT || cl) bdw<R>(u, dwd);
-    if (cl) {
+    d.l = l;
+    bw<R>(u, d.wd);
+    if (POT || d.cl) bdw<R>(u, d.dwd);
+    if (d.cl) {
         const R e = td0 - td;
 #pragma unroll
-        for (int n = 0; n < 4; ++n) wd[n] += e * dwd[n];
+        for (int n = 0; n < 4; ++n) d.wd[n] += e * d.dwd[n];
     }
-    const R sgn1 = dq > R(0) ? (R(1) - dl) : -(R(1) + dl);   // sign(ds) (1 - ds)
-    const R sgn2 = dq > R(0) ? (R(1) + dl) : -(R(1) - dl);   // sign(ds) (1 + ds)
-    R tD = r * sq * K.cD;
+    d.sgn1 = dq > R(0) ? (R(1) - dl) : -(R(1) + dl);  // sign(ds) (1 - ds)
+    d.sgn2 = dq > R(0) ? (R(1) + dl) : -(R(1) - dl);  // sign(ds) (1 + ds)
+}
+
+// The distance-dependent part: phi and (POT) r dphi/dd1, r dphi/dd2 at r^2.
+template <bool POT, typename R>
+__device__ __forceinline__ void dist_part(R r2, R qi, R qj, R inv_qi, R qi2, const Delta<R> &d,
+                                          const Consts<R> &K, const Table<R> &tb, R &phi, R &rd,
+                                          R &rd2) {
+    const R r = rlen(r2);
+    R tD = r * d.sq * K.cD;
     // the table is read only for 0 <= tD <= nD - 1 (false for NaN as well)
     if (tD >= R(0) && tD <= K.tDmax) {
         tD = fmin(tD, K.tDclamp);
@@ -204,29 +263,39 @@ __device__ __forceinline__ void pair_phi(R r2, R qi, R qj, R inv_qi, R qi2, cons
         bw<R>(t, wD);
         if (POT) bdw<R>(t, dwD);
         R pt = 0, pu = 0;
-        interp<POT, R>(tb, k, l, wD, dwD, wd, dwd, phi, pt, pu);
+        interp<POT, R>(tb, k, d.l, wD, dwD, d.wd, d.dwd, phi, pt, pu);
         if (POT) {
-            const R a = r * K.cD * pt, b = isq * K.cd * pu;
-            rd = a + b * sgn1;
-            rd2 = a - b * sgn2;
+            const R a = r * K.cD * pt, b = d.isq * K.cd * pu;
+            rd = a + b * d.sgn1;
+            rd2 = a - b * d.sgn2;
         }
     } else {
         const R r4 = r2 * r2;
         const R qj2 = qj * qj;
         const R s2 = qi2 + qj2;
         const R p17 = -K.C * recip(r4 * r2 * qi2 * qj2 * s2);
-        const R *rc = tb.rho + l;
+        const R *rc = tb.rho + d.l;
         const R c0 = __ldg(rc), c1 = __ldg(rc + 1), c2 = __ldg(rc + 2), c3 = __ldg(rc + 3);
-        const R rho = wd[0] * c0 + wd[1] * c1 + wd[2] * c2 + wd[3] * c3;
+        const R rho = d.wd[0] * c0 + d.wd[1] * c1 + d.wd[2] * c2 + d.wd[3] * c3;
         phi = rho * p17;
         if (POT) {
-            const R drho = dwd[0] * c0 + dwd[1] * c1 + dwd[2] * c2 + dwd[3] * c3;
+            const R drho = d.dwd[1] * (c1 - c0) + d.dwd[2] * (c2 - c0) + d.dwd[3] * (c3 - c0);
             const R is2 = recip(s2);
-            const R b = p17 * isq * K.cd * drho;
-            rd = rho * (R(-2) * p17 * (inv_qi + qi * is2)) + b * sgn1;
-            rd2 = rho * (R(-2) * p17 * (recip(qj) + qj * is2)) - b * sgn2;
+            const R b = p17 * d.isq * K.cd * drho;
+            rd = rho * (R(-2) * p17 * (inv_qi + qi * is2)) + b * d.sgn1;
+            rd2 = rho * (R(-2) * p17 * (recip(qj) + qj * is2)) - b * d.sgn2;
         }
     }
+}
+
+// One pair: phi and (POT) r dphi/dd1, r dphi/dd2; counts a delta past the last node.
+template <bool POT, typename R>
+__device__ __forceinline__ void pair_phi(R r2, R qi, R qj, R inv_qi, R qi2, const Consts<R> &K,
+                                         const Table<R> &tb, R &phi, R &rd, R &rd2, unsigned &ncl) {
+    Delta<R> d;
+    delta_part<POT, R>(qi, qj, K, d);
+    ncl += d.cl ? 1u : 0u;
+    dist_part<POT, R>(r2, qi, qj, inv_qi, qi2, d, K, tb, phi, rd, rd2);
 }
 
 template <typename R>
@@ -251,6 +320,7 @@ __device__ void make_consts(const PairShared &sh, Consts<R> &K) {
 template <typename R>
 __device__ void make_table(const PairShared &sh, Table<R> &tb) {
     tb.S = sh.S;
+    tb.SB = band_stride(sh.S);
     tb.g = sizeof(R) == 4 ? reinterpret_cast<const R *>(sh.tab32) : reinterpret_cast<const R *>(sh.tab64);
     tb.rho = tb.g + static_cast<size_t>(sh.nD + 2) * sh.S;
     tb.s = 0;
@@ -284,7 +354,7 @@ __device__ __forceinline__ bool beyond(double r2, double, double, double, const 
     return r2 > c.rc2d;
 }
 
-// Squared distance between the i box and the j box shifted by image m.
+// Squared distance between the i box shifted by image m and the j box.
 __device__ __forceinline__ float box_gap2(const float ilo[3], const float ihi[3], const float jl[3],
                                           const float jh[3], const int m[3], const int dims[3],
                                           const float h2[3]) {
@@ -320,7 +390,130 @@ __device__ __forceinline__ void flush(WarpTotals &t, const PairLaunch &pl, bool 
     t.pairs = t.evals = t.clamped = 0;
 }
 
+// Two images of one (i, j) pair in the resident band, evaluated together: slot s
+// has cell coordinate tD.s (a slot that is not wanted carries a valid dummy).
+// wdb, dwdb: the pair's delta weights in both halves.  Returns phi and, with
+// POT, the cell-coordinate derivatives pt (along D) and pu (along delta).
+template <bool POT>
+__device__ __forceinline__ void band_pair2(const Table<float> &tb, float2 tD, int l, bool use0,
+                                           bool use1, const float2 wdb[4], const float2 dwdb[4],
+                                           float2 &p, float2 &pt, float2 &pu) {
+    int k0, k1;
+    const float2 t = floor_split2(tD, k0, k1);
+    float2 wD[4], dwD[4];
+    bw2(t, wD);
+    if (POT) bdw2(t, dwD);
+    const uint32_t a0 = tb.s + 4u * static_cast<uint32_t>((k0 - tb.k0) * tb.SB + l);
+    const uint32_t a1 = tb.s + 4u * static_cast<uint32_t>((k1 - tb.k0) * tb.SB + l);
+    const uint32_t rs = 4u * static_cast<uint32_t>(tb.SB);
+    p = f2(0.0f);
+    pt = f2(0.0f);
+    pu = f2(0.0f);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        float2 c[4];
+#pragma unroll
+        for (int n = 0; n < 4; ++n)  // an unused slot reads nothing
+            c[n] = make_float2(use0 ? lds32(a0 + m * rs + 4u * n) : 0.0f, use1 ? lds32(a1 + m * rs + 4u * n) : 0.0f);
+        const float2 row = fma2(wdb[3], c[3], fma2(wdb[2], c[2], fma2(wdb[1], c[1], mul2(wdb[0], c[0]))));
+        p = fma2(wD[m], row, p);
+        if (POT) {
+            // delta derivative from exact coefficient differences (see combine)
+            const float2 c0n = mul2(c[0], f2(-1.0f));
+            const float2 drow = fma2(dwdb[3], add2(c[3], c0n), fma2(dwdb[2], add2(c[2], c0n), mul2(dwdb[1], add2(c[1], c0n))));
+            pt = fma2(dwD[m], row, pt);
+            pu = fma2(wD[m], drow, pu);
+        }
+    }
+}
+
+// The images of mask m for one (i, j) pair (FP32): two at a time with packed
+// arithmetic where both lie in the resident band, one at a time otherwise.
+// Adds sum_images phi, r dphi/dd1, r dphi/dd2 to sA, sU, cU; counts the inside
+// evaluations (ins) and those with r > 0 (hits).
+template <bool POT, typename P>
+__device__ __forceinline__ void images_f32(unsigned m, const P *simg, float xi, float yi, float zi,
+                                           float qi, float inv_qi, float qi2, const P &pj,
+                                           const float h2[3], bool lane_ok, bool use_cut,
+                                           const Cut &cut, const Delta<float> &dp,
+                                           const Consts<float> &K, const Table<float> &tb,
+                                           float band_lo, float band_hi, float &sA, float &sU,
+                                           float &cU, unsigned &ins, unsigned &hits) {
+    float2 wdb[4], dwdb[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        wdb[n] = f2(dp.wd[n]);
+        if (POT) dwdb[n] = f2(dp.dwd[n]);
+    }
+    const float2 sqcD = f2(dp.sq * K.cD);
+    const float bq = dp.isq * K.cd;
+    const float2 b1 = f2(bq * dp.sgn1), b2 = f2(-bq * dp.sgn2);
+    float2 A2 = f2(0.0f), U2 = f2(0.0f), V2 = f2(0.0f);
+    do {
+        const int i0 = __ffs(m) - 1;
+        m &= m - 1u;
+        const bool two = m != 0u;
+        int i1 = i0;
+        if (two) {
+            i1 = __ffs(m) - 1;
+            m &= m - 1u;
+        }
+        const P s0 = simg[i0], s1 = simg[i1];
+        const float dx0 = (xi + s0.x) - pj.x, dy0 = (yi + s0.y) - pj.y, dz0 = (zi + s0.z) - pj.z;
+        const float dx1 = (xi + s1.x) - pj.x, dy1 = (yi + s1.y) - pj.y, dz1 = (zi + s1.z) - pj.z;
+        const float r20 = h2[0] * (dx0 * dx0) + h2[1] * (dy0 * dy0) + h2[2] * (dz0 * dz0);
+        const float r21 = h2[0] * (dx1 * dx1) + h2[1] * (dy1 * dy1) + h2[2] * (dz1 * dz1);
+        const bool in0 = lane_ok && !(use_cut && beyond(r20, dx0, dy0, dz0, cut));
+        const bool in1 = two && lane_ok && !(use_cut && beyond(r21, dx1, dy1, dz1, cut));
+        if (!(in0 || in1)) continue;
+        ins += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
+        hits += ((in0 && r20 > 0.0f) ? 1u : 0u) + ((in1 && r21 > 0.0f) ? 1u : 0u);
+        const float2 rr = make_float2(rlen(r20), rlen(r21));
+        const float2 tD = mul2(rr, sqcD);
+        const bool f0 = !in0 || (tD.x >= band_lo && tD.x < band_hi);
+        const bool f1 = !in1 || (tD.y >= band_lo && tD.y < band_hi);
+        if (f0 && f1) {
+            const float2 tq = make_float2(in0 ? tD.x : band_lo, in1 ? tD.y : band_lo);
+            float2 p, pt, pu;
+            band_pair2<POT>(tb, tq, dp.l, in0, in1, wdb, dwdb, p, pt, pu);
+            const float2 w = make_float2(in0 ? 1.0f : 0.0f, in1 ? 1.0f : 0.0f);
+            A2 = fma2(p, w, A2);
+            if (POT) {
+                const float2 a = mul2(mul2(rr, f2(K.cD)), pt);
+                U2 = fma2(fma2(pu, b1, a), w, U2);
+                V2 = fma2(fma2(pu, b2, a), w, V2);
+            }
+        } else {
+            if (in0) {
+                float phi, rd = 0.0f, rd2 = 0.0f;
+                dist_part<POT, float>(r20, qi, pj.w, inv_qi, qi2, dp, K, tb, phi, rd, rd2);
+                A2.x += phi;
+                U2.x += rd;
+                V2.x += rd2;
+            }
+            if (in1) {
+                float phi, rd = 0.0f, rd2 = 0.0f;
+                dist_part<POT, float>(r21, qi, pj.w, inv_qi, qi2, dp, K, tb, phi, rd, rd2);
+                A2.y += phi;
+                U2.y += rd;
+                V2.y += rd2;
+            }
+        }
+    } while (m != 0u);
+    sA = A2.x + A2.y;
+    sU = U2.x + U2.y;
+    cU = V2.x + V2.y;
+}
+
 // MODE 0: energy (unordered pairs), MODE 1: potential (A, U per point).
+//
+// Per work item the warp holds an i tile (lane = i point).  For each j tile it
+// lists the images whose shifted i box comes within the cutoff of the j box, then
+// each lane marks, for its own j point, which of those images bring the i box
+// within the cutoff of that point.  The pair loop runs over j points (broadcast)
+// and, inside, over the marked images: the delta part of a pair is computed once
+// for all its images, and the j-side sums of the potential are reduced over the
+// warp once per j point.
 template <typename R, int MODE, int NT>
 __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaunch pl) {
     constexpr bool POT = (MODE == 1);
@@ -331,8 +524,9 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
     __shared__ int s_C[kMaxInst];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    P *sp = reinterpret_cast<P *>(smem_raw) + warp * kTile;
-    R *sn = reinterpret_cast<R *>(smem_raw + sizeof(P) * kTile * NW) + warp * kTile;
+    P *sp = reinterpret_cast<P *>(smem_raw) + warp * kTile;             // j tile
+    P *simg = reinterpret_cast<P *>(smem_raw) + (NW + warp) * kTile;    // image shifts
+    R *sn = reinterpret_cast<R *>(smem_raw + 2 * sizeof(P) * kTile * NW) + warp * kTile;
 
     const PairShared &sh = pl.sh;
     Table<R> tb;
@@ -340,13 +534,14 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
     Consts<R> K;
     make_consts<R>(sh, K);
     if constexpr (sizeof(R) == 4) {
-        float *band = reinterpret_cast<float *>(smem_raw + (sizeof(P) + sizeof(R)) * kTile * NW);
+        float *band = reinterpret_cast<float *>(smem_raw + (2 * sizeof(P) + sizeof(R)) * kTile * NW);
         tb.s = static_cast<uint32_t>(__cvta_generic_to_shared(band));
         tb.k0 = sh.ks0;
         tb.kn = sh.ksn;
-        const int nb = sh.ksn * sh.S;
-        const float *src = sh.tab32 + static_cast<size_t>(sh.ks0) * sh.S;
-        for (int e = threadIdx.x; e < nb; e += NT) band[e] = __ldg(src + e);
+        const int S = sh.S, SB = tb.SB;
+        const float *src = sh.tab32 + static_cast<size_t>(sh.ks0) * S;
+        for (int row = warp; row < sh.ksn; row += NW)
+            for (int col = lane; col < S; col += 32) band[row * SB + col] = __ldg(src + row * S + col);
     }
     // work items per instance: (i tiles) x (chunks of jtiles_per_item j tiles)
     if (threadIdx.x == 0) {
@@ -361,6 +556,9 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
         }
         s_prefix[pl.ninst] = acc;
     }
+    // cell coordinates tD with all four rows of the cell in the resident band
+    const float band_lo = static_cast<float>(tb.k0);
+    const float band_hi = static_cast<float>(min(tb.k0 + tb.kn - 3, sh.nD - 1));
     __syncthreads();  // the only block barrier: table band and item counts ready
     const unsigned int n_items = min(s_prefix[pl.ninst], sh.item_limit);
 
@@ -444,88 +642,138 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
             const int jn = min(kTile, n_act - jb);
             const float4 jlo = __ldg(pp.blo + J), jhi = __ldg(pp.bhi + J);
             const float jl[3] = {jlo.x, jlo.y, jlo.z}, jh[3] = {jhi.x, jhi.y, jhi.z};
-            int mlo[3], mhi[3];
+            int mlo[3], nm[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 if (M[a] == 0) {
                     mlo[a] = 0;
-                    mhi[a] = 0;
+                    nm[a] = 1;
                 } else {
                     const float N = static_cast<float>(dims[a]);
                     mlo[a] = max(-M[a], static_cast<int>(ceilf((-rcm[a] - (ihi[a] - jl[a])) / N)));
-                    mhi[a] = min(M[a], static_cast<int>(floorf((rcm[a] - (ilo[a] - jh[a])) / N)));
+                    const int mhi = min(M[a], static_cast<int>(floorf((rcm[a] - (ilo[a] - jh[a])) / N)));
+                    nm[a] = max(0, mhi - mlo[a] + 1);
                 }
             }
-            bool any = false;
-            for (int m0 = mlo[0]; m0 <= mhi[0] && !any; ++m0)
-                for (int m1 = mlo[1]; m1 <= mhi[1] && !any; ++m1)
-                    for (int m2 = mlo[2]; m2 <= mhi[2] && !any; ++m2) {
-                        const int mm[3] = {m0, m1, m2};
-                        any = !use_cut || box_gap2(ilo, ihi, jl, jh, mm, dims, h2f) <= rc2_box;
-                    }
-            if (!any) continue;
-            __syncwarp();
-            if (lane < jn) {
-                sp[lane] = PT<R>::load(pts, jb + lane);
-                sn[lane] = __ldg(nsrc + jb + lane);
-            }
-            __syncwarp();
-            R a_acc = 0, u_acc = 0;  // i side (this lane's i)
-            R ja = 0, ju = 0;        // j side: lane L collects j = jb + L
-            // weights: off-diagonal tiles count every pair for i and for j; in the
-            // diagonal tile j > i counts for both, j == i (self and self-images) for i only
+            const int n_cand = nm[0] * nm[1] * nm[2];
             const bool diag = (J == I);
-            for (int m0 = mlo[0]; m0 <= mhi[0]; ++m0)
-                for (int m1 = mlo[1]; m1 <= mhi[1]; ++m1)
-                    for (int m2 = mlo[2]; m2 <= mhi[2]; ++m2) {
-                        const int mm[3] = {m0, m1, m2};
-                        if (use_cut && box_gap2(ilo, ihi, jl, jh, mm, dims, h2f) > rc2_box) continue;
-                        const R xs = xi + static_cast<R>(m0 * dims[0]);
-                        const R ys = yi + static_cast<R>(m1 * dims[1]);
-                        const R zs = zi + static_cast<R>(m2 * dims[2]);
-                        tot.evals += static_cast<unsigned long long>(jn) * static_cast<unsigned long long>(ni_act);
-#pragma unroll 2
-                        for (int jj = 0; jj < jn; ++jj) {
-                            const P pj = sp[jj];
-                            const R nj = sn[jj];
-                            const R dx = xs - pj.x, dy = ys - pj.y, dz = zs - pj.z;
-                            const R r2 = h2[0] * (dx * dx) + h2[1] * (dy * dy) + h2[2] * (dz * dz);
-                            const bool both = !diag || jj > lane;
-                            const bool inside = act && (both || jj == lane) && !(use_cut && beyond(r2, dx, dy, dz, cut));
-                            R cA = 0, cU = 0;
-                            if (inside) {
-                                R phi, rd = 0, rd2 = 0;
-                                unsigned ncl = 0;
-                                pair_phi<POT, R>(r2, qi, pj.w, inv_qi, qi2, K, tb, phi, rd, rd2, ncl);
-                                const unsigned wt = both ? 2u : 1u;  // ordered pairs represented
-                                if (POT) {
-                                    a_acc += nj * phi;
-                                    u_acc += nj * rd;
-                                    if (both) {
-                                        cA = ni * phi;
-                                        cU = ni * rd2;
-                                    }
-                                } else {
-                                    a_acc += static_cast<R>(wt) * nj * phi;
-                                }
-                                cnt += (r2 > R(0)) ? wt : 0u;
-                                nclamp += ncl * wt;
+            bool staged = false;
+            // candidate images in chunks of 32, one per lane
+            for (int c0 = 0; c0 < n_cand; c0 += 32) {
+                const int t = c0 + lane;
+                bool ok = false;
+                int mm[3] = {0, 0, 0};
+                if (t < n_cand) {
+                    mm[2] = mlo[2] + t % nm[2];
+                    const int t1 = t / nm[2];
+                    mm[1] = mlo[1] + t1 % nm[1];
+                    mm[0] = mlo[0] + t1 / nm[1];
+                    ok = !use_cut || box_gap2(ilo, ihi, jl, jh, mm, dims, h2f) <= rc2_box;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                if (bal == 0u) continue;
+                __syncwarp();  // earlier reads of simg, sp, sn are done
+                if (ok) {
+                    P sft;
+                    sft.x = static_cast<R>(mm[0] * dims[0]);
+                    sft.y = static_cast<R>(mm[1] * dims[1]);
+                    sft.z = static_cast<R>(mm[2] * dims[2]);
+                    sft.w = R(0);
+                    simg[__popc(bal & ((1u << lane) - 1u))] = sft;
+                }
+                if (!staged) {
+                    if (lane < jn) {
+                        sp[lane] = PT<R>::load(pts, jb + lane);
+                        sn[lane] = __ldg(nsrc + jb + lane);
+                    }
+                    staged = true;
+                }
+                __syncwarp();
+                const int nimg = __popc(bal);
+                // this lane's j point: images that bring the i box within the cutoff
+                unsigned jm = 0u;
+                if (lane < jn) {
+                    const P pjl = sp[lane];
+                    const float px = static_cast<float>(pjl.x), py = static_cast<float>(pjl.y),
+                                pz = static_cast<float>(pjl.z);
+                    for (int b = 0; b < nimg; ++b) {
+                        const P sft = simg[b];
+                        const float sx = static_cast<float>(sft.x), sy = static_cast<float>(sft.y),
+                                    sz = static_cast<float>(sft.z);
+                        const float gx = fmaxf(0.0f, fmaxf(ilo[0] + sx - px, px - ihi[0] - sx));
+                        const float gy = fmaxf(0.0f, fmaxf(ilo[1] + sy - py, py - ihi[1] - sy));
+                        const float gz = fmaxf(0.0f, fmaxf(ilo[2] + sz - pz, pz - ihi[2] - sz));
+                        const float d2 = h2f[0] * gx * gx + h2f[1] * gy * gy + h2f[2] * gz * gz;
+                        if (!use_cut || d2 <= rc2_box) jm |= 1u << b;
+                    }
+                }
+                R a_acc = 0, u_acc = 0;  // i side (this lane's i)
+                R ja = 0, ju = 0;        // j side: lane L collects j = jb + L
+                for (int jj = 0; jj < jn; ++jj) {
+                    unsigned m = __shfl_sync(0xffffffffu, jm, jj);
+                    if (m == 0u) continue;
+                    tot.evals += static_cast<unsigned long long>(__popc(m)) * static_cast<unsigned long long>(ni_act);
+                    const P pj = sp[jj];
+                    const R nj = sn[jj];
+                    // weights: off-diagonal tiles count every pair for i and for j; in the
+                    // diagonal tile j > i counts for both, j == i (self and self-images) for i only
+                    const bool both = !diag || jj > lane;
+                    const bool lane_ok = act && (both || jj == lane);
+                    Delta<R> dp;
+                    delta_part<POT, R>(qi, pj.w, K, dp);
+                    R sA = 0, sU = 0, cA = 0, cU = 0;
+                    unsigned ins = 0, hits = 0;
+                    if constexpr (sizeof(R) == 4) {
+                        images_f32<POT, P>(m, simg, xi, yi, zi, qi, inv_qi, qi2, pj, h2, lane_ok, use_cut,
+                                           cut, dp, K, tb, band_lo, band_hi, sA, sU, cU, ins, hits);
+                        cA = sA;
+                    } else do {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1u;
+                        const P sft = simg[b];
+                        const R dx = (xi + sft.x) - pj.x, dy = (yi + sft.y) - pj.y, dz = (zi + sft.z) - pj.z;
+                        const R r2 = h2[0] * (dx * dx) + h2[1] * (dy * dy) + h2[2] * (dz * dz);
+                        if (lane_ok && !(use_cut && beyond(r2, dx, dy, dz, cut))) {
+                            R phi, rd = 0, rd2 = 0;
+                            dist_part<POT, R>(r2, qi, pj.w, inv_qi, qi2, dp, K, tb, phi, rd, rd2);
+                            sA += phi;
+                            if (POT) {
+                                sU += rd;
+                                cA += phi;
+                                cU += rd2;
                             }
-                            if (POT && __any_sync(0xffffffffu, cA != R(0) || cU != R(0))) {
-                                cA = warp_sum(cA);
-                                cU = warp_sum(cU);
-                                if (lane == jj) {
-                                    ja += cA;
-                                    ju += cU;
-                                }
+                            ins += 1u;
+                            hits += (r2 > R(0)) ? 1u : 0u;
+                        }
+                    } while (m != 0u);
+                    const unsigned wt = both ? 2u : 1u;  // ordered pairs represented
+                    cnt += hits * wt;
+                    nclamp += dp.cl ? ins * wt : 0u;
+                    if (POT) {
+                        a_acc += nj * sA;
+                        u_acc += nj * sU;
+                    } else {
+                        a_acc += static_cast<R>(wt) * nj * sA;
+                    }
+                    if (POT) {
+                        cA = both ? ni * cA : R(0);
+                        cU = both ? ni * cU : R(0);
+                        if (__any_sync(0xffffffffu, cA != R(0) || cU != R(0))) {
+                            cA = warp_sum(cA);
+                            cU = warp_sum(cU);
+                            if (lane == jj) {
+                                ja += cA;
+                                ju += cU;
                             }
                         }
                     }
-            A64 += static_cast<double>(a_acc);
-            U64 += static_cast<double>(u_acc);
-            if (POT && lane < jn) {
-                if (ja != R(0)) atomicAdd(pp.A + jb + lane, static_cast<double>(ja));
-                if (ju != R(0)) atomicAdd(pp.U + jb + lane, static_cast<double>(sn[lane]) * static_cast<double>(ju));
+                }
+                A64 += static_cast<double>(a_acc);
+                U64 += static_cast<double>(u_acc);
+                if (POT && lane < jn) {
+                    if (ja != R(0)) atomicAdd(pp.A + jb + lane, static_cast<double>(ja));
+                    if (ju != R(0)) atomicAdd(pp.U + jb + lane, static_cast<double>(sn[lane]) * static_cast<double>(ju));
+                }
             }
         }
         if (act) {
@@ -606,6 +854,7 @@ template <typename R, int MODE>
 int launch_nt(int threads, const PairLaunch &pl, int nctas, size_t smem, cudaStream_t st) {
     switch (threads) {
         case 256: return launch_one<R, MODE, 256>(pl, nctas, smem, st);
+        case 384: return launch_one<R, MODE, 384>(pl, nctas, smem, st);
         case 1024: return launch_one<R, MODE, 1024>(pl, nctas, smem, st);
         default: return launch_one<R, MODE, 512>(pl, nctas, smem, st);
     }
@@ -614,9 +863,11 @@ int launch_nt(int threads, const PairLaunch &pl, int nctas, size_t smem, cudaStr
 }  // namespace
 
 int pair_smem_bytes(int precision, int threads, int ksn, int S) {
-    const size_t pt = precision == VDWDF_FP64 ? sizeof(dvec4) + sizeof(double) : sizeof(float4) + sizeof(float);
+    // per warp: j tile (points, densities) and image shifts; FP32: the table band
+    const size_t pt = precision == VDWDF_FP64 ? 2 * sizeof(dvec4) + sizeof(double)
+                                              : 2 * sizeof(float4) + sizeof(float);
     size_t b = pt * kTile * static_cast<size_t>(threads / 32);
-    if (precision != VDWDF_FP64) b += static_cast<size_t>(ksn) * S * sizeof(float);
+    if (precision != VDWDF_FP64) b += static_cast<size_t>(ksn) * band_stride(S) * sizeof(float);
     return static_cast<int>(b);
 }
 

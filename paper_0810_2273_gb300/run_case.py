@@ -23,6 +23,8 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--table", default=None)
     ap.add_argument("--quad-level", type=int, default=1)
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: library default)")
+    ap.add_argument("--items-per-sm", type=int, default=0, help="work items per warp slot (0: default)")
     a = ap.parse_args(argv)
 
     import torch
@@ -37,17 +39,18 @@ def main(argv=None):
     dev = torch.device("cuda:0")
     n = torch.from_numpy(w["density"]).to(dev)
     args = (w["lengths"], w["periodic"], w["n_cut"], w["r_cut"], T)
+    tu = {"threads": a.threads, "items_per_sm": a.items_per_sm} if (a.threads or a.items_per_sm) else None
     for k in range(a.repeat):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if a.mode == "potential":
-            E, _, res = V.potential(n, *args, precision=a.precision)
+            E, _, res = V.potential(n, *args, precision=a.precision, tuning=tu)
         else:
-            E, res = V.energy(n, *args, precision=a.precision)
+            E, res = V.energy(n, *args, precision=a.precision, tuning=tu)
         torch.cuda.synchronize()
         res = dict(res)
         res.update(call=k, E=E, wall_ms=1e3 * (time.perf_counter() - t0), workload=a.workload,
-                   dims=list(n.shape), mode=a.mode, precision=a.precision,
+                   dims=list(n.shape), mode=a.mode, precision=a.precision, tuning=tu,
                    pairs_per_s=res["pairs"] / max(res["ms_pairs"] * 1e-3, 1e-12))
         print(json.dumps(res), flush=True)
 
