@@ -68,10 +68,19 @@ typedef struct {
 } vdwdf_grid;
 
 /* Opaque kernel table: phi on the node grid D_k = Dmax k/(nD-1),
- * delta_l = l/ndelta (section 2: "redefined to depend on two quantities,
- * D >= 0 and 0 <= delta < 1"; section 7: limits and divisions fixed by
- * refinement), its FP64 and FP32 cubic-spline coefficients, and their device
- * copies.  Owned by the library; free with vdwdf_table_free. */
+ * delta_l = l/ndelta (section 2: the kernel as a function of D >= 0 and
+ * 0 <= delta < 1; section 7: limits and divisions fixed by refinement), its
+ * FP64 and FP32 cubic-spline coefficients, and their device copies.  Owned by
+ * the library; free with vdwdf_table_free.
+ * The kernel the pair sum uses:
+ *  - 0 <= D <= Dmax: the tensor-product interpolating cubic spline of the
+ *    nodes, zero slope at D = 0 and delta = 0, zero curvature at the last
+ *    node of each axis;
+ *  - D > Dmax: Dion eq. 17 times rho(delta), the cubic spline (same end
+ *    conditions) of phi(Dmax, delta_l) / eq. 17 (Dmax, delta_l), so that the
+ *    kernel is continuous at Dmax for every delta;
+ *  - delta above the last node: the spline's linear continuation in delta
+ *    (its curvature is zero there), counted in vdwdf_result.n_clamped. */
 typedef struct vdwdf_table vdwdf_table;
 
 /* Per-call report. */
@@ -81,9 +90,10 @@ typedef struct {
     int64_t n_active;        /* grid points with n >= n_cut                         */
     int64_t pairs;           /* ordered pair interactions (i, j, L) other than the
                                 self term, within r_cut when r_cut > 0              */
-    int64_t pairs_evaluated; /* kernel evaluations done (folded by i<->j symmetry
-                                for energy-only calls, outside-cutoff tests included) */
-    int64_t n_clamped;       /* table lookups with delta beyond the last node      */
+    int64_t pairs_evaluated; /* lane slots run by the pair kernel: (i, j, image)
+                                candidates left after culling, each unordered pair
+                                once (i<->j folded), outside-cutoff tests included */
+    int64_t n_clamped;       /* evaluations with delta past the last node (spline continued linearly) */
     double q0_min, q0_max;   /* over active points                                 */
     float ms_prep;           /* device time: gradient, q0, trimming, tiling        */
     float ms_pairs;          /* device time: pair kernel(s)                         */
