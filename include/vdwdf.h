@@ -204,6 +204,44 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
                          const vdwdf_tuning *tuning, double *E_out, vdwdf_result *out,
                          void *cuda_stream);
 
+/* vdwdf_energy that allocates nothing.  The paper has no counterpart: JuNoLo
+ * allocates its arrays once per run.  This entry point is for callers that
+ * cannot allocate device memory while they run, for example:
+ *  - a host code that has reserved the device memory for its own arrays;
+ *  - a loop that must not synchronise the device (cudaMalloc and cudaFree
+ *    can synchronise);
+ *  - a loop of many small grids (binding curves, geometry steps) where one
+ *    allocation per call costs more than the pair sum.
+ * Same arguments, results and errors as vdwdf_energy, with library default
+ * tuning.  Limits and conditions:
+ *  - Size: at most 65536 grid points and 65536 4x4x4 bricks.  Larger grids
+ *    return VDWDF_EUNSUPPORTED before any device work.
+ *  - Scratch: all of a call's scratch lives in one 8 MiB static device array
+ *    of the library.  It is module data, one copy per device, present as
+ *    soon as the library's module is loaded on that device.  The call makes
+ *    no cudaMalloc/cudaFree and no call into an allocating library; the
+ *    Morton order of the bricks is staged through static host arrays.
+ *  - Set-up: the array's device address is taken with cudaGetSymbolAddress
+ *    once per device, on the first call on that device.  That lookup may
+ *    load the module, so make the first call on each device before any
+ *    stream capture.
+ *  - Table: the table must already be resident on the current device, that
+ *    is, used there once by vdwdf_energy, vdwdf_potential,
+ *    vdwdf_energy_batched or vdwdf_kernel_eval (npts >= 1), because making it
+ *    resident allocates.  Otherwise the call returns VDWDF_ENOTABLE.
+ *  - Overlap: calls overlapping in time would race on the one scratch array.
+ *    The library therefore holds a process-wide lock for the whole call, and
+ *    the call synchronises its stream before returning.  Other code must not
+ *    write the array.
+ *  - Zeroing: everything that must start at zero (the counters and the
+ *    work-queue head) is cleared by the call itself on the stream.  Every
+ *    per-item energy partial is written before it is read.
+ *  - Timings: ms_prep, ms_pairs and ms_post are 0 (no CUDA events are
+ *    created). */
+int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev,
+                         double n_cut, double r_cut, const vdwdf_table *table, int precision,
+                         vdwdf_result *out, void *cuda_stream);
+
 /* Time candidate launch shapes of the pair kernel on this problem (energy
  * path, a sample of the work) and write the fastest to *best. */
 int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, double r_cut,

@@ -16,7 +16,7 @@ import numpy as np
 from . import _native
 from ._native import VDWDF_FP32, VDWDF_FP64, VdwdfError, vdwdf_grid, vdwdf_result, vdwdf_tuning
 
-__all__ = ["Table", "grid", "energy", "potential", "energy_batched", "q0", "kernel_eval",
+__all__ = ["Table", "grid", "energy", "energy_noalloc", "potential", "energy_batched", "q0", "kernel_eval",
            "autotune", "launch_count", "NonlocalEnergy", "nonlocal_energy", "VdwdfError",
            "VDWDF_FP32", "VDWDF_FP64"]
 
@@ -151,6 +151,25 @@ def energy(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", grad=Non
                               float(n_cut), float(r_cut), table.handle, _prec(precision), _tuning(tuning),
                               ctypes.byref(res), _stream(n))
     _native.check(st, "vdwdf_energy")
+    return res.E, res.as_dict()
+
+
+def energy_noalloc(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", grad=None):
+    """As energy, through vdwdf_energy_noalloc: no allocation during the call (grids
+    of at most 65536 points; the table must already be resident on n's device)."""
+    _check_tensor(n, "n")
+    if grad is not None:
+        _check_tensor(grad, "grad")
+    torch = _torch()
+    lib = _native.load()
+    g = grid(lengths, n.shape, periodic)
+    res = vdwdf_result()
+    with torch.cuda.device(n.device):
+        st = lib.vdwdf_energy_noalloc(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()),
+                                      ctypes.c_void_p(grad.data_ptr()) if grad is not None else None,
+                                      float(n_cut), float(r_cut), table.handle, _prec(precision),
+                                      ctypes.byref(res), _stream(n))
+    _native.check(st, "vdwdf_energy_noalloc")
     return res.E, res.as_dict()
 
 

@@ -56,6 +56,8 @@ PROTOTYPES = {
     "vdwdf_energy_batched": (_c_i, [_c_i, ctypes.POINTER(vdwdf_grid), ctypes.POINTER(_c_p), _c_d, _c_d,
                                     _c_p, _c_i, ctypes.POINTER(vdwdf_tuning), _c_p,
                                     ctypes.POINTER(vdwdf_result), _c_p]),
+    "vdwdf_energy_noalloc": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_d, _c_d, _c_p, _c_i,
+                                    ctypes.POINTER(vdwdf_result), _c_p]),
     "vdwdf_autotune": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_d, _c_d, _c_p, _c_i,
                               ctypes.POINTER(vdwdf_tuning), _c_p]),
     "vdwdf_strerror": (ctypes.c_char_p, [_c_i]),

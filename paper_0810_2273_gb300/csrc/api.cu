@@ -969,3 +969,164 @@ int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, do
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The energy without any allocation: all scratch of one call lives in a
+// static device array of the library.
+// ---------------------------------------------------------------------------
+namespace vdwdf {
+namespace {
+
+constexpr long long kNoAllocMaxPoints = 65536;       // grid points per call
+constexpr int kNoAllocMaxBricks = 65536;             // 4x4x4 bricks per call
+constexpr size_t kNoAllocBytes = size_t(8) << 20;    // 8 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+// One per device (module static data); cleared where needed by each call.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;  // held for a whole call: calls never overlap in a process
+unsigned char *g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::pair<uint64_t, int> g_noalloc_keys[kNoAllocMaxBricks];  // host staging, no heap
+int g_noalloc_order[kNoAllocMaxBricks];
+
+size_t round256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
+
+// Device address of the static scratch, looked up once per device.
+int noalloc_base(unsigned char **p) {
+    int dev = 0;
+    VDWDF_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return VDWDF_EUNSUPPORTED;
+    if (!g_noalloc_addr[dev]) {
+        void *a = nullptr;
+        VDWDF_CUDA_TRY(cudaGetSymbolAddress(&a, g_noalloc_scratch));
+        g_noalloc_addr[dev] = static_cast<unsigned char *>(a);
+    }
+    *p = g_noalloc_addr[dev];
+    return VDWDF_OK;
+}
+
+// The table's device copies if they already exist on the current device.
+int table_resident(const vdwdf_table *tc, double **d64, float **d32) {
+    vdwdf_table *t = const_cast<vdwdf_table *>(tc);
+    int dev = 0;
+    VDWDF_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(t->mu);
+    auto it = t->dev.find(dev);
+    if (it == t->dev.end()) return VDWDF_ENOTABLE;
+    *d64 = it->second.first;
+    *d32 = it->second.second;
+    return VDWDF_OK;
+}
+
+long long brick_count(const int dims[3]) {
+    return static_cast<long long>((dims[0] + kBrick - 1) / kBrick) * ((dims[1] + kBrick - 1) / kBrick) *
+           ((dims[2] + kBrick - 1) / kBrick);
+}
+
+// The Morton order of the bricks (as brick_order), built in host statics and
+// copied to order_dev on the stream.
+int noalloc_order(const int dims[3], int *order_dev, cudaStream_t st) {
+    const int bx = (dims[0] + kBrick - 1) / kBrick, by = (dims[1] + kBrick - 1) / kBrick,
+              bz = (dims[2] + kBrick - 1) / kBrick;
+    const int n = bx * by * bz;
+    for (int x = 0; x < bx; ++x)
+        for (int y = 0; y < by; ++y)
+            for (int z = 0; z < bz; ++z) {
+                const int id = (x * by + y) * bz + z;
+                g_noalloc_keys[id] = {spread3(x) << 2 | spread3(y) << 1 | spread3(z), id};
+            }
+    std::sort(g_noalloc_keys, g_noalloc_keys + n);
+    for (int i = 0; i < n; ++i) g_noalloc_order[i] = g_noalloc_keys[i].second;
+    VDWDF_CUDA_TRY(cudaMemcpyAsync(order_dev, g_noalloc_order, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    return VDWDF_OK;
+}
+
+}  // namespace
+}  // namespace vdwdf
+
+extern "C" {
+
+int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev,
+                         double n_cut, double r_cut, const vdwdf_table *table, int precision,
+                         vdwdf_result *out, void *cuda_stream) {
+    using namespace vdwdf;
+    Geom G;
+    int rc = check_grid(grid, G);
+    if (rc) return rc;
+    rc = check_cut(n_cut, r_cut, G);
+    if (rc) return rc;
+    if (!n_dev) return VDWDF_EINVAL;
+    if (!table) return VDWDF_ENOTABLE;
+    if (precision != VDWDF_FP32 && precision != VDWDF_FP64) return VDWDF_EINVAL;
+    // size limits, checked before any device work
+    if (G.N > kNoAllocMaxPoints) return VDWDF_EUNSUPPORTED;
+    const long long nbl = brick_count(G.dims);
+    if (nbl > kNoAllocMaxBricks) return VDWDF_EUNSUPPORTED;
+    const int nb = static_cast<int>(nbl);
+    const bool fp64 = precision == VDWDF_FP64;
+    const size_t o_order = round256(layout(G, nb, false, fp64, nullptr, nullptr));
+    const size_t o_items = o_order + round256(sizeof(int) * nb);
+    if (o_items + 256 * sizeof(double) > kNoAllocBytes) return VDWDF_EUNSUPPORTED;
+    const unsigned int item_space = static_cast<unsigned int>((kNoAllocBytes - o_items) / sizeof(double));
+
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const long long launches0 = g_launches.load();
+    double *d64 = nullptr;
+    float *d32 = nullptr;
+    rc = table_resident(table, &d64, &d32);
+    if (rc) return rc;
+    unsigned char *base = nullptr;
+    rc = noalloc_base(&base);
+    if (rc) return rc;
+    Work w;
+    layout(G, nb, false, fp64, &w, base);
+    int *order_dev = reinterpret_cast<int *>(base + o_order);
+    double *item_E = reinterpret_cast<double *>(base + o_items);
+
+    // as vdwdf_energy: gradient, q0, trimming and tiles, then the pair sum with
+    // one partial per work item summed in a fixed order
+    rc = noalloc_order(G.dims, order_dev, st);
+    if (rc) return rc;
+    rc = reset_stats(w.stats, st);  // counters start at zero (q0 minimum above all floats)
+    if (rc) return rc;
+    rc = launch_grad_q0(G.dims, G.h, n_dev, grad_dev, w.q0, w.qn, w.qg, st);
+    if (rc) return rc;
+    rc = launch_compact(G.dims, n_dev, n_cut, w.q0, order_dev, nb, w.cnt, w.off, nullptr, w.p32, w.n32,
+                        w.p64, w.n64, w.blo, w.bhi, w.stats, st);
+    if (rc) return rc;
+    Stats hs;
+    std::memset(&hs, 0, sizeof(hs));
+    VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+    VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hs.n_active > 0) {
+        Launch ln = choose_launch(precision, false, nullptr, table, hs.n_active);
+        VDWDF_CUDA_TRY(cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st));  // work-queue head
+        PairLaunch pl;
+        std::memset(&pl, 0, sizeof(pl));
+        const long long items = pair_items(hs.n_active, ln.jt);
+        if (items > 0xFFFFFFF0LL) return VDWDF_EINVAL;
+        fill_shared(table, d64, d32, ln, w.queue, static_cast<unsigned int>(items + 2), pl.sh);
+        // every item below item_cap writes its partial; any beyond it are added atomically
+        pl.sh.item_E = item_E;
+        pl.sh.item_cap = static_cast<unsigned int>(std::min<long long>(items, item_space));
+        pl.ninst = 1;
+        fill_params(G, w, pl.inst[0]);
+        rc = launch_pair(precision, false, ln.threads, pl, ln.nctas, st);
+        if (rc) return rc;
+        rc = launch_reduce_items(pl, st);
+        if (rc) return rc;
+    }
+    VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+    VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hs.guard_trips) return VDWDF_ETIMEOUT;
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        fill_result(hs, G, table, out);
+        out->launches = static_cast<int32_t>(g_launches.load() - launches0);
+    }
+    return VDWDF_OK;
+}
+
+}  // extern "C"

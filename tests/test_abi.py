@@ -98,6 +98,11 @@ def test_host_side_argument_errors(native):
     # batched: bad count
     assert lib.vdwdf_energy_batched(0, None, None, 1e-6, 0.0, ctypes.c_void_p(1), 0, None, None, None,
                                     None) == -1
+    # no-allocation energy: a grid larger than its static scratch holds is refused
+    g.cell[0][1] = 0.0
+    g.n[0], g.n[1], g.n[2] = 64, 64, 17
+    assert lib.vdwdf_energy_noalloc(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1),
+                                    0, ctypes.byref(res), None) == -2
 
 
 def test_table_build_matches_oracle_quadrature(oracle_mod):
