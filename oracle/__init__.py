@@ -75,6 +75,12 @@ def lib():
         L.orc_eps_c.argtypes = [_i, _p, _p, _p]
         L.orc_q0.restype = _i
         L.orc_q0.argtypes = [_i, _p, _p, _p, _p, _p]
+        L.orc_fx_many.restype = _i
+        L.orc_fx_many.argtypes = [_i, _p, _d, _p]
+        L.orc_pbe_H_many.restype = _i
+        L.orc_pbe_H_many.argtypes = [_i, _p, _p, _p]
+        L.orc_semilocal.restype = _i
+        L.orc_semilocal.argtypes = [_i, _p, _p, _p, _p]
         _LIB = L
     return _LIB
 
@@ -243,6 +249,49 @@ def q0(n, g):
     qg = np.zeros((3,) + n.shape)
     lib().orc_q0(N, _ptr(n), _ptr(g), _ptr(q), _ptr(qn), _ptr(qg))
     return q, qn, qg
+
+
+# --------------------------------------------------------------------------
+# Semilocal energies of eq. 3 (section 2): LDA, PBE, revPBE
+# --------------------------------------------------------------------------
+KAPPA_PBE = 0.804     # Perdew, Burke, Ernzerhof 1996
+KAPPA_REVPBE = 1.245  # Zhang and Yang 1998
+
+
+def fx(s, kappa):
+    """GGA exchange enhancement factor F_x(s) = 1 + kappa - kappa/(1 + mu s^2/kappa)."""
+    s = _f64(s)
+    out = np.zeros(s.shape)
+    lib().orc_fx_many(s.size, _ptr(s), float(kappa), _ptr(out))
+    return out
+
+
+def pbe_H(rs, t):
+    """Gradient correction H(rs, t) of the PBE correlation (unpolarised)."""
+    rs, t = np.broadcast_arrays(_f64(rs), _f64(t))
+    rs, t = _f64(rs), _f64(t)
+    out = np.zeros(rs.shape)
+    lib().orc_pbe_H_many(rs.size, _ptr(rs), _ptr(t), _ptr(out))
+    return out
+
+
+def semilocal(n, lengths, g=None):
+    """E_x^LDA, E_c^LDA (PW92), E_x^PBE, E_c^PBE, E_x^revPBE (Hartree) of the density
+    n on an orthorhombic grid of the given cell lengths, summed over points with
+    n > 0; g: [3][n0][n1][n2] gradient, or None for the 4th-order periodic stencil."""
+    n = _f64(n)
+    h = [float(L) / d for L, d in zip(lengths, n.shape)]
+    if g is None:
+        g = gradient(n, h)
+    g = _f64(g).reshape((3,) + n.shape)
+    sums = np.zeros(5)
+    count = ctypes.c_int64()
+    lib().orc_semilocal(n.size, _ptr(n), _ptr(g), _ptr(sums), ctypes.byref(count))
+    dV = h[0] * h[1] * h[2]
+    keys = ("Ex_lda", "Ec_lda", "Ex_pbe", "Ec_pbe", "Ex_revpbe")
+    out = {k: dV * v for k, v in zip(keys, sums)}
+    out["n_points"] = count.value
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -32,6 +32,10 @@
  *   orc_pair_AU                     pinned: brute force with direct
  *                                   quadrature, translation invariance,
  *                                   far-fragment asymptotic sum
+ *   orc_semilocal, orc_fx_many,     pinned: exact uniform scaling of the
+ *   orc_pbe_H_many                  exchange energies on the grid, uniform
+ *                                   density (GGA = LDA), enhancement-factor
+ *                                   and gradient-correction limits
  *   paper-level energies            parity unpinned: the paper's Xe density
  *                                   file is not available
  */
@@ -766,5 +770,93 @@ int orc_q0(int N, const double *n, const double *g, double *q0, double *dq0dn, d
             dq0dg[2 * (size_t)N + m] = c * gz;
         }
     }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Semilocal energies of eq. (3).  Section 2 has JuNoLo evaluate E_x^LDA,   */
+/* E_c^LDA, E_x^PBE, E_c^PBE and E_x^revPBE from the density itself, since */
+/* the DFT code may not report them.  Spin-unpolarised, Hartree units,     */
+/* written from the published definitions:                                 */
+/*   eps_x^LDA = -3 k_F / (4 pi),  k_F = (3 pi^2 n)^(1/3)                  */
+/*   eps_x^GGA = eps_x^LDA F_x(s),  s = |grad n| / (2 k_F n),              */
+/*     F_x(s) = 1 + kappa - kappa / (1 + mu s^2 / kappa)                   */
+/*     PBE (Perdew, Burke, Ernzerhof, PRL 77, 3865 (1996)): kappa = 0.804, */
+/*     revPBE (Zhang and Yang, PRL 80, 890 (1998)): kappa = 1.245,         */
+/*     mu = beta pi^2 / 3 in both                                          */
+/*   eps_c^PBE = eps_c^PW92(rs) + H(rs, t),  t = |grad n| / (2 k_s n),     */
+/*     k_s = (4 k_F / pi)^(1/2),                                           */
+/*     H = gamma ln[1 + (beta/gamma) t^2 (1 + A t^2) / (1 + A t^2 + A^2 t^4)], */
+/*     A = (beta/gamma) / (exp(-eps_c^PW92 / gamma) - 1),                  */
+/*     beta = 0.06672455060314922, gamma = (1 - ln 2) / pi^2               */
+/*   E = dV sum over points with n > 0 of n eps.                           */
+/* ---------------------------------------------------------------------- */
+static const double PBE_beta = 0.06672455060314922;
+
+static double pbe_gamma(void) { return (1.0 - log(2.0)) / (M_PI * M_PI); }
+
+static double pbe_mu(void) { return PBE_beta * M_PI * M_PI / 3.0; }
+
+/* exchange enhancement factor F_x(s) for a given kappa */
+static double fx(double s, double kappa)
+{
+    return 1.0 + kappa - kappa / (1.0 + pbe_mu() * s * s / kappa);
+}
+
+/* gradient correction H(rs, t) of the PBE correlation, given eps_c^PW92(rs) */
+static double pbe_H(double ec, double t)
+{
+    double g = pbe_gamma();
+    double A = (PBE_beta / g) / expm1(-ec / g);
+    double t2 = t * t;
+    double num = 1.0 + A * t2;
+    double den = 1.0 + A * t2 + A * A * t2 * t2;
+    return g * log(1.0 + (PBE_beta / g) * t2 * num / den);
+}
+
+int orc_fx_many(int N, const double *s, double kappa, double *out)
+{
+    for (int p = 0; p < N; ++p) out[p] = fx(s[p], kappa);
+    return 0;
+}
+
+int orc_pbe_H_many(int N, const double *rs, const double *t, double *out)
+{
+    for (int p = 0; p < N; ++p) {
+        double ec, de;
+        pw92(rs[p], &ec, &de);
+        out[p] = pbe_H(ec, t[p]);
+    }
+    return 0;
+}
+
+/* sums[0..4] = sum n eps for x^LDA, c^LDA (PW92), x^PBE, c^PBE, x^revPBE over
+ * the N points with n > 0 (g: [3][N] gradient); *count = number of such points */
+int orc_semilocal(int N, const double *n, const double *g, double *sums, int64_t *count)
+{
+    double S[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int64_t c = 0;
+    for (int m = 0; m < N; ++m) {
+        double nn = n[m];
+        if (!(nn > 0.0)) continue;
+        double gx = g[m], gy = g[(size_t)N + m], gz = g[2 * (size_t)N + m];
+        double ag = sqrt(gx * gx + gy * gy + gz * gz);
+        double kF = cbrt(3.0 * M_PI * M_PI * nn);
+        double ks = sqrt(4.0 * kF / M_PI);
+        double s = ag / (2.0 * kF * nn);
+        double t = ag / (2.0 * ks * nn);
+        double rs = cbrt(3.0 / (4.0 * M_PI * nn));
+        double ec, de;
+        pw92(rs, &ec, &de);
+        double ex = -3.0 * kF / (4.0 * M_PI);
+        S[0] += nn * ex;
+        S[1] += nn * ec;
+        S[2] += nn * ex * fx(s, 0.804);
+        S[3] += nn * (ec + pbe_H(ec, t));
+        S[4] += nn * ex * fx(s, 1.245);
+        ++c;
+    }
+    for (int k = 0; k < 5; ++k) sums[k] = S[k];
+    *count = c;
     return 0;
 }
