@@ -188,6 +188,16 @@ def run_gpu(args):
     E64, _, r64 = V.potential(n, *a, precision="fp64")
     fp64_s = time.perf_counter() - t0
 
+    # the semilocal terms of eq. 3 on the same density (outside the timed steps; the
+    # call's own CUDA events, L2 flushed before each call)
+    semi_ms = []
+    for _ in range(5):
+        flush.zero_()
+        torch.cuda.synchronize()
+        semi = V.semilocal(n, w["lengths"], w["periodic"])
+        semi_ms.append(semi["ms"])
+    semi_t = float(np.median(semi_ms[1:]))
+
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([ms, e2e, float(pairs)], dtype=torch.float64, device=dev)
@@ -238,6 +248,12 @@ def run_gpu(args):
                      "kernel": "k_pair<float, potential, 512>", "ms_per_launch": pms,
                      "ops_per_pair": OPS_PER_PAIR_EV,
                      "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (max SM clock)" % (sms, FP32_LANES_PER_SM, clk)},
+        "semilocal": {"ms_per_call": semi_t, "points": int(n.numel()),
+                      "points_per_s": n.numel() / (semi_t * 1e-3),
+                      "hbm_gbs": 8.0 * n.numel() / (semi_t * 1e-3) / 1e9,
+                      "bound": "fp64 (per-point cbrt, log, expm1 at GB300's FP64 rate)",
+                      "E_hartree": {k: semi[k] for k in ("Ex_lda", "Ec_lda", "Ex_pbe", "Ec_pbe", "Ex_revpbe")},
+                      "eq3_needed_number": semi["Ec_lda"] - semi["Ec_pbe"] + results[-1][0]},
         "cpu_baseline": cpu,
         "e2e": {"value": total_pairs / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(n.numel() * 8),
                 "d2h_bytes_per_step": int(n.numel() * 8 + 8), "ms_per_step": e2e},

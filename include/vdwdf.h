@@ -204,6 +204,42 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
                          const vdwdf_tuning *tuning, double *E_out, vdwdf_result *out,
                          void *cuda_stream);
 
+/* --------------------------------------------------------------------- */
+/* Semilocal energies (paper section 2, eq. (3))                           */
+/* --------------------------------------------------------------------- */
+
+typedef struct {
+    double Ex_lda;       /* LDA exchange, Hartree                                 */
+    double Ec_lda;       /* LDA correlation (Perdew-Wang 1992)                   */
+    double Ex_pbe;       /* PBE exchange                                          */
+    double Ec_pbe;       /* PBE correlation                                       */
+    double Ex_revpbe;    /* revPBE exchange                                       */
+    int64_t n_points;    /* grid points with n > 0 (the others contribute 0)      */
+    float ms;            /* device time of the call                               */
+    int32_t launches;    /* kernels launched by the call                          */
+} vdwdf_semilocal_result;
+
+/* The semilocal terms that eq. (3) combines with E_c^nl.  Section 2 has JuNoLo
+ * evaluate them from the density itself, because the DFT code may not report
+ * them; E_x^revPBE is the optional replacement of E_x^PBE in eq. (3).
+ * Spin-unpolarised, FP64, Hartree:
+ *   eps_x^LDA = -3 k_F/(4 pi), k_F = (3 pi^2 n)^(1/3);
+ *   GGA exchange eps_x^LDA F_x(s), F_x = 1 + kappa - kappa/(1 + mu s^2/kappa),
+ *     s = |grad n|/(2 k_F n), mu = beta pi^2/3, kappa = 0.804 (PBE, Perdew,
+ *     Burke and Ernzerhof 1996) or 1.245 (revPBE, Zhang and Yang 1998);
+ *   eps_c^LDA: Perdew-Wang 1992; eps_c^PBE = eps_c^LDA + H with
+ *     H = gamma ln[1 + (beta/gamma) t^2 (1 + A t^2)/(1 + A t^2 + A^2 t^4)],
+ *     t = |grad n|/(2 k_s n), k_s = (4 k_F/pi)^(1/2),
+ *     A = (beta/gamma)/(exp(-eps_c^LDA/gamma) - 1),
+ *     beta = 0.06672455060314922, gamma = (1 - ln 2)/pi^2;
+ *   E = dV sum of n eps over every grid point with n > 0 (no density cutoff).
+ * grad_dev as in vdwdf_q0.  The sum is reproducible: fixed blocks, fixed order.
+ * Synchronises the stream.
+ * Errors: VDWDF_EINVAL, VDWDF_EUNSUPPORTED (non-orthorhombic cell),
+ * VDWDF_ECUDA, VDWDF_EALLOC. */
+int vdwdf_semilocal(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev,
+                    vdwdf_semilocal_result *out, void *cuda_stream);
+
 /* vdwdf_energy that allocates nothing.  The paper has no counterpart: JuNoLo
  * allocates its arrays once per run.  This entry point is for callers that
  * cannot allocate device memory while they run, for example:

@@ -14,9 +14,11 @@ import ctypes
 import numpy as np
 
 from . import _native
-from ._native import VDWDF_FP32, VDWDF_FP64, VdwdfError, vdwdf_grid, vdwdf_result, vdwdf_tuning
+from ._native import (VDWDF_FP32, VDWDF_FP64, VdwdfError, vdwdf_grid, vdwdf_result, vdwdf_semilocal_result,
+                      vdwdf_tuning)
 
 __all__ = ["Table", "grid", "energy", "energy_noalloc", "potential", "energy_batched", "q0", "kernel_eval",
+           "semilocal", "total_energy_nl",
            "autotune", "launch_count", "NonlocalEnergy", "nonlocal_energy", "VdwdfError",
            "VDWDF_FP32", "VDWDF_FP64"]
 
@@ -171,6 +173,37 @@ def energy_noalloc(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", 
                                       ctypes.byref(res), _stream(n))
     _native.check(st, "vdwdf_energy_noalloc")
     return res.E, res.as_dict()
+
+
+def semilocal(n, lengths, periodic, grad=None):
+    """E_x^LDA, E_c^LDA, E_x^PBE, E_c^PBE, E_x^revPBE (Hartree) of density n over all
+    points with n > 0, through vdwdf_semilocal; returns the result dict."""
+    _check_tensor(n, "n")
+    if grad is not None:
+        _check_tensor(grad, "grad")
+    torch = _torch()
+    lib = _native.load()
+    g = grid(lengths, n.shape, periodic)
+    res = vdwdf_semilocal_result()
+    with torch.cuda.device(n.device):
+        st = lib.vdwdf_semilocal(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()),
+                                 ctypes.c_void_p(grad.data_ptr()) if grad is not None else None,
+                                 ctypes.byref(res), _stream(n))
+    _native.check(st, "vdwdf_semilocal")
+    return res.as_dict()
+
+
+def total_energy_nl(E_tot_dft, semi, E_c_nl, exchange="pbe"):
+    """Eq. 3: the total energy with the nonlocal correlation, from the DFT total
+    energy of a PBE calculation, the semilocal terms of that density (the dict of
+    semilocal()) and E_c^nl:
+        E_tot^NL = E_tot^DFT - E_x^PBE - E_c^PBE + (E_x + E_c^LDA + E_c^nl),
+    with E_x = E_x^PBE, or E_x^revPBE for exchange="revpbe" (the alternative the
+    paper mentions after eq. 3).  Plain host arithmetic."""
+    if exchange not in ("pbe", "revpbe"):
+        raise ValueError("exchange must be 'pbe' or 'revpbe'")
+    ex = semi["Ex_pbe"] if exchange == "pbe" else semi["Ex_revpbe"]
+    return E_tot_dft - semi["Ex_pbe"] - semi["Ec_pbe"] + (ex + semi["Ec_lda"] + E_c_nl)
 
 
 def potential(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", tuning=None,

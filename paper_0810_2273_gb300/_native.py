@@ -34,6 +34,14 @@ class vdwdf_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class vdwdf_semilocal_result(ctypes.Structure):
+    _fields_ = [("Ex_lda", _c_d), ("Ec_lda", _c_d), ("Ex_pbe", _c_d), ("Ec_pbe", _c_d),
+                ("Ex_revpbe", _c_d), ("n_points", _c_i64), ("ms", ctypes.c_float), ("launches", _c_i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class vdwdf_tuning(ctypes.Structure):
     _fields_ = [("threads", _c_i32), ("items_per_sm", _c_i32), ("smem_rows", _c_i32),
                 ("smem_row0", _c_i32)]
@@ -56,6 +64,8 @@ PROTOTYPES = {
     "vdwdf_energy_batched": (_c_i, [_c_i, ctypes.POINTER(vdwdf_grid), ctypes.POINTER(_c_p), _c_d, _c_d,
                                     _c_p, _c_i, ctypes.POINTER(vdwdf_tuning), _c_p,
                                     ctypes.POINTER(vdwdf_result), _c_p]),
+    "vdwdf_semilocal": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, ctypes.POINTER(vdwdf_semilocal_result),
+                               _c_p]),
     "vdwdf_energy_noalloc": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_d, _c_d, _c_p, _c_i,
                                     ctypes.POINTER(vdwdf_result), _c_p]),
     "vdwdf_autotune": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_d, _c_d, _c_p, _c_i,

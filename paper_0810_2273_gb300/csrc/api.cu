@@ -724,6 +724,41 @@ int vdwdf_q0(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev
                           static_cast<cudaStream_t>(cuda_stream));
 }
 
+int vdwdf_semilocal(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev,
+                    vdwdf_semilocal_result *out, void *cuda_stream) {
+    Geom G;
+    int rc = check_grid(grid, G);
+    if (rc) return rc;
+    if (!n_dev || !out) return VDWDF_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const long long launches0 = g_launches.load();
+    const size_t nd = static_cast<size_t>(semilocal_scratch_doubles());
+    double *scratch = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&scratch), nd * sizeof(double), st) != cudaSuccess)
+        return VDWDF_EALLOC;
+    Timer tm;
+    double sums[6] = {0, 0, 0, 0, 0, 0};
+    tm.mark(0, st);
+    rc = launch_semilocal(G.dims, G.h, n_dev, grad_dev, scratch, st);
+    tm.mark(1, st);
+    if (rc == VDWDF_OK &&
+        cudaMemcpyAsync(sums, scratch + nd - 6, sizeof(sums), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = VDWDF_ECUDA;
+    cudaFreeAsync(scratch, st);
+    if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
+    if (rc) return rc;
+    std::memset(out, 0, sizeof(*out));
+    out->Ex_lda = G.dV * sums[0];
+    out->Ec_lda = G.dV * sums[1];
+    out->Ex_pbe = G.dV * sums[2];
+    out->Ec_pbe = G.dV * sums[3];
+    out->Ex_revpbe = G.dV * sums[4];
+    out->n_points = static_cast<int64_t>(sums[5]);
+    out->ms = tm.ms(0, 1);
+    out->launches = static_cast<int32_t>(g_launches.load() - launches0);
+    return VDWDF_OK;
+}
+
 int vdwdf_energy(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
                  double r_cut, const vdwdf_table *table, int precision, const vdwdf_tuning *tuning,
                  vdwdf_result *out, void *cuda_stream) {

@@ -81,6 +81,12 @@ struct PairLaunch {
     PairParams inst[kMaxInst];
 };
 
+// Semilocal energies (LDA, PBE, revPBE): scratch of semilocal_scratch_doubles()
+// doubles; the last six hold Ex_lda, Ec_lda, Ex_pbe, Ec_pbe, Ex_revpbe (sums of
+// n eps, not yet times dV) and the number of points with n > 0.
+int semilocal_scratch_doubles();
+int launch_semilocal(const int dims[3], const double h[3], const double *n, const double *grad_in,
+                     double *scratch, cudaStream_t st);
 int launch_grad_q0(const int dims[3], const double h[3], const double *n, const double *grad_in,
                    double *q0, double *dq0dn, double *dq0dg, cudaStream_t st);
 int launch_compact(const int dims[3], const double *n, double n_cut, const double *q0,

@@ -40,6 +40,33 @@ __device__ __forceinline__ int wrap(int i, int n) {
     return i < 0 ? i + n : i;
 }
 
+// grad n at point m = (a, b, c): the caller's [3][N] gradient, or the 4th-order
+// periodic stencil on n.
+__device__ __forceinline__ void grad_at(long long m, int n0, int n1, int n2, double ih0, double ih1,
+                                        double ih2, const double *__restrict__ n,
+                                        const double *__restrict__ gin, double &gx, double &gy,
+                                        double &gz) {
+    const long long N = static_cast<long long>(n0) * n1 * n2;
+    if (gin) {
+        gx = gin[m];
+        gy = gin[N + m];
+        gz = gin[2 * N + m];
+        return;
+    }
+    const int c = static_cast<int>(m % n2);
+    const int b = static_cast<int>((m / n2) % n1);
+    const int a = static_cast<int>(m / (static_cast<long long>(n1) * n2));
+    const long long sa = static_cast<long long>(n1) * n2;
+    const long long row = m - static_cast<long long>(a) * sa;  // b * n2 + c
+    const long long pl = m - c;                                // (a, b, 0)
+    auto at_a = [&](int aa) { return n[static_cast<long long>(wrap(aa, n0)) * sa + row]; };
+    auto at_b = [&](int bb) { return n[static_cast<long long>(a) * sa + static_cast<long long>(wrap(bb, n1)) * n2 + c]; };
+    auto at_c = [&](int cc) { return n[pl + wrap(cc, n2)]; };
+    gx = (8.0 * (at_a(a + 1) - at_a(a - 1)) - (at_a(a + 2) - at_a(a - 2))) * (ih0 / 12.0);
+    gy = (8.0 * (at_b(b + 1) - at_b(b - 1)) - (at_b(b + 2) - at_b(b - 2))) * (ih1 / 12.0);
+    gz = (8.0 * (at_c(c + 1) - at_c(c - 1)) - (at_c(c + 2) - at_c(c - 2))) * (ih2 / 12.0);
+}
+
 __global__ void k_grad_q0(int n0, int n1, int n2, double ih0, double ih1, double ih2,
                           const double *__restrict__ n, const double *__restrict__ gin,
                           double *__restrict__ q0, double *__restrict__ qn, double *__restrict__ qg) {
@@ -47,25 +74,8 @@ __global__ void k_grad_q0(int n0, int n1, int n2, double ih0, double ih1, double
     const double Zab = -0.8491;
     for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < N;
          m += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int c = static_cast<int>(m % n2);
-        const int b = static_cast<int>((m / n2) % n1);
-        const int a = static_cast<int>(m / (static_cast<long long>(n1) * n2));
         double gx, gy, gz;
-        if (gin) {
-            gx = gin[m];
-            gy = gin[N + m];
-            gz = gin[2 * N + m];
-        } else {
-            const long long sa = static_cast<long long>(n1) * n2;
-            const long long row = m - static_cast<long long>(a) * sa;     // b * n2 + c
-            const long long pl = m - c;                                   // (a, b, 0)
-            auto at_a = [&](int aa) { return n[static_cast<long long>(wrap(aa, n0)) * sa + row]; };
-            auto at_b = [&](int bb) { return n[static_cast<long long>(a) * sa + static_cast<long long>(wrap(bb, n1)) * n2 + c]; };
-            auto at_c = [&](int cc) { return n[pl + wrap(cc, n2)]; };
-            gx = (8.0 * (at_a(a + 1) - at_a(a - 1)) - (at_a(a + 2) - at_a(a - 2))) * (ih0 / 12.0);
-            gy = (8.0 * (at_b(b + 1) - at_b(b - 1)) - (at_b(b + 2) - at_b(b - 2))) * (ih1 / 12.0);
-            gz = (8.0 * (at_c(c + 1) - at_c(c - 1)) - (at_c(c + 2) - at_c(c - 2))) * (ih2 / 12.0);
-        }
+        grad_at(m, n0, n1, n2, ih0, ih1, ih2, n, gin, gx, gy, gz);
         const double nn = n[m];
         if (!(nn > 0.0)) {
             q0[m] = 0.0;
@@ -247,7 +257,99 @@ __global__ void k_tiles(const float4 *__restrict__ p32, const double *__restrict
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Semilocal energies of eq. (3) (section 2: E_x^LDA, E_c^LDA, E_x^PBE, E_c^PBE
+// and E_x^revPBE from the density itself), spin-unpolarised, FP64:
+//   eps_x^LDA = -3 k_F/(4 pi);  GGA exchange eps_x^LDA F_x(s),
+//   F_x = 1 + kappa - kappa/(1 + mu s^2/kappa), s = |g|/(2 k_F n),
+//   kappa = 0.804 (PBE) or 1.245 (revPBE), mu = beta pi^2/3;
+//   eps_c^PBE = eps_c^PW92 + gamma ln[1 + (beta/gamma) t^2 (1 + A t^2)/(1 + A t^2 + A^2 t^4)],
+//   t = |g|/(2 k_s n), k_s = (4 k_F/pi)^(1/2), A = (beta/gamma)/(exp(-eps_c/gamma) - 1),
+//   beta = 0.06672455060314922, gamma = (1 - ln 2)/pi^2.
+// Each block sums n eps over its points (fixed grid-stride order, fixed tree);
+// a second kernel adds the block sums in order, so the result is reproducible.
+// ---------------------------------------------------------------------------
+constexpr int kSemiBlocks = 608;  // 4 per SM on 152 SMs
+constexpr int kSemiThreads = 256;
+constexpr int kSemiVals = 6;      // five energies and the point count
+
+__device__ __forceinline__ double gga_fx(double s2, double kappa, double mu) {
+    return 1.0 + kappa - kappa / (1.0 + mu * s2 / kappa);
+}
+
+__global__ void __launch_bounds__(kSemiThreads) k_semilocal(int n0, int n1, int n2, double ih0, double ih1,
+                                                            double ih2, const double *__restrict__ n,
+                                                            const double *__restrict__ gin,
+                                                            double *__restrict__ part) {
+    const long long N = static_cast<long long>(n0) * n1 * n2;
+    const double beta = 0.06672455060314922;
+    const double gamma = (1.0 - log(2.0)) / (kPi * kPi);
+    const double mu = beta * kPi * kPi / 3.0;
+    double acc[kSemiVals] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < N;
+         m += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double nn = n[m];
+        if (!(nn > 0.0)) continue;
+        double gx, gy, gz;
+        grad_at(m, n0, n1, n2, ih0, ih1, ih2, n, gin, gx, gy, gz);
+        const double g2 = gx * gx + gy * gy + gz * gz;
+        const double kF = cbrt(3.0 * kPi * kPi * nn);
+        const double rs = cbrt(3.0 / (4.0 * kPi * nn));
+        double ec, decdrs;
+        pw92_eps(rs, ec, decdrs);
+        const double ex = -3.0 * kF / (4.0 * kPi);
+        const double s2 = g2 / (4.0 * kF * kF * nn * nn);
+        const double ks2 = 4.0 * kF / kPi;
+        const double t2 = g2 / (4.0 * ks2 * nn * nn);
+        const double A = (beta / gamma) / expm1(-ec / gamma);
+        const double At2 = A * t2;
+        const double H = gamma * log1p((beta / gamma) * t2 * (1.0 + At2) / (1.0 + At2 + At2 * At2));
+        acc[0] += nn * ex;
+        acc[1] += nn * ec;
+        acc[2] += nn * ex * gga_fx(s2, 0.804, mu);
+        acc[3] += nn * (ec + H);
+        acc[4] += nn * ex * gga_fx(s2, 1.245, mu);
+        acc[5] += 1.0;
+    }
+    __shared__ double red[kSemiVals][kSemiThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kSemiVals; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kSemiVals) {
+        double v = 0.0;
+        for (int w = 0; w < kSemiThreads / 32; ++w) v += red[threadIdx.x][w];
+        part[static_cast<long long>(blockIdx.x) * kSemiVals + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_semilocal_sum(const double *__restrict__ part, int nblocks, double *__restrict__ out) {
+    if (threadIdx.x < kSemiVals) {
+        double v = 0.0;
+        for (int b = 0; b < nblocks; ++b) v += part[static_cast<long long>(b) * kSemiVals + threadIdx.x];
+        out[threadIdx.x] = v;
+    }
+}
+
 }  // namespace
+
+int semilocal_scratch_doubles() { return (kSemiBlocks + 1) * kSemiVals; }
+
+int launch_semilocal(const int dims[3], const double h[3], const double *n, const double *grad_in,
+                     double *scratch, cudaStream_t st) {
+    k_semilocal<<<kSemiBlocks, kSemiThreads, 0, st>>>(dims[0], dims[1], dims[2], 1.0 / h[0], 1.0 / h[1],
+                                                      1.0 / h[2], n, grad_in, scratch);
+    k_semilocal_sum<<<1, 32, 0, st>>>(scratch, kSemiBlocks, scratch + kSemiBlocks * kSemiVals);
+    count_launches(2);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
+}
 
 int launch_grad_q0(const int dims[3], const double h[3], const double *n, const double *grad_in,
                    double *q0, double *dq0dn, double *dq0dg, cudaStream_t st) {

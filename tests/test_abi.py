@@ -42,7 +42,7 @@ def test_struct_layouts_match_header(native, tmp_path):
     """ctypes structs vs the C compiler's layout of include/vdwdf.h."""
     import subprocess
     fields = {"vdwdf_grid": native.vdwdf_grid, "vdwdf_result": native.vdwdf_result,
-              "vdwdf_tuning": native.vdwdf_tuning}
+              "vdwdf_tuning": native.vdwdf_tuning, "vdwdf_semilocal_result": native.vdwdf_semilocal_result}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "vdwdf.h"', "int main(void) {"]
     for s, cls in fields.items():
         src.append('printf("%s size %%zu\\n", sizeof(%s));' % (s, s))
@@ -98,6 +98,14 @@ def test_host_side_argument_errors(native):
     # batched: bad count
     assert lib.vdwdf_energy_batched(0, None, None, 1e-6, 0.0, ctypes.c_void_p(1), 0, None, None, None,
                                     None) == -1
+    # semilocal energies: null density or result, non-orthorhombic cell
+    g.cell[0][1] = 0.0
+    sres = native.vdwdf_semilocal_result()
+    assert lib.vdwdf_semilocal(ctypes.byref(g), None, None, ctypes.byref(sres), None) == -1
+    assert lib.vdwdf_semilocal(ctypes.byref(g), ctypes.c_void_p(8), None, None, None) == -1
+    g.cell[0][1] = 1.0
+    assert lib.vdwdf_semilocal(ctypes.byref(g), ctypes.c_void_p(8), None, ctypes.byref(sres), None) == -2
+    g.cell[0][1] = 0.0
     # no-allocation energy: a grid larger than its static scratch holds is refused
     g.cell[0][1] = 0.0
     g.n[0], g.n[1], g.n[2] = 64, 64, 17
@@ -132,3 +140,17 @@ def test_table_roundtrip_from_nodes(tmp_path):
     T.save(p)
     T2 = Table.load(p)
     assert np.array_equal(T2.nodes, nodes) and T2.info() == (9, 12.0, 6)
+
+
+def test_total_energy_assembly():
+    """Eq. 3 with PBE exchange leaves E_tot^DFT - E_c^PBE + E_c^LDA + E_c^nl (the
+    correction printed as the "needed number" in the paper's sample output); with
+    revPBE exchange it adds E_x^revPBE - E_x^PBE on top."""
+    import paper_0810_2273_gb300 as V
+    semi = {"Ex_lda": -1.0, "Ec_lda": -0.30, "Ex_pbe": -1.10, "Ec_pbe": -0.20, "Ex_revpbe": -1.12}
+    E = V.total_energy_nl(-50.0, semi, 0.05)
+    assert E == pytest.approx(-50.0 - (-0.20) + (-0.30) + 0.05, abs=1e-15)
+    Er = V.total_energy_nl(-50.0, semi, 0.05, exchange="revpbe")
+    assert Er == pytest.approx(E + (-1.12) - (-1.10), abs=1e-15)
+    with pytest.raises(ValueError):
+        V.total_energy_nl(-50.0, semi, 0.05, exchange="lda")
