@@ -75,6 +75,13 @@ def lib():
         L.orc_eps_c.argtypes = [_i, _p, _p, _p]
         L.orc_q0.restype = _i
         L.orc_q0.argtypes = [_i, _p, _p, _p, _p, _p]
+        L.orc_pair_AU_cell.restype = _i
+        L.orc_pair_AU_cell.argtypes = ([_i, _p, _p, _p, _p, _p, _i, _i, _i, _p, _i, _i, _i, _d,
+                                        _i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p])
+        L.orc_gradient_cell.restype = _i
+        L.orc_gradient_cell.argtypes = [_i, _i, _i, _p, _p, _p]
+        L.orc_gradient_T_cell.restype = _i
+        L.orc_gradient_T_cell.argtypes = [_i, _i, _i, _p, _p, _p]
         L.orc_fx_many.restype = _i
         L.orc_fx_many.argtypes = [_i, _p, _d, _p]
         L.orc_pbe_H_many.restype = _i
@@ -239,6 +246,28 @@ def eps_c(rs):
     return e, de
 
 
+def gradient_cell(f, cell):
+    """Gradient on a general cell (rows of cell: lattice vectors, bohr): the
+    4th-order stencil along each grid axis gives df/du_a, and grad f =
+    sum_a (df/du_a) B_a with the reciprocal rows B_a.  Returns [3][...]."""
+    f = _f64(f)
+    cell = _f64(cell).reshape(3, 3)
+    g = np.zeros((3,) + f.shape)
+    if lib().orc_gradient_cell(*f.shape, _ptr(cell), _ptr(f), _ptr(g)) != 0:
+        raise ValueError("singular cell")
+    return g
+
+
+def gradient_T_cell(w, cell):
+    """Transpose of gradient_cell applied to w [3][...]."""
+    w = _f64(w)
+    cell = _f64(cell).reshape(3, 3)
+    out = np.zeros(w.shape[1:])
+    if lib().orc_gradient_T_cell(*w.shape[1:], _ptr(cell), _ptr(w), _ptr(out)) != 0:
+        raise ValueError("singular cell")
+    return out
+
+
 def q0(n, g):
     """q0 and its partials dq0/dn, dq0/dgrad n at every grid point."""
     n = _f64(n)
@@ -298,23 +327,36 @@ def semilocal(n, lengths, g=None):
 # The double sum and its adjoint (section 2 eq. 2; section 3)
 # --------------------------------------------------------------------------
 class Problem:
-    """A density on an orthorhombic periodic grid, trimmed at n_cut.
+    """A density on a periodic grid, trimmed at n_cut.
 
-    dims: (n0, n1, n2); lengths: (L0, L1, L2) bohr; periodic: 3 flags;
-    rc: spherical pair cutoff in bohr (<= 0: none; required if periodic).
+    dims: (n0, n1, n2); lengths: (L0, L1, L2) bohr of an orthorhombic cell, or
+    cell: 3x3 rows = lattice vectors (bohr) of a general cell (then lengths is
+    ignored); periodic: 3 flags; rc: spherical pair cutoff in bohr (<= 0: none;
+    required if periodic); g: the gradient [3][...] (Cartesian) to use instead
+    of the library-style stencil.
     """
 
-    def __init__(self, density, lengths, periodic, n_cut, rc, spline):
+    def __init__(self, density, lengths, periodic, n_cut, rc, spline, cell=None, g=None):
         self.n = _f64(density)
         self.dims = self.n.shape
-        self.lengths = tuple(float(x) for x in lengths)
         self.periodic = tuple(int(bool(p)) for p in periodic)
         self.n_cut = float(n_cut)
         self.rc = float(rc)
         self.spline = spline
-        self.h = tuple(L / d for L, d in zip(self.lengths, self.dims))
-        self.dV = float(np.prod(self.lengths)) / float(np.prod(self.dims))
-        self.g = gradient(self.n, self.h)
+        if cell is None:
+            self.cell = None
+            self.lengths = tuple(float(x) for x in lengths)
+            self.h = tuple(L / d for L, d in zip(self.lengths, self.dims))
+            self.dV = float(np.prod(self.lengths)) / float(np.prod(self.dims))
+        else:
+            self.cell = _f64(cell).reshape(3, 3)
+            self.lengths = None
+            self.h = None
+            self.dV = abs(float(np.linalg.det(self.cell))) / float(np.prod(self.dims))
+        if g is not None:
+            self.g = _f64(g).reshape((3,) + self.dims)
+        else:
+            self.g = gradient(self.n, self.h) if self.cell is None else gradient_cell(self.n, self.cell)
         self.q0, self.dq0dn, self.dq0dg = q0(self.n, self.g)
         flat = self.n.ravel()
         self.active = np.nonzero(flat >= self.n_cut)[0]          # row-major order
@@ -339,10 +381,16 @@ class Problem:
         npairs = np.zeros(len(qidx), dtype=np.int64)
         ncl = np.zeros(len(qidx), dtype=np.int64)
         s = self.spline
-        rc = lib().orc_pair_AU(self.n_active, _ptr(self.i0), _ptr(self.i1), _ptr(self.i2),
-                               _ptr(self.na), _ptr(self.qa), *self.dims, *self.lengths,
-                               *self.periodic, self.rc, *s._kargs(), len(qidx), _ptr(qidx),
-                               _ptr(A), _ptr(U), _ptr(npairs), _ptr(ncl))
+        if self.cell is None:
+            rc = lib().orc_pair_AU(self.n_active, _ptr(self.i0), _ptr(self.i1), _ptr(self.i2),
+                                   _ptr(self.na), _ptr(self.qa), *self.dims, *self.lengths,
+                                   *self.periodic, self.rc, *s._kargs(), len(qidx), _ptr(qidx),
+                                   _ptr(A), _ptr(U), _ptr(npairs), _ptr(ncl))
+        else:
+            rc = lib().orc_pair_AU_cell(self.n_active, _ptr(self.i0), _ptr(self.i1), _ptr(self.i2),
+                                        _ptr(self.na), _ptr(self.qa), *self.dims, _ptr(self.cell),
+                                        *self.periodic, self.rc, *s._kargs(), len(qidx), _ptr(qidx),
+                                        _ptr(A), _ptr(U), _ptr(npairs), _ptr(ncl))
         if rc != 0:
             raise RuntimeError("orc_pair_AU failed (%d)" % rc)
         return A, U, npairs, ncl
@@ -366,7 +414,10 @@ class Problem:
         Ag[self.active] = A
         Ug[self.active] = U
         w = self.dq0dg.reshape(3, -1) * Ug[None, :]
-        div = gradient_T(w.reshape((3,) + self.dims), self.h).ravel()
+        if self.cell is None:
+            div = gradient_T(w.reshape((3,) + self.dims), self.h).ravel()
+        else:
+            div = gradient_T_cell(w.reshape((3,) + self.dims), self.cell).ravel()
         chi = np.zeros(flat_n)
         chi[self.active] = 1.0
         v = self.dV * (chi * (Ag + Ug * self.dq0dn.ravel()) + div)
@@ -395,6 +446,12 @@ class Problem:
         out = np.zeros(len(points))
         qn = self.dq0dn.ravel()
         qg = self.dq0dg.reshape(3, -1)
+        # (D_ax^T applied to (B_ax . w)), B_ax the reciprocal row scaled by N_ax; on an
+        # orthorhombic cell B_ax . w = w_ax / L_ax and N_ax / L_ax = 1 / h_ax
+        if self.cell is None:
+            Bs = np.diag([1.0 / h for h in self.h])
+        else:
+            Bs = np.linalg.inv(self.cell).T * np.array(d, dtype=float)[:, None]
         for t, (m, c) in enumerate(zip(points, coords)):
             val = 0.0
             s = int(self.slot[m])
@@ -408,7 +465,7 @@ class Problem:
                     mm = int(np.ravel_multi_index(cc, d))
                     ss = int(self.slot[mm])
                     if ss >= 0:
-                        val += c4[o + 2] * Umap[ss] * qg[ax, mm] / self.h[ax]
+                        val += c4[o + 2] * Umap[ss] * float(np.dot(Bs[ax], qg[:, mm]))
             out[t] = self.dV * val
         return out
 

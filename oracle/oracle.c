@@ -36,6 +36,11 @@
  *   orc_pbe_H_many                  exchange energies on the grid, uniform
  *                                   density (GGA = LDA), enhancement-factor
  *                                   and gradient-correction limits
+ *   orc_pair_AU_cell,               pinned: equals the orthogonal code on
+ *   orc_gradient_cell,              diagonal cells, lattice-basis and rotation
+ *   orc_gradient_T_cell             invariance of E, exact Fourier symbol of
+ *                                   the skewed gradient, adjoint identity,
+ *                                   brute-force pair counts
  *   paper-level energies            parity unpinned: the paper's Xe density
  *                                   file is not available
  */
@@ -858,5 +863,154 @@ int orc_semilocal(int N, const double *n, const double *g, double *sums, int64_t
     }
     for (int k = 0; k < 5; ++k) sums[k] = S[k];
     *count = c;
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* General cells (section 2: the grid axes need not be orthogonal; the     */
+/* paper's Xe monolayer cell is hexagonal).  Rows of cell[9] are the       */
+/* lattice vectors M_0, M_1, M_2 (bohr); grid point (i_0, i_1, i_2) sits at */
+/* r = sum_a (i_a / N_a) M_a, images are L = sum_a m_a M_a over the        */
+/* periodic axes.  Reciprocal rows B_a with B_a . M_b = delta_ab.          */
+/* ---------------------------------------------------------------------- */
+static int cell_recip(const double *M, double *B)
+{
+    /* B = (M^{-1})^T: B_a = (M_b x M_c) / det, (a, b, c) cyclic */
+    double det = M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                 M[2] * (M[3] * M[7] - M[4] * M[6]);
+    if (!(fabs(det) > 0.0)) return -1;
+    for (int a = 0; a < 3; ++a) {
+        const double *u = M + 3 * ((a + 1) % 3), *v = M + 3 * ((a + 2) % 3);
+        B[3 * a + 0] = (u[1] * v[2] - u[2] * v[1]) / det;
+        B[3 * a + 1] = (u[2] * v[0] - u[0] * v[2]) / det;
+        B[3 * a + 2] = (u[0] * v[1] - u[1] * v[0]) / det;
+    }
+    return 0;
+}
+
+/* The pair sum of orc_pair_AU for a general cell.  Image range per periodic
+ * axis: every L with |r_i - r_j + L| <= rc has |m_a| <= rc |B_a| + 1, since
+ * the fractional coordinate of a vector r along a is r . B_a and that of
+ * r_i - r_j lies in (-1, 1). */
+int orc_pair_AU_cell(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2,
+                     const double *n, const double *q, int n0, int n1, int n2, const double *cell,
+                     int per0, int per1, int per2, double rc,
+                     int nD, double hD, int nd, double hd, const double *f,
+                     const double *fDD, const double *fdd, const double *fDDdd,
+                     const double *rho, const double *rhoM,
+                     int nq, const int32_t *qidx, double *A, double *U,
+                     int64_t *npairs, int64_t *nclamp)
+{
+    if ((per0 || per1 || per2) && !(rc > 0.0)) return -1;
+    double B[9];
+    if (cell_recip(cell, B)) return -1;
+    orc_spline s = {nD, nd, hD, hd, f, fDD, fdd, fDDdd, rho, rhoM};
+    double Dmax = (nD - 1) * hD;
+    int per[3] = {per0, per1, per2};
+    int Mx[3];
+    for (int a = 0; a < 3; ++a) {
+        double bl = sqrt(B[3 * a] * B[3 * a] + B[3 * a + 1] * B[3 * a + 1] + B[3 * a + 2] * B[3 * a + 2]);
+        Mx[a] = per[a] ? (int)ceil(rc * bl) + 1 : 0;
+    }
+    int N[3] = {n0, n1, n2};
+    double phi00 = f[0];
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int t = 0; t < nq; ++t) {
+        int i = qidx[t];
+        double ri[3], a_ = 0.0, u_ = 0.0;
+        int64_t cnt = 0;
+        int cl = 0;
+        int ii[3] = {i0[i], i1[i], i2[i]};
+        for (int c = 0; c < 3; ++c)
+            ri[c] = ii[0] / (double)N[0] * cell[c] + ii[1] / (double)N[1] * cell[3 + c] +
+                    ii[2] / (double)N[2] * cell[6 + c];
+        for (int j = 0; j < Na; ++j) {
+            int jj[3] = {i0[j], i1[j], i2[j]};
+            double rj[3];
+            for (int c = 0; c < 3; ++c)
+                rj[c] = jj[0] / (double)N[0] * cell[c] + jj[1] / (double)N[1] * cell[3 + c] +
+                        jj[2] / (double)N[2] * cell[6 + c];
+            for (int m0 = -Mx[0]; m0 <= Mx[0]; ++m0)
+                for (int m1 = -Mx[1]; m1 <= Mx[1]; ++m1)
+                    for (int m2 = -Mx[2]; m2 <= Mx[2]; ++m2) {
+                        if (j == i && m0 == 0 && m1 == 0 && m2 == 0) {
+                            a_ += n[i] * phi00;
+                            continue;
+                        }
+                        double d[3];
+                        for (int c = 0; c < 3; ++c)
+                            d[c] = ri[c] - rj[c] + m0 * cell[c] + m1 * cell[3 + c] + m2 * cell[6 + c];
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (rc > 0.0 && r2 > rc * rc * (1.0 + 1e-12)) continue;
+                        double p, rd;
+                        kernel_pair(&s, Dmax, sqrt(r2), q[i], q[j], &p, &rd, &cl);
+                        a_ += n[j] * p;
+                        u_ += n[j] * rd;
+                        ++cnt;
+                    }
+        }
+        A[t] = a_;
+        U[t] = n[i] * u_;
+        if (npairs) npairs[t] = cnt;
+        if (nclamp) nclamp[t] = cl;
+    }
+    return 0;
+}
+
+/* Gradient on a general cell: the 4th-order central difference along grid
+ * axis a gives df/du_a (u_a = i_a / N_a, the fractional coordinate), and
+ * grad f = sum_a (df/du_a) B_a.  g is [3][N], Cartesian. */
+int orc_gradient_cell(int n0, int n1, int n2, const double *cell, const double *f, double *g)
+{
+    double B[9];
+    if (cell_recip(cell, B)) return -1;
+    size_t N = (size_t)n0 * n1 * n2;
+    int dims[3] = {n0, n1, n2};
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int a = 0; a < n0; ++a)
+        for (int b = 0; b < n1; ++b)
+            for (int c = 0; c < n2; ++c) {
+                int idx[3] = {a, b, c};
+                size_t m = ((size_t)a * n1 + b) * n2 + c;
+                double du[3];
+                for (int ax = 0; ax < 3; ++ax) {
+                    double s = 0.0;
+                    for (int o = -2; o <= 2; ++o) {
+                        int jj[3] = {idx[0], idx[1], idx[2]};
+                        jj[ax] = ((idx[ax] + o) % dims[ax] + dims[ax]) % dims[ax];
+                        s += orc_fd_c[o + 2] * f[((size_t)jj[0] * n1 + jj[1]) * n2 + jj[2]];
+                    }
+                    du[ax] = s * dims[ax];
+                }
+                for (int k = 0; k < 3; ++k) g[k * N + m] = du[0] * B[k] + du[1] * B[3 + k] + du[2] * B[6 + k];
+            }
+    return 0;
+}
+
+/* The transpose of orc_gradient_cell: out = sum_a D_a^T (sum_k B_a[k] w_k),
+ * D_a the index stencil times N_a; w is [3][N], Cartesian. */
+int orc_gradient_T_cell(int n0, int n1, int n2, const double *cell, const double *w, double *out)
+{
+    double B[9];
+    if (cell_recip(cell, B)) return -1;
+    size_t N = (size_t)n0 * n1 * n2;
+    int dims[3] = {n0, n1, n2};
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int a = 0; a < n0; ++a)
+        for (int b = 0; b < n1; ++b)
+            for (int c = 0; c < n2; ++c) {
+                int idx[3] = {a, b, c};
+                size_t m = ((size_t)a * n1 + b) * n2 + c;
+                double s = 0.0;
+                for (int ax = 0; ax < 3; ++ax)
+                    for (int o = -2; o <= 2; ++o) {
+                        int jj[3] = {idx[0], idx[1], idx[2]};
+                        jj[ax] = ((idx[ax] - o) % dims[ax] + dims[ax]) % dims[ax];
+                        size_t mm = ((size_t)jj[0] * n1 + jj[1]) * n2 + jj[2];
+                        double wa = B[3 * ax] * w[mm] + B[3 * ax + 1] * w[N + mm] + B[3 * ax + 2] * w[2 * N + mm];
+                        s += orc_fd_c[o + 2] * dims[ax] * wa;
+                    }
+                out[m] = s;
+            }
     return 0;
 }
