@@ -30,8 +30,13 @@
  *    returning; the others return without waiting.
  *  - Scratch device memory is taken with cudaMallocAsync on the call's stream
  *    and freed on it before return; the library owns it.
- *  - Only orthorhombic cells (diagonal cell matrix) are accepted by the GPU
- *    path (VDWDF_EUNSUPPORTED otherwise).
+ *  - Cells: the rows of vdwdf_grid.cell are the lattice vectors M_0, M_1,
+ *    M_2 (section 2: equidistant grid, axes need not be orthogonal); grid
+ *    point (i_0, i_1, i_2) sits at sum_a (i_a / n_a) M_a.  A singular cell is
+ *    VDWDF_EINVAL.  On a non-diagonal cell the finite differences along each
+ *    grid axis give d/du_a (u_a = i_a / n_a) and grad n = sum_a (d/du_a) B_a,
+ *    with B_a the reciprocal rows (B_a . M_b = delta_ab); the pair sum uses
+ *    the full metric.
  */
 #ifndef VDWDF_H
 #define VDWDF_H
@@ -47,7 +52,7 @@ extern "C" {
 /* status codes */
 #define VDWDF_OK 0
 #define VDWDF_EINVAL (-1)        /* bad argument: null pointer, size, value   */
-#define VDWDF_EUNSUPPORTED (-2)  /* valid but not implemented (non-orthorhombic cell) */
+#define VDWDF_EUNSUPPORTED (-2)  /* valid, but beyond what the entry point supports */
 #define VDWDF_ECUDA (-3)         /* a CUDA runtime call failed                */
 #define VDWDF_EALLOC (-4)        /* host or device allocation failed          */
 #define VDWDF_ETIMEOUT (-5)      /* a device-side work loop hit its iteration cap */
@@ -235,8 +240,7 @@ typedef struct {
  *   E = dV sum of n eps over every grid point with n > 0 (no density cutoff).
  * grad_dev as in vdwdf_q0.  The sum is reproducible: fixed blocks, fixed order.
  * Synchronises the stream.
- * Errors: VDWDF_EINVAL, VDWDF_EUNSUPPORTED (non-orthorhombic cell),
- * VDWDF_ECUDA, VDWDF_EALLOC. */
+ * Errors: VDWDF_EINVAL, VDWDF_ECUDA, VDWDF_EALLOC. */
 int vdwdf_semilocal(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev,
                     vdwdf_semilocal_result *out, void *cuda_stream);
 

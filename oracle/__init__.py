@@ -304,19 +304,26 @@ def pbe_H(rs, t):
     return out
 
 
-def semilocal(n, lengths, g=None):
+def semilocal(n, lengths, g=None, cell=None):
     """E_x^LDA, E_c^LDA (PW92), E_x^PBE, E_c^PBE, E_x^revPBE (Hartree) of the density
-    n on an orthorhombic grid of the given cell lengths, summed over points with
-    n > 0; g: [3][n0][n1][n2] gradient, or None for the 4th-order periodic stencil."""
+    n on an orthorhombic grid of the given cell lengths (or on the general cell
+    ``cell``, rows = lattice vectors), summed over points with n > 0;
+    g: [3][n0][n1][n2] Cartesian gradient, or None for the 4th-order stencil."""
     n = _f64(n)
-    h = [float(L) / d for L, d in zip(lengths, n.shape)]
-    if g is None:
-        g = gradient(n, h)
+    if cell is not None:
+        cell = _f64(cell).reshape(3, 3)
+        if g is None:
+            g = gradient_cell(n, cell)
+        dV = abs(float(np.linalg.det(cell))) / n.size
+    else:
+        h = [float(L) / d for L, d in zip(lengths, n.shape)]
+        if g is None:
+            g = gradient(n, h)
+        dV = h[0] * h[1] * h[2]
     g = _f64(g).reshape((3,) + n.shape)
     sums = np.zeros(5)
     count = ctypes.c_int64()
     lib().orc_semilocal(n.size, _ptr(n), _ptr(g), _ptr(sums), ctypes.byref(count))
-    dV = h[0] * h[1] * h[2]
     keys = ("Ex_lda", "Ec_lda", "Ex_pbe", "Ec_pbe", "Ex_revpbe")
     out = {k: dV * v for k, v in zip(keys, sums)}
     out["n_points"] = count.value

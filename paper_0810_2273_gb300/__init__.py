@@ -99,11 +99,16 @@ class Table:
 
 
 def grid(lengths, dims, periodic=(False, False, False)):
-    """vdwdf_grid for an orthorhombic cell lengths[0] x lengths[1] x lengths[2] bohr."""
+    """vdwdf_grid for an orthorhombic cell lengths[0] x lengths[1] x lengths[2] bohr, or,
+    when ``lengths`` is 3x3, for the general cell whose rows are the lattice vectors."""
     g = vdwdf_grid()
+    cell = np.asarray(lengths, dtype=np.float64)
     for a in range(3):
         for b in range(3):
-            g.cell[a][b] = float(lengths[a]) if a == b else 0.0
+            if cell.shape == (3, 3):
+                g.cell[a][b] = float(cell[a, b])
+            else:
+                g.cell[a][b] = float(cell[a]) if a == b else 0.0
         g.n[a] = int(dims[a])
         g.periodic[a] = 1 if periodic[a] else 0
     return g

@@ -141,37 +141,83 @@ int sm_count() {
 struct Geom {
     int dims[3];
     int per[3];
-    double L[3], h[3];
+    double L[3], h[3];  // |M_a| and |M_a| / N_a
     double dV;
     long long N;
     int M[3];
     double rc;
     bool use_cut;
+    double B[9];        // reciprocal rows: B_a . M_b = delta_ab
+    double met[6];      // metric in index units: 00, 11, 22, 01, 02, 12
+    double lmin;        // its smallest eigenvalue
+    bool skew;          // non-diagonal metric
+    AxisMap am;         // grid-axis derivatives to Cartesian gradient
 };
+
+// Smallest eigenvalue of the symmetric 3x3 matrix (a00, a11, a22, a01, a02, a12)
+// (trigonometric solution of the characteristic cubic).
+double sym3_min_eig(const double m[6]) {
+    const double p1 = m[3] * m[3] + m[4] * m[4] + m[5] * m[5];
+    if (p1 == 0.0) return std::min(m[0], std::min(m[1], m[2]));
+    const double q = (m[0] + m[1] + m[2]) / 3.0;
+    const double p2 = (m[0] - q) * (m[0] - q) + (m[1] - q) * (m[1] - q) + (m[2] - q) * (m[2] - q) + 2.0 * p1;
+    const double p = std::sqrt(p2 / 6.0);
+    const double b00 = (m[0] - q) / p, b11 = (m[1] - q) / p, b22 = (m[2] - q) / p;
+    const double b01 = m[3] / p, b02 = m[4] / p, b12 = m[5] / p;
+    const double detB = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
+    const double r = std::max(-1.0, std::min(1.0, detB / 2.0));
+    const double phi = std::acos(r) / 3.0;
+    return q + 2.0 * p * std::cos(phi + 2.0 * kPi / 3.0);
+}
 
 int check_grid(const vdwdf_grid *g, Geom &G) {
     if (!g) return VDWDF_EINVAL;
     long long N = 1;
+    const double(*M)[3] = g->cell;
     for (int a = 0; a < 3; ++a) {
         if (g->n[a] < 1 || g->n[a] > (1 << 20)) return VDWDF_EINVAL;
         if (g->periodic[a] != 0 && g->periodic[a] != 1) return VDWDF_EINVAL;
         N *= g->n[a];
-        for (int b = 0; b < 3; ++b) {
-            const double v = g->cell[a][b];
-            if (!std::isfinite(v)) return VDWDF_EINVAL;
-            if (a != b && v != 0.0) return VDWDF_EUNSUPPORTED;
-        }
-        if (!(g->cell[a][a] > 0.0)) return VDWDF_EINVAL;
+        for (int b = 0; b < 3; ++b)
+            if (!std::isfinite(M[a][b])) return VDWDF_EINVAL;
     }
     if (N > (1LL << 31) - 1) return VDWDF_EINVAL;
+    const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                       M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                       M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return VDWDF_EINVAL;
+    bool diagonal = true;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (a != b && M[a][b] != 0.0) diagonal = false;
+    if (diagonal)
+        for (int a = 0; a < 3; ++a)
+            if (!(M[a][a] > 0.0)) return VDWDF_EINVAL;
     for (int a = 0; a < 3; ++a) {
         G.dims[a] = g->n[a];
         G.per[a] = g->periodic[a];
-        G.L[a] = g->cell[a][a];
+        G.L[a] = diagonal ? M[a][a] : std::sqrt(M[a][0] * M[a][0] + M[a][1] * M[a][1] + M[a][2] * M[a][2]);
         G.h[a] = G.L[a] / g->n[a];
+        // B_a = (M_b x M_c) / det, (a, b, c) cyclic
+        const double *u = M[(a + 1) % 3], *v = M[(a + 2) % 3];
+        G.B[3 * a + 0] = (u[1] * v[2] - u[2] * v[1]) / det;
+        G.B[3 * a + 1] = (u[2] * v[0] - u[0] * v[2]) / det;
+        G.B[3 * a + 2] = (u[0] * v[1] - u[1] * v[0]) / det;
     }
     G.N = N;
-    G.dV = G.L[0] * G.L[1] * G.L[2] / static_cast<double>(N);
+    G.dV = diagonal ? G.L[0] * G.L[1] * G.L[2] / static_cast<double>(N) : std::fabs(det) / static_cast<double>(N);
+    auto dot = [&](int a, int b) { return M[a][0] * M[b][0] + M[a][1] * M[b][1] + M[a][2] * M[b][2]; };
+    for (int a = 0; a < 3; ++a) G.met[a] = diagonal ? G.h[a] * G.h[a] : dot(a, a) / (double(G.dims[a]) * G.dims[a]);
+    G.met[3] = diagonal ? 0.0 : dot(0, 1) / (double(G.dims[0]) * G.dims[1]);
+    G.met[4] = diagonal ? 0.0 : dot(0, 2) / (double(G.dims[0]) * G.dims[2]);
+    G.met[5] = diagonal ? 0.0 : dot(1, 2) / (double(G.dims[1]) * G.dims[2]);
+    G.skew = G.met[3] != 0.0 || G.met[4] != 0.0 || G.met[5] != 0.0;
+    G.lmin = sym3_min_eig(G.met);
+    if (!(G.lmin > 0.0)) return VDWDF_EINVAL;
+    G.am.general = diagonal ? 0 : 1;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c)
+            G.am.S[3 * a + c] = diagonal ? (a == c ? (1.0 / G.h[a]) / 12.0 : 0.0) : G.dims[a] * G.B[3 * a + c] / 12.0;
     return VDWDF_OK;
 }
 
@@ -183,7 +229,11 @@ int check_cut(double n_cut, double r_cut, Geom &G) {
     G.use_cut = r_cut > 0.0;
     G.rc = G.use_cut ? r_cut : 0.0;
     for (int a = 0; a < 3; ++a) {
-        G.M[a] = G.per[a] ? static_cast<int>(std::ceil(r_cut / G.L[a])) + 1 : 0;
+        // every image L with |r_i - r_j + L| <= r_cut has |m_a| <= r_cut |B_a| + 1
+        const double bl = std::sqrt(G.B[3 * a] * G.B[3 * a] + G.B[3 * a + 1] * G.B[3 * a + 1] +
+                                    G.B[3 * a + 2] * G.B[3 * a + 2]);
+        const double ext = G.skew ? r_cut * bl : r_cut / G.L[a];
+        G.M[a] = G.per[a] ? static_cast<int>(std::ceil(ext)) + 1 : 0;
         if (G.M[a] > kMaxImages) return VDWDF_EINVAL;
     }
     return VDWDF_OK;
@@ -273,19 +323,28 @@ int prepare(const Geom &G, const double *n_dev, const double *grad_dev, double n
     if (rc) return rc;
     rc = reset_stats(w.stats, st);
     if (rc) return rc;
-    rc = launch_grad_q0(G.dims, G.h, n_dev, grad_dev, w.q0, w.qn, w.qg, st);
+    rc = launch_grad_q0(G.dims, G.am, n_dev, grad_dev, w.q0, w.qn, w.qg, st);
     if (rc) return rc;
     return launch_compact(G.dims, n_dev, n_cut, w.q0, order, nb, w.cnt, w.off, pot ? w.slot : nullptr,
                           w.p32, w.n32, w.p64, w.n64, w.blo, w.bhi, w.stats, st);
 }
 
 void fill_params(const Geom &G, const Work &w, PairParams &pp) {
+    pp.rc2 = G.rc * G.rc * (1.0 + 1e-12);  // inclusive cutoff, rounding ties inside
     for (int a = 0; a < 3; ++a) {
-        pp.h2[a] = G.h[a] * G.h[a];
+        pp.h2[a] = G.met[a];
+        pp.g2x[a] = 2.0 * G.met[3 + a];
         pp.dims[a] = G.dims[a];
         pp.M[a] = G.M[a];
+        // culling: exact per-axis metric on orthogonal cells, its smallest eigenvalue
+        // (a lower bound of r^2 / |d|^2) on skewed ones; the cutoff's extent in index
+        // units along a is r_cut sqrt(1/h2) or r_cut |B_a| N_a
+        pp.cull_h2[a] = static_cast<float>(G.skew ? G.lmin : G.met[a]);
+        const double bl = std::sqrt(G.B[3 * a] * G.B[3 * a] + G.B[3 * a + 1] * G.B[3 * a + 1] +
+                                    G.B[3 * a + 2] * G.B[3 * a + 2]);
+        const double ext = G.skew ? std::sqrt(pp.rc2) * bl * G.dims[a] : std::sqrt(pp.rc2 / G.met[a]);
+        pp.rcm[a] = G.use_cut ? static_cast<float>(ext) * 1.0001f + 1e-3f : 0.0f;
     }
-    pp.rc2 = G.rc * G.rc * (1.0 + 1e-12);  // inclusive cutoff, rounding ties inside
     pp.use_cut = G.use_cut ? 1 : 0;
     pp.p32 = w.p32;
     pp.n32 = w.n32;
@@ -349,11 +408,11 @@ void fill_shared(const vdwdf_table *t, const double *d64, const float *d32, cons
 }
 
 Launch choose_launch(int precision, bool pot, const vdwdf_tuning *tu, const vdwdf_table *t,
-                     long long n_active) {
+                     long long n_active, bool skew) {
     Launch ln;
     const int S = t->nd + 2;
-    if (tu && (tu->threads == 256 || tu->threads == 384 || tu->threads == 512 || tu->threads == 1024))
-        ln.threads = tu->threads;
+    if (!skew && tu && (tu->threads == 256 || tu->threads == 384 || tu->threads == 512 || tu->threads == 1024))
+        ln.threads = tu->threads;  // skewed cells: the 512-thread kernel only
     const int sms = sm_count();
     ln.nctas = sms * ctas_per_sm(precision, pot, ln.threads, 0, S);
     // work items are (tile of kTile i points) x (jt j tiles); aim at ipsm items per
@@ -458,7 +517,7 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
             VDWDF_CUDA_TRY(cudaMemsetAsync(w.U, 0, sizeof(double) * G.N, st));
         }
         if (hs.n_active > 0) {
-            Launch ln = choose_launch(precision, pot, tu, table, hs.n_active);
+            Launch ln = choose_launch(precision, pot, tu, table, hs.n_active, G.skew);
             VDWDF_CUDA_TRY(cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st));
             PairLaunch pl;
             std::memset(&pl, 0, sizeof(pl));
@@ -474,14 +533,14 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
             }
             pl.ninst = 1;
             fill_params(G, w, pl.inst[0]);
-            r = launch_pair(precision, pot, ln.threads, pl, ln.nctas, st);
+            r = launch_pair(precision, pot, G.skew, ln.threads, pl, ln.nctas, st);
             if (r) return r;
             r = launch_reduce_items(pl, st);
             if (r) return r;
         }
         tm.mark(2, st);
         if (pot) {
-            r = launch_assemble(G.dims, G.h, G.dV, w.slot, w.A, w.U, w.qn, w.qg, v_dev, A_grid, U_grid, st);
+            r = launch_assemble(G.dims, G.am, G.dV, w.slot, w.A, w.U, w.qn, w.qg, v_dev, A_grid, U_grid, st);
             if (r) return r;
             r = launch_energy_from_A(static_cast<int>(G.N), w.A, w.n64, w.stats, st);
             if (r) return r;
@@ -555,7 +614,9 @@ int record_batch(BatchPlan &bp, int ninst, const double *const *n_dev, double n_
         const int k0 = g * kMaxInst, k1 = std::min(ninst, k0 + kMaxInst);
         long long gsum = 0;
         for (int k = k0; k < k1; ++k) gsum += bp.geo[k].N;
-        Launch ln = choose_launch(precision, false, tu, table, std::max<long long>(1, gsum / (k1 - k0)));
+        bool gskew = false;
+        for (int k = k0; k < k1; ++k) gskew = gskew || bp.geo[k].skew;
+        Launch ln = choose_launch(precision, false, tu, table, std::max<long long>(1, gsum / (k1 - k0)), gskew);
         VDWDF_CUDA_TRY(cudaMemsetAsync(bp.queues + g, 0, sizeof(unsigned int), st));
         PairLaunch pl;
         std::memset(&pl, 0, sizeof(pl));
@@ -566,8 +627,12 @@ int record_batch(BatchPlan &bp, int ninst, const double *const *n_dev, double n_
         pl.sh.item_E = bp.item_bufs[g];
         pl.sh.item_cap = static_cast<unsigned int>(bp.item_caps[g]);
         pl.ninst = k1 - k0;
-        for (int k = k0; k < k1; ++k) fill_params(bp.geo[k], bp.work[k], pl.inst[k - k0]);
-        int rc = launch_pair(precision, false, ln.threads, pl, ln.nctas, st);
+        bool skew = false;
+        for (int k = k0; k < k1; ++k) {
+            fill_params(bp.geo[k], bp.work[k], pl.inst[k - k0]);
+            skew = skew || bp.geo[k].skew;
+        }
+        int rc = launch_pair(precision, false, skew, ln.threads, pl, ln.nctas, st);
         if (rc) return rc;
         rc = launch_reduce_items(pl, st);
         if (rc) return rc;
@@ -720,7 +785,7 @@ int vdwdf_q0(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev
     int rc = check_grid(grid, G);
     if (rc) return rc;
     if (!n_dev || !q0_dev) return VDWDF_EINVAL;
-    return launch_grad_q0(G.dims, G.h, n_dev, grad_dev, q0_dev, dq0dn_dev, dq0dg_dev,
+    return launch_grad_q0(G.dims, G.am, n_dev, grad_dev, q0_dev, dq0dn_dev, dq0dg_dev,
                           static_cast<cudaStream_t>(cuda_stream));
 }
 
@@ -739,7 +804,7 @@ int vdwdf_semilocal(const vdwdf_grid *grid, const double *n_dev, const double *g
     Timer tm;
     double sums[6] = {0, 0, 0, 0, 0, 0};
     tm.mark(0, st);
-    rc = launch_semilocal(G.dims, G.h, n_dev, grad_dev, scratch, st);
+    rc = launch_semilocal(G.dims, G.am, n_dev, grad_dev, scratch, st);
     tm.mark(1, st);
     if (rc == VDWDF_OK &&
         cudaMemcpyAsync(sums, scratch + nd - 6, sizeof(sums), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -857,8 +922,12 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
         for (int g = 0; g < ngroups; ++g) {
             const int k0 = g * kMaxInst, k1 = std::min(ninst, k0 + kMaxInst);
             long long gsum = 0;
-            for (int k = k0; k < k1; ++k) gsum += geo[k].N;
-            const Launch ln = choose_launch(precision, false, tuning, table, std::max<long long>(1, gsum / (k1 - k0)));
+            bool gskew = false;
+            for (int k = k0; k < k1; ++k) {
+                gsum += geo[k].N;
+                gskew = gskew || geo[k].skew;
+            }
+            const Launch ln = choose_launch(precision, false, tuning, table, std::max<long long>(1, gsum / (k1 - k0)), gskew);
             long long items = 0;
             for (int k = k0; k < k1; ++k) items += pair_items(geo[k].N, ln.jt);
             double *b = nullptr;
@@ -965,7 +1034,7 @@ int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, do
     Timer tm;
     for (int ci = 0; ci < kCand && rc == VDWDF_OK && hs.n_active > 0; ++ci) {
         if (fp64 && cand[ci].smem_rows != 0) continue;
-        Launch ln = choose_launch(precision, false, &cand[ci], table, hs.n_active);
+        Launch ln = choose_launch(precision, false, &cand[ci], table, hs.n_active, G.skew);
         for (int rep = 0; rep < 2 && rc == VDWDF_OK; ++rep) {
             if (cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st) != cudaSuccess) rc = VDWDF_ECUDA;
             Stats zero;
@@ -981,7 +1050,7 @@ int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, do
             pl.ninst = 1;
             fill_params(G, w, pl.inst[0]);
             tm.mark(0, st);
-            if (rc == VDWDF_OK) rc = launch_pair(precision, false, ln.threads, pl, ln.nctas, st);
+            if (rc == VDWDF_OK) rc = launch_pair(precision, false, G.skew, ln.threads, pl, ln.nctas, st);
             tm.mark(1, st);
             Stats out;
             if (rc == VDWDF_OK &&
@@ -1126,7 +1195,7 @@ int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const doub
     if (rc) return rc;
     rc = reset_stats(w.stats, st);  // counters start at zero (q0 minimum above all floats)
     if (rc) return rc;
-    rc = launch_grad_q0(G.dims, G.h, n_dev, grad_dev, w.q0, w.qn, w.qg, st);
+    rc = launch_grad_q0(G.dims, G.am, n_dev, grad_dev, w.q0, w.qn, w.qg, st);
     if (rc) return rc;
     rc = launch_compact(G.dims, n_dev, n_cut, w.q0, order_dev, nb, w.cnt, w.off, nullptr, w.p32, w.n32,
                         w.p64, w.n64, w.blo, w.bhi, w.stats, st);
@@ -1136,7 +1205,7 @@ int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const doub
     VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
     VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
     if (hs.n_active > 0) {
-        Launch ln = choose_launch(precision, false, nullptr, table, hs.n_active);
+        Launch ln = choose_launch(precision, false, nullptr, table, hs.n_active, G.skew);
         VDWDF_CUDA_TRY(cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st));  // work-queue head
         PairLaunch pl;
         std::memset(&pl, 0, sizeof(pl));
@@ -1148,7 +1217,7 @@ int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const doub
         pl.sh.item_cap = static_cast<unsigned int>(std::min<long long>(items, item_space));
         pl.ninst = 1;
         fill_params(G, w, pl.inst[0]);
-        rc = launch_pair(precision, false, ln.threads, pl, ln.nctas, st);
+        rc = launch_pair(precision, false, G.skew, ln.threads, pl, ln.nctas, st);
         if (rc) return rc;
         rc = launch_reduce_items(pl, st);
         if (rc) return rc;

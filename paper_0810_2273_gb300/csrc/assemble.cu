@@ -3,8 +3,10 @@
 // section 3 frozen):
 //   dE/dn_m = dV^2 [chi_m (A_m + U_m dq0/dn_m) + sum_a (G_a^T w_a)_m],
 //   w_a = chi U dq0/dg_a,
-// where G_a is the periodic 4th-order central-difference stencil along axis a.
-// G_a is antisymmetric, so G_a^T w = -G_a w and
+// where G_a is the periodic 4th-order central-difference stencil along grid
+// axis a mapped to Cartesian components (on a general cell the gradient is
+// sum_a (d/du_a) B_a, so w_a becomes sum_c S[3a + c] w_c).  The stencil is
+// antisymmetric, so G_a^T w = -G_a w and
 //   v_m = dE/dn_m / dV = dV [chi_m (A_m + U_m dq0/dn_m) - sum_a (G_a w_a)_m].
 // Also E = 1/2 dV^2 sum_i n_i A_i.
 #include <cuda_runtime.h>
@@ -20,7 +22,7 @@ __device__ __forceinline__ int wrap(int i, int n) {
     return i < 0 ? i + n : i;
 }
 
-__global__ void k_assemble(int n0, int n1, int n2, double ih0, double ih1, double ih2, double dV,
+__global__ void k_assemble(int n0, int n1, int n2, const AxisMap am, double dV,
                            const int *__restrict__ slot, const double *__restrict__ A,
                            const double *__restrict__ U, const double *__restrict__ qn,
                            const double *__restrict__ qg, double *__restrict__ v,
@@ -32,18 +34,24 @@ __global__ void k_assemble(int n0, int n1, int n2, double ih0, double ih1, doubl
         const int b = static_cast<int>((m / n2) % n1);
         const int a = static_cast<int>(m / (static_cast<long long>(n1) * n2));
         const long long sa = static_cast<long long>(n1) * n2;
-        // w_ax at a neighbour index (0 at inactive points)
+        // w along grid axis ax at a neighbour index (0 at inactive points): on a
+        // diagonal cell U dq0/dg_ax, scaled below; on a general cell the
+        // transpose of the axis map, sum_c S[3 ax + c] U dq0/dg_c
         auto w = [&](long long mm, int ax) {
             const int s = slot[mm];
-            return s >= 0 ? U[s] * qg[ax * N + mm] : 0.0;
+            if (s < 0) return 0.0;
+            if (!am.general) return U[s] * qg[ax * N + mm];
+            return U[s] * (am.S[3 * ax] * qg[mm] + am.S[3 * ax + 1] * qg[N + mm] + am.S[3 * ax + 2] * qg[2 * N + mm]);
         };
+        const double f0 = am.general ? 1.0 : am.S[0], f1 = am.general ? 1.0 : am.S[4],
+                     f2 = am.general ? 1.0 : am.S[8];
         auto ia = [&](int aa) { return static_cast<long long>(wrap(aa, n0)) * sa + static_cast<long long>(b) * n2 + c; };
         auto ib = [&](int bb) { return static_cast<long long>(a) * sa + static_cast<long long>(wrap(bb, n1)) * n2 + c; };
         auto ic = [&](int cc) { return static_cast<long long>(a) * sa + static_cast<long long>(b) * n2 + wrap(cc, n2); };
         const double div =
-            (8.0 * (w(ia(a + 1), 0) - w(ia(a - 1), 0)) - (w(ia(a + 2), 0) - w(ia(a - 2), 0))) * (ih0 / 12.0) +
-            (8.0 * (w(ib(b + 1), 1) - w(ib(b - 1), 1)) - (w(ib(b + 2), 1) - w(ib(b - 2), 1))) * (ih1 / 12.0) +
-            (8.0 * (w(ic(c + 1), 2) - w(ic(c - 1), 2)) - (w(ic(c + 2), 2) - w(ic(c - 2), 2))) * (ih2 / 12.0);
+            (8.0 * (w(ia(a + 1), 0) - w(ia(a - 1), 0)) - (w(ia(a + 2), 0) - w(ia(a - 2), 0))) * f0 +
+            (8.0 * (w(ib(b + 1), 1) - w(ib(b - 1), 1)) - (w(ib(b + 2), 1) - w(ib(b - 2), 1))) * f1 +
+            (8.0 * (w(ic(c + 1), 2) - w(ic(c - 1), 2)) - (w(ic(c + 2), 2) - w(ic(c - 2), 2))) * f2;
         const int s = slot[m];
         double loc = 0.0, av = 0.0, uv = 0.0;
         if (s >= 0) {
@@ -77,16 +85,15 @@ __global__ void k_energy_from_A(int n_max, const double *__restrict__ A, const d
 
 }  // namespace
 
-int launch_assemble(const int dims[3], const double h[3], double dV, const int *slot,
+int launch_assemble(const int dims[3], const AxisMap &am, double dV, const int *slot,
                     const double *A, const double *U, const double *dq0dn, const double *dq0dg,
                     double *v, double *A_grid, double *U_grid, cudaStream_t st) {
     const long long N = static_cast<long long>(dims[0]) * dims[1] * dims[2];
     const int bs = 256;
     long long nb = (N + bs - 1) / bs;
     if (nb > 1 << 20) nb = 1 << 20;
-    k_assemble<<<static_cast<int>(nb), bs, 0, st>>>(dims[0], dims[1], dims[2], 1.0 / h[0], 1.0 / h[1],
-                                                     1.0 / h[2], dV, slot, A, U, dq0dn, dq0dg, v,
-                                                     A_grid, U_grid);
+    k_assemble<<<static_cast<int>(nb), bs, 0, st>>>(dims[0], dims[1], dims[2], am, dV, slot, A, U, dq0dn,
+                                                     dq0dg, v, A_grid, U_grid);
     count_launches(1);
     VDWDF_CUDA_TRY(cudaGetLastError());
     return VDWDF_OK;

@@ -42,9 +42,23 @@ struct Stats {
     int n_active;
 };
 
+// Derivatives along the grid axes to Cartesian components: the gradient is
+// g_c = sum_a S[3a + c] (8 (f_{+1} - f_{-1}) - (f_{+2} - f_{-2}))_a with
+// S[3a + c] = N_a B_a[c] / 12, B_a the reciprocal rows of the cell (B_a . M_b =
+// delta_ab).  On a diagonal cell S[4a] = (1/h_a)/12, the rest 0, and general = 0.
+struct AxisMap {
+    double S[9];
+    int general;
+};
+
 // Per-instance inputs of the pair kernel.
 struct PairParams {
-    double h2[3];        // squared grid spacings (r^2 = sum h2_a d_a^2, d in index units)
+    double h2[3];        // metric in index units, diagonal: |M_a|^2 / N_a^2
+    double g2x[3];       // 2 x off-diagonal metric (01, 02, 12): r^2 = sum h2_a d_a^2
+                         //   + g2x[0] d_0 d_1 + g2x[1] d_0 d_2 + g2x[2] d_1 d_2
+    float cull_h2[3];    // culling metric: h2 on orthogonal cells, the smallest
+                         //   eigenvalue of the metric on skewed ones (a lower bound)
+    float rcm[3];        // cutoff extent in index units along each axis (widened)
     double rc2;          // squared cutoff times (1 + 1e-12): inside iff r^2 <= rc2
     int dims[3];
     int M[3];            // max |image index| per axis (0: not periodic)
@@ -85,15 +99,16 @@ struct PairLaunch {
 // doubles; the last six hold Ex_lda, Ec_lda, Ex_pbe, Ec_pbe, Ex_revpbe (sums of
 // n eps, not yet times dV) and the number of points with n > 0.
 int semilocal_scratch_doubles();
-int launch_semilocal(const int dims[3], const double h[3], const double *n, const double *grad_in,
+int launch_semilocal(const int dims[3], const AxisMap &am, const double *n, const double *grad_in,
                      double *scratch, cudaStream_t st);
-int launch_grad_q0(const int dims[3], const double h[3], const double *n, const double *grad_in,
+int launch_grad_q0(const int dims[3], const AxisMap &am, const double *n, const double *grad_in,
                    double *q0, double *dq0dn, double *dq0dg, cudaStream_t st);
 int launch_compact(const int dims[3], const double *n, double n_cut, const double *q0,
                    const int *brick_order, int nbricks, int *brick_cnt, int *brick_off, int *slot,
                    float4 *p32, float *n32, dvec4 *p64, double *n64, float4 *blo, float4 *bhi,
                    Stats *stats, cudaStream_t st);
-int launch_pair(int precision, bool potential, int threads, const PairLaunch &pl, int nctas,
+// skew: some instance has a non-diagonal metric (the kernel adds the cross terms)
+int launch_pair(int precision, bool potential, bool skew, int threads, const PairLaunch &pl, int nctas,
                 cudaStream_t st);
 // Row stride of the shared-memory table band: odd, so that one column of
 // consecutive rows falls in distinct banks.
@@ -107,7 +122,7 @@ __host__ __device__ inline long long pair_items(long long n_active, int jt) {
     const long long nT = (n_active + kTile - 1) / kTile;
     return nT * ((nT + jt - 1) / jt);
 }
-int launch_assemble(const int dims[3], const double h[3], double dV, const int *slot,
+int launch_assemble(const int dims[3], const AxisMap &am, double dV, const int *slot,
                     const double *A, const double *U, const double *dq0dn, const double *dq0dg,
                     double *v, double *A_grid, double *U_grid, cudaStream_t st);
 int launch_energy_from_A(int n_max, const double *A, const double *n64, Stats *stats,

@@ -342,14 +342,19 @@ __device__ __forceinline__ T warp_sum(T v) {
 struct Cut {
     double rc2d;
     double h2d[3];
+    double g2d[3];  // 2 x off-diagonal metric (skewed cells)
     float lo, hi;
 };
+template <bool SKEW>
 __device__ __forceinline__ bool beyond(float r2, float dx, float dy, float dz, const Cut &c) {
     if (r2 > c.hi) return true;
     if (r2 <= c.lo) return false;
     const double X = dx, Y = dy, Z = dz;
-    return c.h2d[0] * (X * X) + c.h2d[1] * (Y * Y) + c.h2d[2] * (Z * Z) > c.rc2d;
+    double e = c.h2d[0] * (X * X) + c.h2d[1] * (Y * Y) + c.h2d[2] * (Z * Z);
+    if (SKEW) e += c.g2d[0] * (X * Y) + c.g2d[1] * (X * Z) + c.g2d[2] * (Y * Z);
+    return e > c.rc2d;
 }
+template <bool SKEW>
 __device__ __forceinline__ bool beyond(double r2, double, double, double, const Cut &c) {
     return r2 > c.rc2d;
 }
@@ -431,10 +436,10 @@ __device__ __forceinline__ void band_pair2(const Table<float> &tb, float2 tD, in
 // arithmetic where both lie in the resident band, one at a time otherwise.
 // Adds sum_images phi, r dphi/dd1, r dphi/dd2 to sA, sU, cU; counts the inside
 // evaluations (ins) and those with r > 0 (hits).
-template <bool POT, typename P>
+template <bool POT, bool SKEW, typename P>
 __device__ __forceinline__ void images_f32(unsigned m, const P *simg, float xi, float yi, float zi,
                                            float qi, float inv_qi, float qi2, const P &pj,
-                                           const float h2[3], bool lane_ok, bool use_cut,
+                                           const float h2[3], const float g2x[3], bool lane_ok, bool use_cut,
                                            const Cut &cut, const Delta<float> &dp,
                                            const Consts<float> &K, const Table<float> &tb,
                                            float band_lo, float band_hi, float &sA, float &sU,
@@ -461,10 +466,14 @@ __device__ __forceinline__ void images_f32(unsigned m, const P *simg, float xi, 
         const P s0 = simg[i0], s1 = simg[i1];
         const float dx0 = (xi + s0.x) - pj.x, dy0 = (yi + s0.y) - pj.y, dz0 = (zi + s0.z) - pj.z;
         const float dx1 = (xi + s1.x) - pj.x, dy1 = (yi + s1.y) - pj.y, dz1 = (zi + s1.z) - pj.z;
-        const float r20 = h2[0] * (dx0 * dx0) + h2[1] * (dy0 * dy0) + h2[2] * (dz0 * dz0);
-        const float r21 = h2[0] * (dx1 * dx1) + h2[1] * (dy1 * dy1) + h2[2] * (dz1 * dz1);
-        const bool in0 = lane_ok && !(use_cut && beyond(r20, dx0, dy0, dz0, cut));
-        const bool in1 = two && lane_ok && !(use_cut && beyond(r21, dx1, dy1, dz1, cut));
+        float r20 = h2[0] * (dx0 * dx0) + h2[1] * (dy0 * dy0) + h2[2] * (dz0 * dz0);
+        float r21 = h2[0] * (dx1 * dx1) + h2[1] * (dy1 * dy1) + h2[2] * (dz1 * dz1);
+        if (SKEW) {
+            r20 += g2x[0] * (dx0 * dy0) + g2x[1] * (dx0 * dz0) + g2x[2] * (dy0 * dz0);
+            r21 += g2x[0] * (dx1 * dy1) + g2x[1] * (dx1 * dz1) + g2x[2] * (dy1 * dz1);
+        }
+        const bool in0 = lane_ok && !(use_cut && beyond<SKEW>(r20, dx0, dy0, dz0, cut));
+        const bool in1 = two && lane_ok && !(use_cut && beyond<SKEW>(r21, dx1, dy1, dz1, cut));
         if (!(in0 || in1)) continue;
         ins += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
         hits += ((in0 && r20 > 0.0f) ? 1u : 0u) + ((in1 && r21 > 0.0f) ? 1u : 0u);
@@ -514,7 +523,7 @@ __device__ __forceinline__ void images_f32(unsigned m, const P *simg, float xi, 
 // and, inside, over the marked images: the delta part of a pair is computed once
 // for all its images, and the j-side sums of the potential are reduced over the
 // warp once per j point.
-template <typename R, int MODE, int NT>
+template <typename R, int MODE, int NT, bool SKEW>
 __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaunch pl) {
     constexpr bool POT = (MODE == 1);
     constexpr int NW = NT / 32;
@@ -596,23 +605,31 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
             continue;
         }
 
-        R h2[3];
-        float h2f[3], rcm[3];
+        R h2[3], g2x[3];
+        float h2f[3], g2f[3], rcm[3];
         int dims[3], M[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             h2[a] = static_cast<R>(pp.h2[a]);
+            g2x[a] = static_cast<R>(pp.g2x[a]);
             h2f[a] = static_cast<float>(pp.h2[a]);
+            g2f[a] = static_cast<float>(pp.g2x[a]);
             dims[a] = pp.dims[a];
             M[a] = pp.M[a];
             // cutoff in index units along a, widened so that rounding never drops an image
-            rcm[a] = pp.use_cut ? static_cast<float>(sqrt(pp.rc2 / pp.h2[a])) * 1.0001f + 1e-3f : 0.0f;
+            rcm[a] = pp.rcm[a];
         }
+        // culling metric: h2 on orthogonal cells, a lower bound of r^2/|d|^2 on skewed ones
+        const float cull[3] = {pp.cull_h2[0], pp.cull_h2[1], pp.cull_h2[2]};
+        (void)h2f;
         Cut cut;
         cut.rc2d = pp.rc2;
         cut.h2d[0] = pp.h2[0];
         cut.h2d[1] = pp.h2[1];
         cut.h2d[2] = pp.h2[2];
+        cut.g2d[0] = pp.g2x[0];
+        cut.g2d[1] = pp.g2x[1];
+        cut.g2d[2] = pp.g2x[2];
         cut.lo = static_cast<float>(pp.rc2) * (1.0f - 1e-5f);
         cut.hi = static_cast<float>(pp.rc2) * (1.0f + 1e-5f);
         const float rc2_box = static_cast<float>(pp.rc2) * 1.0002f + 1e-6f;
@@ -668,7 +685,7 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
                     const int t1 = t / nm[2];
                     mm[1] = mlo[1] + t1 % nm[1];
                     mm[0] = mlo[0] + t1 / nm[1];
-                    ok = !use_cut || box_gap2(ilo, ihi, jl, jh, mm, dims, h2f) <= rc2_box;
+                    ok = !use_cut || box_gap2(ilo, ihi, jl, jh, mm, dims, cull) <= rc2_box;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, ok);
                 if (bal == 0u) continue;
@@ -703,7 +720,7 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
                         const float gx = fmaxf(0.0f, fmaxf(ilo[0] + sx - px, px - ihi[0] - sx));
                         const float gy = fmaxf(0.0f, fmaxf(ilo[1] + sy - py, py - ihi[1] - sy));
                         const float gz = fmaxf(0.0f, fmaxf(ilo[2] + sz - pz, pz - ihi[2] - sz));
-                        const float d2 = h2f[0] * gx * gx + h2f[1] * gy * gy + h2f[2] * gz * gz;
+                        const float d2 = cull[0] * gx * gx + cull[1] * gy * gy + cull[2] * gz * gz;
                         if (!use_cut || d2 <= rc2_box) jm |= 1u << b;
                     }
                 }
@@ -724,16 +741,18 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
                     R sA = 0, sU = 0, cA = 0, cU = 0;
                     unsigned ins = 0, hits = 0;
                     if constexpr (sizeof(R) == 4) {
-                        images_f32<POT, P>(m, simg, xi, yi, zi, qi, inv_qi, qi2, pj, h2, lane_ok, use_cut,
-                                           cut, dp, K, tb, band_lo, band_hi, sA, sU, cU, ins, hits);
+                        images_f32<POT, SKEW, P>(m, simg, xi, yi, zi, qi, inv_qi, qi2, pj, h2, g2f, lane_ok,
+                                                 use_cut, cut, dp, K, tb, band_lo, band_hi, sA, sU, cU, ins,
+                                                 hits);
                         cA = sA;
                     } else do {
                         const int b = __ffs(m) - 1;
                         m &= m - 1u;
                         const P sft = simg[b];
                         const R dx = (xi + sft.x) - pj.x, dy = (yi + sft.y) - pj.y, dz = (zi + sft.z) - pj.z;
-                        const R r2 = h2[0] * (dx * dx) + h2[1] * (dy * dy) + h2[2] * (dz * dz);
-                        if (lane_ok && !(use_cut && beyond(r2, dx, dy, dz, cut))) {
+                        R r2 = h2[0] * (dx * dx) + h2[1] * (dy * dy) + h2[2] * (dz * dz);
+                        if (SKEW) r2 += g2x[0] * (dx * dy) + g2x[1] * (dx * dz) + g2x[2] * (dy * dz);
+                        if (lane_ok && !(use_cut && beyond<SKEW>(r2, dx, dy, dz, cut))) {
                             R phi, rd = 0, rd2 = 0;
                             dist_part<POT, R>(r2, qi, pj.w, inv_qi, qi2, dp, K, tb, phi, rd, rd2);
                             sA += phi;
@@ -839,9 +858,9 @@ __global__ void k_kernel_eval(const PairShared sh, int64_t npts, const double *r
     }
 }
 
-template <typename R, int MODE, int NT>
+template <typename R, int MODE, int NT, bool SKEW>
 int launch_one(const PairLaunch &pl, int nctas, size_t smem, cudaStream_t st) {
-    auto kern = k_pair<R, MODE, NT>;
+    auto kern = k_pair<R, MODE, NT, SKEW>;
     VDWDF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         static_cast<int>(smem)));
     kern<<<nctas, NT, smem, st>>>(pl);
@@ -850,13 +869,16 @@ int launch_one(const PairLaunch &pl, int nctas, size_t smem, cudaStream_t st) {
     return VDWDF_OK;
 }
 
+// Skewed cells run the 512-thread kernel only (the launch configuration is
+// chosen for 512 threads when any instance is skewed).
 template <typename R, int MODE>
-int launch_nt(int threads, const PairLaunch &pl, int nctas, size_t smem, cudaStream_t st) {
+int launch_nt(int threads, bool skew, const PairLaunch &pl, int nctas, size_t smem, cudaStream_t st) {
+    if (skew) return launch_one<R, MODE, 512, true>(pl, nctas, smem, st);
     switch (threads) {
-        case 256: return launch_one<R, MODE, 256>(pl, nctas, smem, st);
-        case 384: return launch_one<R, MODE, 384>(pl, nctas, smem, st);
-        case 1024: return launch_one<R, MODE, 1024>(pl, nctas, smem, st);
-        default: return launch_one<R, MODE, 512>(pl, nctas, smem, st);
+        case 256: return launch_one<R, MODE, 256, false>(pl, nctas, smem, st);
+        case 384: return launch_one<R, MODE, 384, false>(pl, nctas, smem, st);
+        case 1024: return launch_one<R, MODE, 1024, false>(pl, nctas, smem, st);
+        default: return launch_one<R, MODE, 512, false>(pl, nctas, smem, st);
     }
 }
 
@@ -871,14 +893,15 @@ int pair_smem_bytes(int precision, int threads, int ksn, int S) {
     return static_cast<int>(b);
 }
 
-int launch_pair(int precision, bool potential, int threads, const PairLaunch &pl, int nctas,
+int launch_pair(int precision, bool potential, bool skew, int threads, const PairLaunch &pl, int nctas,
                 cudaStream_t st) {
+    if (skew && threads != 512) return VDWDF_EINVAL;  // the caller chooses 512 for skewed cells
     const size_t smem = static_cast<size_t>(pair_smem_bytes(precision, threads, pl.sh.ksn, pl.sh.S));
     if (precision == VDWDF_FP64)
-        return potential ? launch_nt<double, 1>(threads, pl, nctas, smem, st)
-                         : launch_nt<double, 0>(threads, pl, nctas, smem, st);
-    return potential ? launch_nt<float, 1>(threads, pl, nctas, smem, st)
-                     : launch_nt<float, 0>(threads, pl, nctas, smem, st);
+        return potential ? launch_nt<double, 1>(threads, skew, pl, nctas, smem, st)
+                         : launch_nt<double, 0>(threads, skew, pl, nctas, smem, st);
+    return potential ? launch_nt<float, 1>(threads, skew, pl, nctas, smem, st)
+                     : launch_nt<float, 0>(threads, skew, pl, nctas, smem, st);
 }
 
 int launch_reduce_items(const PairLaunch &pl, cudaStream_t st) {

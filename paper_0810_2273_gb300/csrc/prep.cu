@@ -1,8 +1,10 @@
 // Grid-level steps before the pair sum, FP64:
-//  - gradient by 4th-order central differences along the orthogonal axes with
-//    periodic wrap (paper section 3: "real space finite differences ...
-//    perpendicular axes only"),
-//      g_a = (n_{-2} - 8 n_{-1} + 8 n_{+1} - n_{+2}) / (12 h_a);
+//  - gradient by 4th-order central differences along the grid axes with
+//    periodic wrap (section 3 uses finite differences along perpendicular axes;
+//    on a general cell the differences along each axis give d/du_a, u_a the
+//    fractional coordinate, and grad = sum_a (d/du_a) B_a with the reciprocal
+//    rows B_a),
+//      along axis a: (n_{-2} - 8 n_{-1} + 8 n_{+1} - n_{+2}) / 12 per index step;
 //  - q0 of Dion eqs. 11-12 (section 2 relies on it through D and delta):
 //      q0 = k_F - (Zab/36) |g|^2 / (k_F n^2) - (4 pi/3) eps_c(r_s),
 //    k_F = (3 pi^2 n)^(1/3), Zab = -0.8491, eps_c of Perdew-Wang 1992, and the
@@ -41,9 +43,10 @@ __device__ __forceinline__ int wrap(int i, int n) {
 }
 
 // grad n at point m = (a, b, c): the caller's [3][N] gradient, or the 4th-order
-// periodic stencil on n.
-__device__ __forceinline__ void grad_at(long long m, int n0, int n1, int n2, double ih0, double ih1,
-                                        double ih2, const double *__restrict__ n,
+// periodic stencil on n along each grid axis, mapped to Cartesian components
+// (general cells: g_c = sum_a S[3a + c] stencil_a).
+__device__ __forceinline__ void grad_at(long long m, int n0, int n1, int n2, const AxisMap &am,
+                                        const double *__restrict__ n,
                                         const double *__restrict__ gin, double &gx, double &gy,
                                         double &gz) {
     const long long N = static_cast<long long>(n0) * n1 * n2;
@@ -62,12 +65,21 @@ __device__ __forceinline__ void grad_at(long long m, int n0, int n1, int n2, dou
     auto at_a = [&](int aa) { return n[static_cast<long long>(wrap(aa, n0)) * sa + row]; };
     auto at_b = [&](int bb) { return n[static_cast<long long>(a) * sa + static_cast<long long>(wrap(bb, n1)) * n2 + c]; };
     auto at_c = [&](int cc) { return n[pl + wrap(cc, n2)]; };
-    gx = (8.0 * (at_a(a + 1) - at_a(a - 1)) - (at_a(a + 2) - at_a(a - 2))) * (ih0 / 12.0);
-    gy = (8.0 * (at_b(b + 1) - at_b(b - 1)) - (at_b(b + 2) - at_b(b - 2))) * (ih1 / 12.0);
-    gz = (8.0 * (at_c(c + 1) - at_c(c - 1)) - (at_c(c + 2) - at_c(c - 2))) * (ih2 / 12.0);
+    const double s0 = 8.0 * (at_a(a + 1) - at_a(a - 1)) - (at_a(a + 2) - at_a(a - 2));
+    const double s1 = 8.0 * (at_b(b + 1) - at_b(b - 1)) - (at_b(b + 2) - at_b(b - 2));
+    const double s2 = 8.0 * (at_c(c + 1) - at_c(c - 1)) - (at_c(c + 2) - at_c(c - 2));
+    if (!am.general) {
+        gx = s0 * am.S[0];
+        gy = s1 * am.S[4];
+        gz = s2 * am.S[8];
+    } else {
+        gx = s0 * am.S[0] + s1 * am.S[3] + s2 * am.S[6];
+        gy = s0 * am.S[1] + s1 * am.S[4] + s2 * am.S[7];
+        gz = s0 * am.S[2] + s1 * am.S[5] + s2 * am.S[8];
+    }
 }
 
-__global__ void k_grad_q0(int n0, int n1, int n2, double ih0, double ih1, double ih2,
+__global__ void k_grad_q0(int n0, int n1, int n2, const AxisMap am,
                           const double *__restrict__ n, const double *__restrict__ gin,
                           double *__restrict__ q0, double *__restrict__ qn, double *__restrict__ qg) {
     const long long N = static_cast<long long>(n0) * n1 * n2;
@@ -75,7 +87,7 @@ __global__ void k_grad_q0(int n0, int n1, int n2, double ih0, double ih1, double
     for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < N;
          m += static_cast<long long>(gridDim.x) * blockDim.x) {
         double gx, gy, gz;
-        grad_at(m, n0, n1, n2, ih0, ih1, ih2, n, gin, gx, gy, gz);
+        grad_at(m, n0, n1, n2, am, n, gin, gx, gy, gz);
         const double nn = n[m];
         if (!(nn > 0.0)) {
             q0[m] = 0.0;
@@ -278,8 +290,8 @@ __device__ __forceinline__ double gga_fx(double s2, double kappa, double mu) {
     return 1.0 + kappa - kappa / (1.0 + mu * s2 / kappa);
 }
 
-__global__ void __launch_bounds__(kSemiThreads) k_semilocal(int n0, int n1, int n2, double ih0, double ih1,
-                                                            double ih2, const double *__restrict__ n,
+__global__ void __launch_bounds__(kSemiThreads) k_semilocal(int n0, int n1, int n2, const AxisMap am,
+                                                            const double *__restrict__ n,
                                                             const double *__restrict__ gin,
                                                             double *__restrict__ part) {
     const long long N = static_cast<long long>(n0) * n1 * n2;
@@ -292,7 +304,7 @@ __global__ void __launch_bounds__(kSemiThreads) k_semilocal(int n0, int n1, int 
         const double nn = n[m];
         if (!(nn > 0.0)) continue;
         double gx, gy, gz;
-        grad_at(m, n0, n1, n2, ih0, ih1, ih2, n, gin, gx, gy, gz);
+        grad_at(m, n0, n1, n2, am, n, gin, gx, gy, gz);
         const double g2 = gx * gx + gy * gy + gz * gz;
         const double kF = cbrt(3.0 * kPi * kPi * nn);
         const double rs = cbrt(3.0 / (4.0 * kPi * nn));
@@ -341,24 +353,22 @@ __global__ void k_semilocal_sum(const double *__restrict__ part, int nblocks, do
 
 int semilocal_scratch_doubles() { return (kSemiBlocks + 1) * kSemiVals; }
 
-int launch_semilocal(const int dims[3], const double h[3], const double *n, const double *grad_in,
+int launch_semilocal(const int dims[3], const AxisMap &am, const double *n, const double *grad_in,
                      double *scratch, cudaStream_t st) {
-    k_semilocal<<<kSemiBlocks, kSemiThreads, 0, st>>>(dims[0], dims[1], dims[2], 1.0 / h[0], 1.0 / h[1],
-                                                      1.0 / h[2], n, grad_in, scratch);
+    k_semilocal<<<kSemiBlocks, kSemiThreads, 0, st>>>(dims[0], dims[1], dims[2], am, n, grad_in, scratch);
     k_semilocal_sum<<<1, 32, 0, st>>>(scratch, kSemiBlocks, scratch + kSemiBlocks * kSemiVals);
     count_launches(2);
     VDWDF_CUDA_TRY(cudaGetLastError());
     return VDWDF_OK;
 }
 
-int launch_grad_q0(const int dims[3], const double h[3], const double *n, const double *grad_in,
+int launch_grad_q0(const int dims[3], const AxisMap &am, const double *n, const double *grad_in,
                    double *q0, double *dq0dn, double *dq0dg, cudaStream_t st) {
     const long long N = static_cast<long long>(dims[0]) * dims[1] * dims[2];
     const int bs = 256;
     long long nb = (N + bs - 1) / bs;
     if (nb > 1 << 20) nb = 1 << 20;
-    k_grad_q0<<<static_cast<int>(nb), bs, 0, st>>>(dims[0], dims[1], dims[2], 1.0 / h[0], 1.0 / h[1],
-                                                    1.0 / h[2], n, grad_in, q0, dq0dn, dq0dg);
+    k_grad_q0<<<static_cast<int>(nb), bs, 0, st>>>(dims[0], dims[1], dims[2], am, n, grad_in, q0, dq0dn, dq0dg);
     count_launches(1);
     VDWDF_CUDA_TRY(cudaGetLastError());
     return VDWDF_OK;

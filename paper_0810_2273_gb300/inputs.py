@@ -14,7 +14,11 @@ Workloads (``config(i)``):
   3 binding_curve   16 dimers (6.0..12.0 bohr) + 2 single atoms, open
   4 slab_adsorbate  4-layer 144-atom slab + 30-atom flake, 128x112x200,
                     periodic x,y
-Seeds: NumPy PCG64, 20081021 + workload index.
+  5 xe_monolayer_hex  the monolayer in a 4-atom hexagonal cell (60 degrees),
+                    48x48x120, periodic along the in-plane lattice vectors
+Seeds: NumPy PCG64, 20081021 + workload index.  Workloads on a general cell
+carry it as w["cell"] (rows: lattice vectors); w["lengths"] is then only its
+diagonal and must not be used as the cell.
 """
 import math
 
@@ -74,6 +78,29 @@ def density(dims, lengths, atoms, periodic=(False, False, False), floor=1e-14):
     return out
 
 
+def density_cell(dims, cell, atoms, periodic=(False, False, False), floor=1e-14):
+    """As density(), on a general cell: rows of ``cell`` are the lattice vectors,
+    grid point (i, j, k) sits at i/n0 M_0 + j/n1 M_1 + k/n2 M_2.  Periodic axes add
+    the atom's images one cell either side (by lattice vectors)."""
+    dims = tuple(int(d) for d in dims)
+    M = np.asarray(cell, dtype=np.float64).reshape(3, 3)
+    u = np.meshgrid(*[np.arange(d, dtype=np.float64) / d for d in dims], indexing="ij")
+    P = u[0][..., None] * M[0] + u[1][..., None] * M[1] + u[2][..., None] * M[2]
+    out = np.zeros(dims, dtype=np.float64)
+    shifts = [(-1, 0, 1) if p else (0,) for p in periodic]
+    for pos, comps in atoms:
+        pos = np.asarray(pos, dtype=np.float64)
+        for s0 in shifts[0]:
+            for s1 in shifts[1]:
+                for s2 in shifts[2]:
+                    c = pos + s0 * M[0] + s1 * M[1] + s2 * M[2]
+                    r = np.sqrt(((P - c) ** 2).sum(-1))
+                    for A, a in comps:
+                        e = A * np.exp(-r / a)
+                        out += np.where(e > floor, e, 0.0)
+    return out
+
+
 def _noise(n, rng, amp):
     """Multiplicative seeded noise n (1 + amp U(-1, 1))."""
     return n * (1.0 + amp * rng.uniform(-1.0, 1.0, size=n.shape))
@@ -108,6 +135,26 @@ def xe_monolayer(dims=(48, 84, 120)):
     n = density(dims, L, atoms, periodic=(True, True, False))
     n = _noise(n, _rng(1), 0.01)
     return _workload("xe_monolayer", 1, n, L, (True, True, False), 1e-6, 20.0, atoms=atoms)
+
+
+def xe_monolayer_hex(dims=(48, 48, 120)):
+    """The rare-gas monolayer of xe_monolayer in a hexagonal cell, as the paper's
+    own Xe cell is (section 6.2): a 2 x 2 supercell of the primitive cell with
+    nearest neighbours 8.2 bohr, M_0 = (16.4, 0, 0), M_1 = (8.2, 14.2028, 0)
+    (60 degrees), M_2 = (0, 0, 40); 4 atoms at z = 20; periodic along M_0, M_1;
+    20 bohr pair cutoff, 1% multiplicative noise, density cutoff 1e-6.  The
+    grid spacing along the in-plane axes is 0.342 bohr, as in xe_monolayer."""
+    a = 8.2
+    p1 = np.array([a, 0.0, 0.0])
+    p2 = np.array([a / 2.0, a * math.sqrt(3.0) / 2.0, 0.0])
+    cell = np.array([2 * p1, 2 * p2, [0.0, 0.0, 40.0]])
+    atoms = [(tuple(i * p1 + j * p2 + np.array([0.0, 0.0, 20.0])), rare_gas_shells())
+             for i in range(2) for j in range(2)]
+    n = density_cell(dims, cell, atoms, periodic=(True, True, False))
+    n = _noise(n, _rng(5), 0.01)
+    w = _workload("xe_monolayer_hex", 5, n, np.diag(cell), (True, True, False), 1e-6, 20.0, atoms=atoms)
+    w["cell"] = cell
+    return w
 
 
 def molecule24(dims=(64, 64, 64)):

@@ -16,7 +16,7 @@ import time
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--workload", default="xe_monolayer",
-                    choices=["kr_dimer", "xe_monolayer", "molecule24", "slab_adsorbate"])
+                    choices=["kr_dimer", "xe_monolayer", "xe_monolayer_hex", "molecule24", "slab_adsorbate"])
     ap.add_argument("--dims", type=int, nargs=3, default=None)
     ap.add_argument("--mode", default="potential", choices=["potential", "energy", "semilocal"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -38,13 +38,14 @@ def main(argv=None):
     w = maker(tuple(a.dims)) if a.dims else maker()
     dev = torch.device("cuda:0")
     n = torch.from_numpy(w["density"]).to(dev)
-    args = (w["lengths"], w["periodic"], w["n_cut"], w["r_cut"], T)
+    cell = w.get("cell", w["lengths"])  # general cells carry their lattice vectors
+    args = (cell, w["periodic"], w["n_cut"], w["r_cut"], T)
     tu = {"threads": a.threads, "items_per_sm": a.items_per_sm} if (a.threads or a.items_per_sm) else None
     for k in range(a.repeat):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if a.mode == "semilocal":
-            res = V.semilocal(n, w["lengths"], w["periodic"])
+            res = V.semilocal(n, cell, w["periodic"])
             torch.cuda.synchronize()
             res.update(call=k, wall_ms=1e3 * (time.perf_counter() - t0), workload=a.workload,
                        dims=list(n.shape), mode=a.mode, points_per_s=n.numel() / max(res["ms"] * 1e-3, 1e-12))

@@ -91,21 +91,21 @@ def test_host_side_argument_errors(native):
                             None, ctypes.byref(res), None) == -1
     assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1), 5,
                             None, ctypes.byref(res), None) == -1
-    # non-orthorhombic cell
-    g.cell[0][1] = 1.0
+    # singular cell (two parallel lattice vectors)
+    g.cell[1][0], g.cell[1][1] = 10.0, 0.0
     assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1), 0,
-                            None, ctypes.byref(res), None) == -2
+                            None, ctypes.byref(res), None) == -1
+    g.cell[1][0], g.cell[1][1] = 0.0, 10.0
     # batched: bad count
     assert lib.vdwdf_energy_batched(0, None, None, 1e-6, 0.0, ctypes.c_void_p(1), 0, None, None, None,
                                     None) == -1
-    # semilocal energies: null density or result, non-orthorhombic cell
-    g.cell[0][1] = 0.0
+    # semilocal energies: null density or result, singular cell
     sres = native.vdwdf_semilocal_result()
     assert lib.vdwdf_semilocal(ctypes.byref(g), None, None, ctypes.byref(sres), None) == -1
     assert lib.vdwdf_semilocal(ctypes.byref(g), ctypes.c_void_p(8), None, None, None) == -1
-    g.cell[0][1] = 1.0
-    assert lib.vdwdf_semilocal(ctypes.byref(g), ctypes.c_void_p(8), None, ctypes.byref(sres), None) == -2
-    g.cell[0][1] = 0.0
+    g.cell[2][0], g.cell[2][2] = 10.0, 0.0
+    assert lib.vdwdf_semilocal(ctypes.byref(g), ctypes.c_void_p(8), None, ctypes.byref(sres), None) == -1
+    g.cell[2][0], g.cell[2][2] = 0.0, 10.0
     # no-allocation energy: a grid larger than its static scratch holds is refused
     g.cell[0][1] = 0.0
     g.n[0], g.n[1], g.n[2] = 64, 64, 17
