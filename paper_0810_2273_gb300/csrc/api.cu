@@ -152,6 +152,7 @@ struct Geom {
     double lmin;        // its smallest eigenvalue
     bool skew;          // non-diagonal metric
     AxisMap am;         // grid-axis derivatives to Cartesian gradient
+    CellRows vrow;      // M_a / N_a (float), for Cartesian tile boxes
 };
 
 // Smallest eigenvalue of the symmetric 3x3 matrix (a00, a11, a22, a01, a02, a12)
@@ -214,6 +215,8 @@ int check_grid(const vdwdf_grid *g, Geom &G) {
     G.skew = G.met[3] != 0.0 || G.met[4] != 0.0 || G.met[5] != 0.0;
     G.lmin = sym3_min_eig(G.met);
     if (!(G.lmin > 0.0)) return VDWDF_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) G.vrow.v[3 * a + c] = static_cast<float>(M[a][c] / G.dims[a]);
     G.am.general = diagonal ? 0 : 1;
     for (int a = 0; a < 3; ++a)
         for (int c = 0; c < 3; ++c)
@@ -261,6 +264,7 @@ struct Work {
     dvec4 *p64 = nullptr;
     double *n64 = nullptr;
     float4 *blo = nullptr, *bhi = nullptr;
+    float4 *clo = nullptr, *chi = nullptr;  // skewed cells only
     double *A = nullptr, *U = nullptr;
     Stats *stats = nullptr;
     unsigned int *queue = nullptr;
@@ -282,6 +286,8 @@ size_t layout(const Geom &G, int nb, bool pot, bool fp64, Work *w, unsigned char
     const size_t o_n64 = c.take<double>(N);
     const size_t o_blo = c.take<float4>(tiles);
     const size_t o_bhi = c.take<float4>(tiles);
+    const size_t o_clo = G.skew ? c.take<float4>(tiles) : 0;
+    const size_t o_chi = G.skew ? c.take<float4>(tiles) : 0;
     const size_t o_A = pot ? c.take<double>(N) : 0;
     const size_t o_U = pot ? c.take<double>(N) : 0;
     const size_t o_st = c.take<Stats>(1);
@@ -300,6 +306,8 @@ size_t layout(const Geom &G, int nb, bool pot, bool fp64, Work *w, unsigned char
         w->n64 = reinterpret_cast<double *>(base + o_n64);
         w->blo = reinterpret_cast<float4 *>(base + o_blo);
         w->bhi = reinterpret_cast<float4 *>(base + o_bhi);
+        w->clo = G.skew ? reinterpret_cast<float4 *>(base + o_clo) : nullptr;
+        w->chi = G.skew ? reinterpret_cast<float4 *>(base + o_chi) : nullptr;
         w->A = pot ? reinterpret_cast<double *>(base + o_A) : nullptr;
         w->U = pot ? reinterpret_cast<double *>(base + o_U) : nullptr;
         w->stats = reinterpret_cast<Stats *>(base + o_st);
@@ -325,8 +333,10 @@ int prepare(const Geom &G, const double *n_dev, const double *grad_dev, double n
     if (rc) return rc;
     rc = launch_grad_q0(G.dims, G.am, n_dev, grad_dev, w.q0, w.qn, w.qg, st);
     if (rc) return rc;
-    return launch_compact(G.dims, n_dev, n_cut, w.q0, order, nb, w.cnt, w.off, pot ? w.slot : nullptr,
-                          w.p32, w.n32, w.p64, w.n64, w.blo, w.bhi, w.stats, st);
+    rc = launch_compact(G.dims, n_dev, n_cut, w.q0, order, nb, w.cnt, w.off, pot ? w.slot : nullptr,
+                        w.p32, w.n32, w.p64, w.n64, w.blo, w.bhi, w.stats, st);
+    if (rc || !G.skew) return rc;
+    return launch_tiles_cart(w.p32, w.stats, G.vrow, w.clo, w.chi, G.N, st);
 }
 
 void fill_params(const Geom &G, const Work &w, PairParams &pp) {
@@ -352,6 +362,9 @@ void fill_params(const Geom &G, const Work &w, PairParams &pp) {
     pp.n64 = w.n64;
     pp.blo = w.blo;
     pp.bhi = w.bhi;
+    pp.clo = w.clo;
+    pp.chi = w.chi;
+    pp.vrow = G.vrow;
     pp.A = w.A;
     pp.U = w.U;
     pp.stats = w.stats;
@@ -1200,6 +1213,10 @@ int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const doub
     rc = launch_compact(G.dims, n_dev, n_cut, w.q0, order_dev, nb, w.cnt, w.off, nullptr, w.p32, w.n32,
                         w.p64, w.n64, w.blo, w.bhi, w.stats, st);
     if (rc) return rc;
+    if (G.skew) {
+        rc = launch_tiles_cart(w.p32, w.stats, G.vrow, w.clo, w.chi, G.N, st);
+        if (rc) return rc;
+    }
     Stats hs;
     std::memset(&hs, 0, sizeof(hs));
     VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));

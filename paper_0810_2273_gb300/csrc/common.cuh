@@ -51,6 +51,12 @@ struct AxisMap {
     int general;
 };
 
+// Rows v_a = M_a / N_a of a general cell (float): grid point (i, j, k) sits at
+// i v_0 + j v_1 + k v_2.
+struct CellRows {
+    float v[9];
+};
+
 // Per-instance inputs of the pair kernel.
 struct PairParams {
     double h2[3];        // metric in index units, diagonal: |M_a|^2 / N_a^2
@@ -68,6 +74,8 @@ struct PairParams {
     const dvec4 *p64;
     const double *n64;
     const float4 *blo, *bhi;  // bounding boxes of kTile-point tiles (index units)
+    const float4 *clo, *chi;  // skewed cells: Cartesian bounding boxes of the tiles
+    CellRows vrow;            // skewed cells: v_a = M_a / N_a
     double *A, *U;       // potential mode: per active point, accumulated
     Stats *stats;
 };
@@ -101,6 +109,9 @@ struct PairLaunch {
 int semilocal_scratch_doubles();
 int launch_semilocal(const int dims[3], const AxisMap &am, const double *n, const double *grad_in,
                      double *scratch, cudaStream_t st);
+// Cartesian bounding boxes of the tiles of a general cell (rows v_a = M_a / N_a).
+int launch_tiles_cart(const float4 *p32, const Stats *stats, const CellRows &vrow, float4 *clo, float4 *chi,
+                      long long n_max, cudaStream_t st);
 int launch_grad_q0(const int dims[3], const AxisMap &am, const double *n, const double *grad_in,
                    double *q0, double *dq0dn, double *dq0dg, cudaStream_t st);
 int launch_compact(const int dims[3], const double *n, double n_cut, const double *q0,

@@ -373,6 +373,22 @@ __device__ __forceinline__ float box_gap2(const float ilo[3], const float ihi[3]
     return d2;
 }
 
+// Skewed cells: squared distance between the Cartesian box of the i tile shifted
+// by image m (L = sum_a m_a N_a v_a) and the Cartesian box of the j tile.
+__device__ __forceinline__ float box_gap2_cart(const float4 &il, const float4 &ih, const float4 &jl,
+                                               const float4 &jh, const int m[3], const int dims[3],
+                                               const CellRows &vr) {
+    const float s0 = static_cast<float>(m[0] * dims[0]), s1 = static_cast<float>(m[1] * dims[1]),
+                s2 = static_cast<float>(m[2] * dims[2]);
+    const float L0 = s0 * vr.v[0] + s1 * vr.v[3] + s2 * vr.v[6];
+    const float L1 = s0 * vr.v[1] + s1 * vr.v[4] + s2 * vr.v[7];
+    const float L2 = s0 * vr.v[2] + s1 * vr.v[5] + s2 * vr.v[8];
+    const float g0 = fmaxf(0.0f, fmaxf(il.x + L0 - jh.x, jl.x - ih.x - L0));
+    const float g1 = fmaxf(0.0f, fmaxf(il.y + L1 - jh.y, jl.y - ih.y - L1));
+    const float g2 = fmaxf(0.0f, fmaxf(il.z + L2 - jh.z, jl.z - ih.z - L2));
+    return g0 * g0 + g1 * g1 + g2 * g2;
+}
+
 // Per-warp running totals, flushed to the instance's counters when the warp
 // moves to another instance and at exit (lane 0 holds the warp's total).
 struct WarpTotals {
@@ -652,6 +668,11 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
         const R inv_qi = R(1) / qi, qi2 = qi * qi;
         const float4 ib0 = __ldg(pp.blo + I), ib1 = __ldg(pp.bhi + I);
         const float ilo[3] = {ib0.x, ib0.y, ib0.z}, ihi[3] = {ib1.x, ib1.y, ib1.z};
+        float4 cil = make_float4(0.f, 0.f, 0.f, 0.f), cih = cil;  // skewed: Cartesian i box
+        if (SKEW) {
+            cil = __ldg(pp.clo + I);
+            cih = __ldg(pp.chi + I);
+        }
         double A64 = 0.0, U64 = 0.0;
         unsigned int cnt = 0, nclamp = 0;
         for (int J = J0; J < J1; ++J) {
@@ -673,6 +694,11 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
                 }
             }
             const int n_cand = nm[0] * nm[1] * nm[2];
+            float4 cjl = make_float4(0.f, 0.f, 0.f, 0.f), cjh = cjl;  // skewed: Cartesian j box
+            if (SKEW) {
+                cjl = __ldg(pp.clo + J);
+                cjh = __ldg(pp.chi + J);
+            }
             const bool diag = (J == I);
             bool staged = false;
             // candidate images in chunks of 32, one per lane
@@ -685,7 +711,10 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
                     const int t1 = t / nm[2];
                     mm[1] = mlo[1] + t1 % nm[1];
                     mm[0] = mlo[0] + t1 / nm[1];
-                    ok = !use_cut || box_gap2(ilo, ihi, jl, jh, mm, dims, cull) <= rc2_box;
+                    if (SKEW)
+                        ok = !use_cut || box_gap2_cart(cil, cih, cjl, cjh, mm, dims, pp.vrow) <= rc2_box;
+                    else
+                        ok = !use_cut || box_gap2(ilo, ihi, jl, jh, mm, dims, cull) <= rc2_box;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, ok);
                 if (bal == 0u) continue;
@@ -717,10 +746,24 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
                         const P sft = simg[b];
                         const float sx = static_cast<float>(sft.x), sy = static_cast<float>(sft.y),
                                     sz = static_cast<float>(sft.z);
-                        const float gx = fmaxf(0.0f, fmaxf(ilo[0] + sx - px, px - ihi[0] - sx));
-                        const float gy = fmaxf(0.0f, fmaxf(ilo[1] + sy - py, py - ihi[1] - sy));
-                        const float gz = fmaxf(0.0f, fmaxf(ilo[2] + sz - pz, pz - ihi[2] - sz));
-                        const float d2 = cull[0] * gx * gx + cull[1] * gy * gy + cull[2] * gz * gz;
+                        float d2;
+                        if (SKEW) {
+                            // the point less the shift, in Cartesian coordinates, against the i box
+                            const float ux = px - sx, uy = py - sy, uz = pz - sz;
+                            const CellRows &vr = pp.vrow;
+                            const float q0c = ux * vr.v[0] + uy * vr.v[3] + uz * vr.v[6];
+                            const float q1c = ux * vr.v[1] + uy * vr.v[4] + uz * vr.v[7];
+                            const float q2c = ux * vr.v[2] + uy * vr.v[5] + uz * vr.v[8];
+                            const float gx = fmaxf(0.0f, fmaxf(cil.x - q0c, q0c - cih.x));
+                            const float gy = fmaxf(0.0f, fmaxf(cil.y - q1c, q1c - cih.y));
+                            const float gz = fmaxf(0.0f, fmaxf(cil.z - q2c, q2c - cih.z));
+                            d2 = gx * gx + gy * gy + gz * gz;
+                        } else {
+                            const float gx = fmaxf(0.0f, fmaxf(ilo[0] + sx - px, px - ihi[0] - sx));
+                            const float gy = fmaxf(0.0f, fmaxf(ilo[1] + sy - py, py - ihi[1] - sy));
+                            const float gz = fmaxf(0.0f, fmaxf(ilo[2] + sz - pz, pz - ihi[2] - sz));
+                            d2 = cull[0] * gx * gx + cull[1] * gy * gy + cull[2] * gz * gz;
+                        }
                         if (!use_cut || d2 <= rc2_box) jm |= 1u << b;
                     }
                 }

@@ -269,6 +269,36 @@ __global__ void k_tiles(const float4 *__restrict__ p32, const double *__restrict
     }
 }
 
+// Cartesian bounding boxes of the kTile-point tiles on a general cell: point
+// (i, j, k) sits at i v_0 + j v_1 + k v_2 with v_a = M_a / N_a (rows of vrow).
+__global__ void k_tiles_cart(const float4 *__restrict__ p32, const Stats *stats, const CellRows vrow,
+                             float4 *__restrict__ clo, float4 *__restrict__ chi, int ntiles_max) {
+    const int na = stats->n_active;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= ntiles_max || t * kTile >= na) return;
+    const int i = t * kTile + lane;
+    const bool in = i < na;
+    const float4 p = in ? p32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float lo[3], hi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float x = p.x * vrow.v[c] + p.y * vrow.v[3 + c] + p.z * vrow.v[6 + c];
+        lo[c] = in ? x : 3e38f;
+        hi[c] = in ? x : -3e38f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    if (lane == 0) {
+        clo[t] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        chi[t] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Semilocal energies of eq. (3) (section 2: E_x^LDA, E_c^LDA, E_x^PBE, E_c^PBE
@@ -358,6 +388,15 @@ int launch_semilocal(const int dims[3], const AxisMap &am, const double *n, cons
     k_semilocal<<<kSemiBlocks, kSemiThreads, 0, st>>>(dims[0], dims[1], dims[2], am, n, grad_in, scratch);
     k_semilocal_sum<<<1, 32, 0, st>>>(scratch, kSemiBlocks, scratch + kSemiBlocks * kSemiVals);
     count_launches(2);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
+}
+
+int launch_tiles_cart(const float4 *p32, const Stats *stats, const CellRows &vrow, float4 *clo, float4 *chi,
+                      long long n_max, cudaStream_t st) {
+    const int tiles = static_cast<int>((n_max + kTile - 1) / kTile);
+    k_tiles_cart<<<(tiles + 7) / 8, 256, 0, st>>>(p32, stats, vrow, clo, chi, tiles);
+    count_launches(1);
     VDWDF_CUDA_TRY(cudaGetLastError());
     return VDWDF_OK;
 }
