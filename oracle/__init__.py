@@ -82,6 +82,8 @@ def lib():
         L.orc_gradient_cell.argtypes = [_i, _i, _i, _p, _p, _p]
         L.orc_gradient_T_cell.restype = _i
         L.orc_gradient_T_cell.argtypes = [_i, _i, _i, _p, _p, _p]
+        L.orc_phi0_many.restype = _i
+        L.orc_phi0_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _p, _i, _p, _p, _i, _i]
         L.orc_fx_many.restype = _i
         L.orc_fx_many.argtypes = [_i, _p, _d, _p]
         L.orc_pbe_H_many.restype = _i
@@ -207,6 +209,17 @@ class Spline:
         p, pD, pd = (np.zeros_like(D) for _ in range(3))
         lib().orc_spline_eval_many(*self._args(), len(D), _ptr(D), _ptr(dl), _ptr(p), _ptr(pD), _ptr(pd))
         return p, pD, pd
+
+    def phi0(self, vox, q, panels=6, npts=6):
+        """Voxel-averaged kernel at delta = 0, phi0(q), for the voxel spanned by the
+        rows of vox (v_a = M_a / N_a), at each q (see orc_phi0_many)."""
+        vox = _f64(vox).reshape(3, 3)
+        q = np.atleast_1d(_f64(q))
+        out = np.zeros_like(q)
+        rc = lib().orc_phi0_many(*self._kargs(), _ptr(vox), len(q), _ptr(q), _ptr(out), int(panels), int(npts))
+        if rc != 0:
+            raise RuntimeError("orc_phi0_many failed (%d)" % rc)
+        return out
 
     def kernel(self, r, qi, qj):
         """phi and r dphi/dd1 for pairs (d1 = qi r, d2 = qj r); returns (phi, rdphi1, nclamped)."""
@@ -475,6 +488,19 @@ class Problem:
                         val += c4[o + 2] * Umap[ss] * float(np.dot(Bs[ax], qg[:, mm]))
             out[t] = self.dV * val
         return out
+
+    def voxel(self):
+        """Rows v_a = M_a / N_a spanning one voxel."""
+        cell = np.diag(self.lengths) if self.cell is None else self.cell
+        return cell / np.array(self.dims, dtype=float)[:, None]
+
+    def diag_voxel(self, panels=5, npts=5):
+        """The voxel-averaged self term 1/2 dV^2 sum_i n_i^2 phi0(q_i) over the active
+        points (each phi0 by direct quadrature), and the table self term it replaces."""
+        p0 = self.spline.phi0(self.voxel(), self.qa, panels, npts)
+        E = 0.5 * self.dV ** 2 * float(np.dot(self.na * self.na, p0))
+        E_tab = 0.5 * self.dV ** 2 * float(np.dot(self.na, self.na)) * self.spline.f[0, 0]
+        return dict(E_diag_voxel=E, E_diag_table=E_tab, phi0=p0)
 
     def brute_energy(self, quad=QUAD_FAST):
         """E from direct quadrature of eq. (14) at every pair (no table)."""

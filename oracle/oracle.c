@@ -41,6 +41,9 @@
  *   orc_gradient_T_cell             invariance of E, exact Fourier symbol of
  *                                   the skewed gradient, adjoint identity,
  *                                   brute-force pair counts
+ *   orc_phi0_many                   pinned: large-voxel limit fixed by the
+ *                                   kernel's D^3 moment, small-voxel
+ *                                   logarithmic limit, Monte Carlo average
  *   paper-level energies            parity unpinned: the paper's Xe density
  *                                   file is not available
  */
@@ -1012,5 +1015,83 @@ int orc_gradient_T_cell(int n0, int n1, int n2, const double *cell, const double
                     }
                 out[m] = s;
             }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Voxel-averaged diagonal ("phi0").  The paper's Appendix A output shows   */
+/* a separate diagonal step (nphi0, E_DIAG_nlc) but the paper does not     */
+/* describe it.  Reading: with n and q0 constant over voxel i, the i = j,  */
+/* L = 0 term of eq. (1) is 1/2 n_i^2 dV^2 phi0(q_i) with                 */
+/*   phi0(q) = int_{[-1,1]^3} prod_a (1 - |t_a|) phi_0(q |sum_a t_a v_a|) d^3t, */
+/* the kernel at delta = 0 averaged over pairs of points of one voxel      */
+/* (v_a = M_a / N_a: r - r' = sum_a t_a v_a with t_a the difference of two */
+/* uniform variables, density 1 - |t_a|).  phi_0(D) is the kernel of       */
+/* orc_kernel_many at delta = 0 for D >= D_1 (first table node after 0);    */
+/* below D_1, where eq. (14) diverges like -(2/pi) ln D and the table's row */
+/* 0 is softened, phi_0 = -(2/pi) ln D + psi0 + c2 D^2 with psi = phi +     */
+/* (2/pi) ln D fitted at the nodes D_1, D_2 (psi0 = (4 psi1 - psi2)/3,      */
+/* c2 = (psi1 - psi0) / D_1^2).  The singularity is integrable.            */
+/* Quadrature: the eight sign octants of t, in each a tensor Gauss-Legendre */
+/* rule on geometric panels [0, 2^-(P-1)], ..., [1/4, 1/2], [1/2, 1] per     */
+/* axis (np points per panel), graded towards the singular corner t = 0.   */
+/* ---------------------------------------------------------------------- */
+static double phi_delta0(const orc_spline *s, double Dmax, double D, double D1, double psi0, double c2)
+{
+    if (D < D1) return -(2.0 / M_PI) * log(D) + psi0 + c2 * D * D;
+    double p, rd;
+    int cl = 0;
+    kernel_pair(s, Dmax, D, 1.0, 1.0, &p, &rd, &cl);
+    return p;
+}
+
+int orc_phi0_many(int nD, double hD, int nd, double hd, const double *f,
+                  const double *fDD, const double *fdd, const double *fDDdd,
+                  const double *rho, const double *rhoM, const double *vox,
+                  int nq, const double *q, double *out, int panels, int np)
+{
+    if (panels < 1 || np < 1 || np > 64 || nD < 3) return -1;
+    orc_spline s = {nD, nd, hD, hd, f, fDD, fdd, fDDdd, rho, rhoM};
+    double Dmax = (nD - 1) * hD;
+    double D1 = hD, D2 = 2.0 * hD;
+    double psi1 = f[(size_t)1 * nd] + (2.0 / M_PI) * log(D1);
+    double psi2 = f[(size_t)2 * nd] + (2.0 / M_PI) * log(D2);
+    double psi0 = (4.0 * psi1 - psi2) / 3.0;
+    double c2 = (psi1 - psi0) / (D1 * D1);
+    /* 1-D composite rule on [0, 1] */
+    double gx[64], gw[64];
+    gl_rule(np, gx, gw);
+    int nn = panels * np;
+    double *x = (double *)malloc(sizeof(double) * nn), *w = (double *)malloc(sizeof(double) * nn);
+    if (!x || !w) { free(x); free(w); return -2; }
+    for (int p = 0; p < panels; ++p) {
+        double a = (p == 0) ? 0.0 : ldexp(1.0, p - panels);
+        double b = ldexp(1.0, p + 1 - panels);
+        for (int k = 0; k < np; ++k) {
+            /* gl_rule gives nodes and weights on [-1, 1] */
+            x[p * np + k] = 0.5 * (a + b) + 0.5 * (b - a) * gx[k];
+            w[p * np + k] = 0.5 * (b - a) * gw[k];
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < nq; ++t) {
+        double acc = 0.0;
+        for (int sg = 0; sg < 8; ++sg) {
+            double s0 = (sg & 1) ? -1.0 : 1.0, s1 = (sg & 2) ? -1.0 : 1.0, s2 = (sg & 4) ? -1.0 : 1.0;
+            for (int i = 0; i < nn; ++i)
+                for (int j = 0; j < nn; ++j)
+                    for (int k = 0; k < nn; ++k) {
+                        double t0 = s0 * x[i], t1 = s1 * x[j], t2 = s2 * x[k];
+                        double r[3];
+                        for (int c = 0; c < 3; ++c) r[c] = t0 * vox[c] + t1 * vox[3 + c] + t2 * vox[6 + c];
+                        double D = q[t] * sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                        double wt = w[i] * w[j] * w[k] * (1.0 - x[i]) * (1.0 - x[j]) * (1.0 - x[k]);
+                        acc += wt * phi_delta0(&s, Dmax, D, D1, psi0, c2);
+                    }
+        }
+        out[t] = acc;
+    }
+    free(x);
+    free(w);
     return 0;
 }
