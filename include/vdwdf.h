@@ -244,6 +244,53 @@ typedef struct {
 int vdwdf_semilocal(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev,
                     vdwdf_semilocal_result *out, void *cuda_stream);
 
+/* --------------------------------------------------------------------- */
+/* Voxel-averaged diagonal (the "phi0" step of the paper's Appendix A      */
+/* output; the paper does not describe its method)                        */
+/* --------------------------------------------------------------------- */
+
+typedef struct {
+    double E_diag_voxel;   /* 1/2 dV^2 sum_i n_i^2 phi0(q0_i), Hartree            */
+    double E_diag_table;   /* the self term the pair sum uses,
+                              1/2 dV^2 sum_i n_i^2 phi(0, 0) (table row 0)        */
+    double q0_min, q0_max; /* over the points with n >= n_cut                      */
+    int64_t n_active;      /* points with n >= n_cut                              */
+    int32_t nphi0;         /* q points of the phi0 table                           */
+    float ms;              /* device time of the call                              */
+    int32_t launches;      /* kernels launched by the call                         */
+} vdwdf_diag_result;
+
+/* phi0(q) for the voxel spanned by the rows of voxel[9] (host; v_a = M_a / N_a,
+ * bohr) at nq values q_dev (device FP64) into phi0_dev (device FP64):
+ *   phi0(q) = int_{[-1,1]^3} prod_a (1 - |t_a|) phi_0(q |sum_a t_a v_a|) d^3t,
+ * the kernel at delta = 0 averaged over pairs of points of one voxel (r - r' =
+ * sum_a t_a v_a, t_a the difference of two uniform variables).  phi_0(D) is the
+ * pair sum's kernel at delta = 0 for D >= D_1 = Dmax/(nD - 1); below, where
+ * eq. 14 diverges like -(2/pi) ln D and the table's row 0 is softened, it is
+ * -(2/pi) ln D + psi0 + c2 D^2 with psi = phi + (2/pi) ln D fitted at the nodes
+ * D_1, D_2 (psi0 = (4 psi1 - psi2)/3, c2 = (psi1 - psi0)/D_1^2).  The eight
+ * sign octants times a 48-node graded Gauss rule per axis (agreement with a
+ * finer rule: ~1e-5 relative); integrand in FP32, sums in FP64.
+ * Synchronises the stream.  Errors: VDWDF_EINVAL, VDWDF_ENOTABLE, VDWDF_ECUDA,
+ * VDWDF_EALLOC. */
+int vdwdf_phi0_eval(const vdwdf_table *table, const double *voxel, int64_t nq, const double *q_dev,
+                    double *phi0_dev, void *cuda_stream);
+
+/* The voxel-averaged self term of the density (reading of the paper's
+ * undocumented diagonal step, printed there as E_DIAG_nlc): with n and q0
+ * constant over voxel i, the i = j, L = 0 term of eq. (1) is
+ *   1/2 dV^2 n_i^2 phi0(q0_i)
+ * (phi0 as in vdwdf_phi0_eval for the grid's voxel), summed over the points
+ * with n >= n_cut.  phi0 comes from a table of nphi0 (0: 100, the paper's
+ * nphi0) log-spaced q over the active q0 range, by 4-point Lagrange
+ * interpolation in ln q.  E_c^nl with this diagonal is
+ *   E (vdwdf_energy) - E_diag_table + E_diag_voxel.
+ * grad_dev as in vdwdf_q0.  Sums in a fixed order (reproducible).
+ * Synchronises the stream.  Errors: VDWDF_EINVAL, VDWDF_ENOTABLE,
+ * VDWDF_ECUDA, VDWDF_EALLOC. */
+int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
+                     const vdwdf_table *table, int nphi0, vdwdf_diag_result *out, void *cuda_stream);
+
 /* vdwdf_energy that allocates nothing.  The paper has no counterpart: JuNoLo
  * allocates its arrays once per run.  This entry point is for callers that
  * cannot allocate device memory while they run, for example:

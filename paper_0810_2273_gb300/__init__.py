@@ -14,11 +14,11 @@ import ctypes
 import numpy as np
 
 from . import _native
-from ._native import (VDWDF_FP32, VDWDF_FP64, VdwdfError, vdwdf_grid, vdwdf_result, vdwdf_semilocal_result,
-                      vdwdf_tuning)
+from ._native import (VDWDF_FP32, VDWDF_FP64, VdwdfError, vdwdf_diag_result, vdwdf_grid, vdwdf_result,
+                      vdwdf_semilocal_result, vdwdf_tuning)
 
 __all__ = ["Table", "grid", "energy", "energy_noalloc", "potential", "energy_batched", "q0", "kernel_eval",
-           "semilocal", "total_energy_nl",
+           "semilocal", "total_energy_nl", "phi0_eval", "diag_voxel",
            "autotune", "launch_count", "NonlocalEnergy", "nonlocal_energy", "VdwdfError",
            "VDWDF_FP32", "VDWDF_FP64"]
 
@@ -195,6 +195,40 @@ def semilocal(n, lengths, periodic, grad=None):
                                  ctypes.c_void_p(grad.data_ptr()) if grad is not None else None,
                                  ctypes.byref(res), _stream(n))
     _native.check(st, "vdwdf_semilocal")
+    return res.as_dict()
+
+
+def phi0_eval(table, voxel, q):
+    """The voxel-averaged kernel at delta = 0, phi0(q), for the voxel spanned by the
+    rows of ``voxel`` (3x3, bohr), at the values of the CUDA FP64 tensor q."""
+    _check_tensor(q, "q")
+    torch = _torch()
+    lib = _native.load()
+    vox = np.ascontiguousarray(np.asarray(voxel, dtype=np.float64).reshape(9))
+    out = torch.empty_like(q)
+    with torch.cuda.device(q.device):
+        st = lib.vdwdf_phi0_eval(table.handle, vox.ctypes.data_as(ctypes.c_void_p), int(q.numel()),
+                                 ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(out.data_ptr()), _stream(q))
+    _native.check(st, "vdwdf_phi0_eval")
+    return out
+
+
+def diag_voxel(n, lengths, periodic, n_cut, table, nphi0=0, grad=None):
+    """The voxel-averaged self term 1/2 dV^2 sum n_i^2 phi0(q0_i) over the points with
+    n >= n_cut, and the table self term it replaces; returns the result dict.  E_c^nl
+    with this diagonal is E - E_diag_table + E_diag_voxel."""
+    _check_tensor(n, "n")
+    if grad is not None:
+        _check_tensor(grad, "grad")
+    torch = _torch()
+    lib = _native.load()
+    g = grid(lengths, n.shape, periodic)
+    res = vdwdf_diag_result()
+    with torch.cuda.device(n.device):
+        st = lib.vdwdf_diag_voxel(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()),
+                                  ctypes.c_void_p(grad.data_ptr()) if grad is not None else None,
+                                  float(n_cut), table.handle, int(nphi0), ctypes.byref(res), _stream(n))
+    _native.check(st, "vdwdf_diag_voxel")
     return res.as_dict()
 
 

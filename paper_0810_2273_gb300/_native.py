@@ -42,6 +42,14 @@ class vdwdf_semilocal_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class vdwdf_diag_result(ctypes.Structure):
+    _fields_ = [("E_diag_voxel", _c_d), ("E_diag_table", _c_d), ("q0_min", _c_d), ("q0_max", _c_d),
+                ("n_active", _c_i64), ("nphi0", _c_i32), ("ms", ctypes.c_float), ("launches", _c_i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class vdwdf_tuning(ctypes.Structure):
     _fields_ = [("threads", _c_i32), ("items_per_sm", _c_i32), ("smem_rows", _c_i32),
                 ("smem_row0", _c_i32)]
@@ -66,6 +74,9 @@ PROTOTYPES = {
                                     ctypes.POINTER(vdwdf_result), _c_p]),
     "vdwdf_semilocal": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, ctypes.POINTER(vdwdf_semilocal_result),
                                _c_p]),
+    "vdwdf_phi0_eval": (_c_i, [_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p]),
+    "vdwdf_diag_voxel": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_d, _c_p, _c_i,
+                                ctypes.POINTER(vdwdf_diag_result), _c_p]),
     "vdwdf_energy_noalloc": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_d, _c_d, _c_p, _c_i,
                                     ctypes.POINTER(vdwdf_result), _c_p]),
     "vdwdf_autotune": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_d, _c_d, _c_p, _c_i,

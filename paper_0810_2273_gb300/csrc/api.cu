@@ -655,6 +655,66 @@ int record_batch(BatchPlan &bp, int ninst, const double *const *n_dev, double n_
     return VDWDF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// voxel-averaged diagonal: the quadrature rule and the small-D model
+// ---------------------------------------------------------------------------
+constexpr int kPhi0Panels = 6, kPhi0Points = 8;
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on the three-term recurrence).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pn = (n == 1) ? z : p1, pm = (n == 1) ? 1.0 : p0;
+            dp = n * (z * pn - pm) / (z * z - 1.0);
+            const double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Nodes then weights on [0, 1]: np-point Gauss rules on the geometric panels
+// [0, 2^-(P-1)], ..., [1/4, 1/2], [1/2, 1], graded towards the singular corner.
+void phi0_rule(std::vector<double> &xw) {
+    std::vector<double> gx, gw;
+    gauss_legendre(kPhi0Points, gx, gw);
+    const int nn = kPhi0Panels * kPhi0Points;
+    xw.assign(2 * nn, 0.0);
+    for (int p = 0; p < kPhi0Panels; ++p) {
+        const double a = (p == 0) ? 0.0 : std::ldexp(1.0, p - kPhi0Panels);
+        const double b = std::ldexp(1.0, p + 1 - kPhi0Panels);
+        for (int k = 0; k < kPhi0Points; ++k) {
+            xw[p * kPhi0Points + k] = 0.5 * (a + b) + 0.5 * (b - a) * gx[k];
+            xw[nn + p * kPhi0Points + k] = 0.5 * (b - a) * gw[k];
+        }
+    }
+}
+
+// The kernel at delta = 0 below D_1 = Dmax/(nD - 1): -(2/pi) ln D + psi0 + c2 D^2,
+// psi = phi + (2/pi) ln D fitted at the nodes D_1 and D_2.
+void phi0_model(const vdwdf_table *t, const double vox[9], Phi0Rule &rule) {
+    for (int k = 0; k < 9; ++k) rule.v[k] = vox[k];
+    const double D1 = t->Dmax / (t->nD - 1);
+    const double psi1 = t->nodes[static_cast<size_t>(1) * t->nd] + (2.0 / kPi) * std::log(D1);
+    const double psi2 = t->nodes[static_cast<size_t>(2) * t->nd] + (2.0 / kPi) * std::log(2.0 * D1);
+    rule.D1 = D1;
+    rule.psi0 = (4.0 * psi1 - psi2) / 3.0;
+    rule.c2 = (psi1 - rule.psi0) / (D1 * D1);
+    rule.nn = kPhi0Panels * kPhi0Points;
+}
+
 }  // namespace
 
 void note_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
@@ -833,6 +893,134 @@ int vdwdf_semilocal(const vdwdf_grid *grid, const double *n_dev, const double *g
     out->Ex_revpbe = G.dV * sums[4];
     out->n_points = static_cast<int64_t>(sums[5]);
     out->ms = tm.ms(0, 1);
+    out->launches = static_cast<int32_t>(g_launches.load() - launches0);
+    return VDWDF_OK;
+}
+
+int vdwdf_phi0_eval(const vdwdf_table *table, const double *voxel, int64_t nq, const double *q_dev,
+                    double *phi0_dev, void *cuda_stream) {
+    if (!table) return VDWDF_ENOTABLE;
+    if (!voxel || nq < 0 || nq > (1LL << 30) || (nq > 0 && (!q_dev || !phi0_dev))) return VDWDF_EINVAL;
+    for (int k = 0; k < 9; ++k)
+        if (!std::isfinite(voxel[k])) return VDWDF_EINVAL;
+    if (table->nD < 3) return VDWDF_EINVAL;
+    if (nq == 0) return VDWDF_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    double *d64 = nullptr;
+    float *d32 = nullptr;
+    int rc = table_on_device(table, &d64, &d32);
+    if (rc) return rc;
+    Phi0Rule rule;
+    phi0_model(table, voxel, rule);
+    std::vector<double> xw;
+    phi0_rule(xw);
+    double *xw_dev = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&xw_dev), sizeof(double) * (xw.size() + 8 * nq), st) !=
+        cudaSuccess)
+        return VDWDF_EALLOC;
+    Launch ln;
+    PairShared sh;
+    std::memset(&sh, 0, sizeof(sh));
+    fill_shared(table, d64, d32, ln, nullptr, 0, sh);
+    if (cudaMemcpyAsync(xw_dev, xw.data(), sizeof(double) * xw.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = VDWDF_ECUDA;
+    if (rc == VDWDF_OK)
+        rc = launch_phi0(sh, rule, static_cast<int>(nq), q_dev, xw_dev, xw_dev + xw.size(), phi0_dev, st);
+    cudaFreeAsync(xw_dev, st);
+    if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
+    return rc;
+}
+
+int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
+                     const vdwdf_table *table, int nphi0, vdwdf_diag_result *out, void *cuda_stream) {
+    Geom G;
+    int rc = check_grid(grid, G);
+    if (rc) return rc;
+    if (!n_dev || !out) return VDWDF_EINVAL;
+    if (!(n_cut > 0.0) || !std::isfinite(n_cut)) return VDWDF_EINVAL;
+    if (!table) return VDWDF_ENOTABLE;
+    const int nq = nphi0 == 0 ? 100 : nphi0;
+    if (nq < 4 || nq > 100000) return VDWDF_EINVAL;
+    if (table->nD < 3) return VDWDF_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const long long launches0 = g_launches.load();
+    double *d64 = nullptr;
+    float *d32 = nullptr;
+    rc = table_on_device(table, &d64, &d32);
+    if (rc) return rc;
+    Phi0Rule rule;
+    double vox[9];
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) vox[3 * a + c] = grid->cell[a][c] / G.dims[a];
+    phi0_model(table, vox, rule);
+    std::vector<double> xw;
+    phi0_rule(xw);
+    // scratch: q0 [N], range (3), block sums (2 x 608), sums (2), q grid and table [nq], rule nodes
+    Carve c;
+    const size_t o_q0 = c.take<double>(G.N), o_mm = c.take<unsigned long long>(3), o_part = c.take<double>(2 * 608),
+                 o_sums = c.take<double>(2), o_qg = c.take<double>(nq), o_tab = c.take<double>(nq),
+                 o_xw = c.take<double>(xw.size()), o_op = c.take<double>(8 * static_cast<size_t>(nq));
+    unsigned char *base = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&base), c.off, st) != cudaSuccess) return VDWDF_EALLOC;
+    double *q0 = reinterpret_cast<double *>(base + o_q0);
+    unsigned long long *mm = reinterpret_cast<unsigned long long *>(base + o_mm);
+    double *part = reinterpret_cast<double *>(base + o_part), *sums = reinterpret_cast<double *>(base + o_sums);
+    double *qg = reinterpret_cast<double *>(base + o_qg), *tab = reinterpret_cast<double *>(base + o_tab);
+    double *xw_dev = reinterpret_cast<double *>(base + o_xw), *opart = reinterpret_cast<double *>(base + o_op);
+    Timer tm;
+    unsigned long long hmm[3] = {0, 0, 0};
+    double hs[2] = {0.0, 0.0};
+    std::vector<double> qh(nq);
+    double lnq0 = 0.0, dlnq = 1.0;
+    auto body = [&]() -> int {
+        tm.mark(0, st);
+        int r = launch_grad_q0(G.dims, G.am, n_dev, grad_dev, q0, nullptr, nullptr, st);
+        if (r) return r;
+        VDWDF_CUDA_TRY(cudaMemsetAsync(mm, 0xFF, sizeof(unsigned long long), st));
+        VDWDF_CUDA_TRY(cudaMemsetAsync(mm + 1, 0, 2 * sizeof(unsigned long long), st));
+        r = launch_diag_range(G.N, n_dev, q0, n_cut, mm, st);
+        if (r) return r;
+        VDWDF_CUDA_TRY(cudaMemcpyAsync(hmm, mm, sizeof(hmm), cudaMemcpyDeviceToHost, st));
+        VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hmm[2] == 0) return VDWDF_OK;
+        double qmin, qmax;
+        std::memcpy(&qmin, &hmm[0], 8);
+        std::memcpy(&qmax, &hmm[1], 8);
+        // log-spaced table, slightly wider than the range so that every q0 interpolates inside
+        const double lo = std::log(qmin), hi = std::log(qmax);
+        const double pad = 1e-6 + 1e-9 * std::fabs(hi);
+        lnq0 = lo - pad;
+        dlnq = (hi + pad - lnq0) / (nq - 1);
+        for (int k = 0; k < nq; ++k) qh[k] = std::exp(lnq0 + k * dlnq);
+        VDWDF_CUDA_TRY(cudaMemcpyAsync(qg, qh.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+        VDWDF_CUDA_TRY(cudaMemcpyAsync(xw_dev, xw.data(), sizeof(double) * xw.size(), cudaMemcpyHostToDevice, st));
+        Launch ln;
+        PairShared sh;
+        std::memset(&sh, 0, sizeof(sh));
+        fill_shared(table, d64, d32, ln, nullptr, 0, sh);
+        r = launch_phi0(sh, rule, nq, qg, xw_dev, opart, tab, st);
+        if (r) return r;
+        r = launch_diag_sum(G.N, n_dev, q0, n_cut, tab, nq, lnq0, dlnq, part, sums, st);
+        if (r) return r;
+        tm.mark(1, st);
+        VDWDF_CUDA_TRY(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+        return VDWDF_OK;
+    };
+    rc = body();
+    cudaFreeAsync(base, st);
+    if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
+    if (rc) return rc;
+    std::memset(out, 0, sizeof(*out));
+    out->n_active = static_cast<int64_t>(hmm[2]);
+    out->nphi0 = nq;
+    if (hmm[2]) {
+        std::memcpy(&out->q0_min, &hmm[0], 8);
+        std::memcpy(&out->q0_max, &hmm[1], 8);
+        out->E_diag_voxel = 0.5 * G.dV * G.dV * hs[0];
+        out->E_diag_table = 0.5 * G.dV * G.dV * hs[1] * table->nodes[0];
+        out->ms = tm.ms(0, 1);
+    }
     out->launches = static_cast<int32_t>(g_launches.load() - launches0);
     return VDWDF_OK;
 }

@@ -83,7 +83,117 @@ __global__ void k_energy_from_A(int n_max, const double *__restrict__ A, const d
     }
 }
 
+// ---------------------------------------------------------------------------
+// Voxel-averaged diagonal: grid passes over the points with n >= n_cut.
+// ---------------------------------------------------------------------------
+constexpr int kDiagBlocks = 608;
+constexpr int kDiagThreads = 256;
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// q0 > 0 at active points, so the bit patterns of the doubles order like the values
+__global__ void k_diag_range(long long N, const double *__restrict__ n, const double *__restrict__ q0,
+                             double n_cut, unsigned long long *mm) {
+    unsigned long long lo = ~0ull, hi = 0ull, cnt = 0ull;
+    for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < N;
+         m += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (n[m] >= n_cut) {
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(q0[m]));
+            lo = b < lo ? b : lo;
+            hi = b > hi ? b : hi;
+            ++cnt;
+        }
+    }
+    lo = warp_min_u64(lo);
+    hi = warp_max_u64(hi);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) {
+        atomicMin(&mm[0], lo);
+        atomicMax(&mm[1], hi);
+        atomicAdd(&mm[2], cnt);
+    }
+}
+
+__global__ void __launch_bounds__(kDiagThreads) k_diag_sum(long long N, const double *__restrict__ n,
+                                                           const double *__restrict__ q0, double n_cut,
+                                                           const double *__restrict__ tab, int nq,
+                                                           double lnq0, double dlnq, double *__restrict__ part) {
+    double s0 = 0.0, s1 = 0.0;
+    for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < N;
+         m += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double nn = n[m];
+        if (!(nn >= n_cut)) continue;
+        // 4-point Lagrange interpolation in ln q on the uniform table
+        const double x = (log(q0[m]) - lnq0) / dlnq;
+        int k = static_cast<int>(floor(x));
+        k = max(1, min(nq - 3, k));
+        const double u = x - k;
+        const double lm = -u * (u - 1.0) * (u - 2.0) / 6.0, l0 = (u + 1.0) * (u - 1.0) * (u - 2.0) / 2.0,
+                     l1 = -(u + 1.0) * u * (u - 2.0) / 2.0, l2 = (u + 1.0) * u * (u - 1.0) / 6.0;
+        const double p0 = lm * tab[k - 1] + l0 * tab[k] + l1 * tab[k + 1] + l2 * tab[k + 2];
+        s0 += nn * nn * p0;
+        s1 += nn * nn;
+    }
+    __shared__ double r0[kDiagThreads], r1[kDiagThreads];
+    r0[threadIdx.x] = s0;
+    r1[threadIdx.x] = s1;
+    __syncthreads();
+    for (int o = kDiagThreads / 2; o > 0; o >>= 1) {
+        if (static_cast<int>(threadIdx.x) < o) {
+            r0[threadIdx.x] += r0[threadIdx.x + o];
+            r1[threadIdx.x] += r1[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = r0[0];
+        part[2 * blockIdx.x + 1] = r1[0];
+    }
+}
+
+__global__ void k_diag_final(const double *__restrict__ part, int nb, double *__restrict__ sums) {
+    if (threadIdx.x < 2) {
+        double v = 0.0;
+        for (int b = 0; b < nb; ++b) v += part[2 * b + threadIdx.x];
+        sums[threadIdx.x] = v;
+    }
+}
+
 }  // namespace
+
+int launch_diag_range(long long N, const double *n, const double *q0, double n_cut, unsigned long long *mm,
+                      cudaStream_t st) {
+    k_diag_range<<<kDiagBlocks, kDiagThreads, 0, st>>>(N, n, q0, n_cut, mm);
+    count_launches(1);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
+}
+
+// part: 2 kDiagBlocks doubles of scratch
+int launch_diag_sum(long long N, const double *n, const double *q0, double n_cut, const double *tab, int nq,
+                    double lnq0, double dlnq, double *part, double *sums, cudaStream_t st) {
+    k_diag_sum<<<kDiagBlocks, kDiagThreads, 0, st>>>(N, n, q0, n_cut, tab, nq, lnq0, dlnq, part);
+    k_diag_final<<<1, 32, 0, st>>>(part, kDiagBlocks, sums);
+    count_launches(2);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
+}
 
 int launch_assemble(const int dims[3], const AxisMap &am, double dV, const int *slot,
                     const double *A, const double *U, const double *dq0dn, const double *dq0dg,

@@ -138,6 +138,24 @@ int launch_assemble(const int dims[3], const AxisMap &am, double dV, const int *
                     double *v, double *A_grid, double *U_grid, cudaStream_t st);
 int launch_energy_from_A(int n_max, const double *A, const double *n64, Stats *stats,
                          cudaStream_t st);
+// Voxel-averaged diagonal: voxel rows v (M_a / N_a), the small-D model below D1
+// and the tensor rule (nn nodes per axis on [0, 1]; xw = nodes then weights).
+struct Phi0Rule {
+    double v[9];
+    double D1, psi0, c2;
+    int nn;
+};
+// part: 8 nq doubles of scratch (one per q and sign octant)
+int launch_phi0(const PairShared &sh, const Phi0Rule &rule, int nq, const double *q, const double *xw,
+                double *part, double *out, cudaStream_t st);
+// Grid passes of the diagonal: q0 range and count of the points with n >= n_cut
+// (mm[0] = min bits, mm[1] = max bits of the positive doubles, mm[2] = count),
+// then sums[0] = sum n^2 phi0(q0) (phi0 from the log-q table by 4-point
+// Lagrange interpolation) and sums[1] = sum n^2, one pair per block in part.
+int launch_diag_range(long long N, const double *n, const double *q0, double n_cut,
+                      unsigned long long *mm, cudaStream_t st);
+int launch_diag_sum(long long N, const double *n, const double *q0, double n_cut, const double *tab,
+                    int nq, double lnq0, double dlnq, double *part, double *sums, cudaStream_t st);
 int launch_kernel_eval(int precision, const PairShared &sh, int64_t npts, const double *r,
                        const double *qi, const double *qj, double *phi, double *rdphi,
                        cudaStream_t st);

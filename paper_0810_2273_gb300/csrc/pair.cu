@@ -881,6 +881,68 @@ __global__ void k_reduce_items(const __grid_constant__ PairLaunch pl) {
     if (threadIdx.x == 0) atomicAdd(&pl.inst[k].stats->E_pair, part[0]);
 }
 
+// Voxel-averaged kernel at delta = 0 (the diagonal "phi0" step):
+//   phi0(q) = int_{[-1,1]^3} prod_a (1 - |t_a|) phi_0(q |sum_a t_a v_a|) d^3t,
+// phi_0(D) the kernel at delta = 0 for D >= D_1 and -(2/pi) ln D + psi0 + c2 D^2
+// below (the divergence of eq. 14 at D -> 0 that the table's row 0 softens).
+// Block (q, octant): one of the eight sign octants of t times a tensor rule of
+// nn nodes (x, w on [0, 1]) per axis.  The integrand is evaluated in FP32 (the
+// FP32 table path, errors ~1e-7 relative per term, far below the rule's
+// ~1e-5) and summed in FP64; the octant sums are added in a fixed order.
+__global__ void k_phi0(const PairShared sh, Phi0Rule rule, const double *__restrict__ q,
+                       const double *__restrict__ xw, double *__restrict__ part) {
+    Table<float> tb;
+    make_table<float>(sh, tb);
+    Consts<float> K;
+    make_consts<float>(sh, K);
+    const int nn = rule.nn;
+    const float qq = static_cast<float>(q[blockIdx.x]);
+    const int sg = blockIdx.y;
+    const float s0 = (sg & 1) ? -1.0f : 1.0f, s1 = (sg & 2) ? -1.0f : 1.0f, s2 = (sg & 4) ? -1.0f : 1.0f;
+    float v[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = static_cast<float>(rule.v[k]);
+    const float D1 = static_cast<float>(rule.D1), psi0 = static_cast<float>(rule.psi0),
+                c2 = static_cast<float>(rule.c2);
+    const int total = nn * nn * nn;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int i = e / (nn * nn), j = (e / nn) % nn, k = e % nn;
+        const float t0 = s0 * static_cast<float>(xw[i]), t1 = s1 * static_cast<float>(xw[j]),
+                    t2 = s2 * static_cast<float>(xw[k]);
+        const float r0 = t0 * v[0] + t1 * v[3] + t2 * v[6];
+        const float r1 = t0 * v[1] + t1 * v[4] + t2 * v[7];
+        const float r2 = t0 * v[2] + t1 * v[5] + t2 * v[8];
+        const float D = qq * sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
+        float phi;
+        if (D < D1) {
+            phi = -0.63661977236758134f * logf(D) + psi0 + c2 * D * D;
+        } else {
+            float rd = 0.0f, rd2 = 0.0f;
+            unsigned ncl = 0;
+            pair_phi<false, float>(D * D, 1.0f, 1.0f, 1.0f, 1.0f, K, tb, phi, rd, rd2, ncl);
+        }
+        const double wt = xw[nn + i] * xw[nn + j] * xw[nn + k] * (1.0 - xw[i]) * (1.0 - xw[j]) * (1.0 - xw[k]);
+        acc += wt * static_cast<double>(phi);
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (static_cast<int>(threadIdx.x) < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x * 8 + blockIdx.y] = red[0];
+}
+
+__global__ void k_phi0_sum(const double *__restrict__ part, int nq, double *__restrict__ out) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int o = 0; o < 8; ++o) s += part[t * 8 + o];
+        out[t] = s;
+    }
+}
+
 // The kernel at given (r, q_i, q_j), for isolated checks of the interpolation.
 template <typename R>
 __global__ void k_kernel_eval(const PairShared sh, int64_t npts, const double *r,
@@ -951,6 +1013,16 @@ int launch_reduce_items(const PairLaunch &pl, cudaStream_t st) {
     if (!pl.sh.item_E) return VDWDF_OK;
     k_reduce_items<<<pl.ninst, 256, 0, st>>>(pl);
     count_launches(1);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
+}
+
+int launch_phi0(const PairShared &sh, const Phi0Rule &rule, int nq, const double *q, const double *xw,
+                double *part, double *out, cudaStream_t st) {
+    if (nq <= 0) return VDWDF_OK;
+    k_phi0<<<dim3(nq, 8), 256, 0, st>>>(sh, rule, q, xw, part);
+    k_phi0_sum<<<(nq + 255) / 256, 256, 0, st>>>(part, nq, out);
+    count_launches(2);
     VDWDF_CUDA_TRY(cudaGetLastError());
     return VDWDF_OK;
 }

@@ -18,7 +18,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="xe_monolayer",
                     choices=["kr_dimer", "xe_monolayer", "xe_monolayer_hex", "molecule24", "slab_adsorbate"])
     ap.add_argument("--dims", type=int, nargs=3, default=None)
-    ap.add_argument("--mode", default="potential", choices=["potential", "energy", "semilocal"])
+    ap.add_argument("--mode", default="potential", choices=["potential", "energy", "semilocal", "diag"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--table", default=None)
@@ -44,6 +44,13 @@ def main(argv=None):
     for k in range(a.repeat):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        if a.mode == "diag":
+            res = V.diag_voxel(n, cell, w["periodic"], w["n_cut"], T)
+            torch.cuda.synchronize()
+            res.update(call=k, wall_ms=1e3 * (time.perf_counter() - t0), workload=a.workload,
+                       dims=list(n.shape), mode=a.mode)
+            print(json.dumps(res), flush=True)
+            continue
         if a.mode == "semilocal":
             res = V.semilocal(n, cell, w["periodic"])
             torch.cuda.synchronize()

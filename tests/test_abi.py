@@ -42,7 +42,8 @@ def test_struct_layouts_match_header(native, tmp_path):
     """ctypes structs vs the C compiler's layout of include/vdwdf.h."""
     import subprocess
     fields = {"vdwdf_grid": native.vdwdf_grid, "vdwdf_result": native.vdwdf_result,
-              "vdwdf_tuning": native.vdwdf_tuning, "vdwdf_semilocal_result": native.vdwdf_semilocal_result}
+              "vdwdf_tuning": native.vdwdf_tuning, "vdwdf_semilocal_result": native.vdwdf_semilocal_result,
+              "vdwdf_diag_result": native.vdwdf_diag_result}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "vdwdf.h"', "int main(void) {"]
     for s, cls in fields.items():
         src.append('printf("%s size %%zu\\n", sizeof(%s));' % (s, s))
@@ -106,6 +107,16 @@ def test_host_side_argument_errors(native):
     g.cell[2][0], g.cell[2][2] = 10.0, 0.0
     assert lib.vdwdf_semilocal(ctypes.byref(g), ctypes.c_void_p(8), None, ctypes.byref(sres), None) == -1
     g.cell[2][0], g.cell[2][2] = 0.0, 10.0
+    # voxel diagonal: no table, bad table size, null result
+    dres = native.vdwdf_diag_result()
+    assert lib.vdwdf_diag_voxel(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, None, 0, ctypes.byref(dres),
+                                None) == -6
+    assert lib.vdwdf_diag_voxel(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, ctypes.c_void_p(1), 2,
+                                ctypes.byref(dres), None) == -1
+    assert lib.vdwdf_diag_voxel(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, ctypes.c_void_p(1), 0, None,
+                                None) == -1
+    vox = (ctypes.c_double * 9)(*([0.3] * 9))
+    assert lib.vdwdf_phi0_eval(None, vox, 1, ctypes.c_void_p(8), ctypes.c_void_p(8), None) == -6
     # no-allocation energy: a grid larger than its static scratch holds is refused
     g.cell[0][1] = 0.0
     g.n[0], g.n[1], g.n[2] = 64, 64, 17
