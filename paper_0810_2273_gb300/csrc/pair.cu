@@ -340,23 +340,23 @@ __device__ __forceinline__ T warp_sum(T v) {
 // rounding count as inside in every path).  FP32 decides pairs clearly away from
 // the boundary and re-checks the rest in FP64 from the exact index offsets.
 struct Cut {
-    double rc2d;
-    double h2d[3];
-    double g2d[3];  // 2 x off-diagonal metric (skewed cells)
+    const PairParams *pp;  // FP64 metric and cutoff (kernel parameters), read only
+                           // by the recheck near the boundary
     float lo, hi;
 };
 template <bool SKEW>
 __device__ __forceinline__ bool beyond(float r2, float dx, float dy, float dz, const Cut &c) {
     if (r2 > c.hi) return true;
     if (r2 <= c.lo) return false;
+    const PairParams &p = *c.pp;
     const double X = dx, Y = dy, Z = dz;
-    double e = c.h2d[0] * (X * X) + c.h2d[1] * (Y * Y) + c.h2d[2] * (Z * Z);
-    if (SKEW) e += c.g2d[0] * (X * Y) + c.g2d[1] * (X * Z) + c.g2d[2] * (Y * Z);
-    return e > c.rc2d;
+    double e = p.h2[0] * (X * X) + p.h2[1] * (Y * Y) + p.h2[2] * (Z * Z);
+    if (SKEW) e += p.g2x[0] * (X * Y) + p.g2x[1] * (X * Z) + p.g2x[2] * (Y * Z);
+    return e > p.rc2;
 }
 template <bool SKEW>
 __device__ __forceinline__ bool beyond(double r2, double, double, double, const Cut &c) {
-    return r2 > c.rc2d;
+    return r2 > c.pp->rc2;
 }
 
 // Squared distance between the i box shifted by image m and the j box.
@@ -389,26 +389,15 @@ __device__ __forceinline__ float box_gap2_cart(const float4 &il, const float4 &i
     return g0 * g0 + g1 * g1 + g2 * g2;
 }
 
-// Per-warp running totals, flushed to the instance's counters when the warp
-// moves to another instance and at exit (lane 0 holds the warp's total).
-struct WarpTotals {
-    double E;
-    unsigned long long pairs, evals, clamped;
-    int inst;
-};
-
-__device__ __forceinline__ void flush(WarpTotals &t, const PairLaunch &pl, bool energy) {
-    const double E = warp_sum(t.E);
-    const unsigned long long pairs = warp_sum(t.pairs), clamped = warp_sum(t.clamped);
-    if (t.inst >= 0 && (threadIdx.x & 31) == 0) {
-        Stats *s = pl.inst[t.inst].stats;
-        if (energy && E != 0.0) atomicAdd(&s->E_pair, E);
-        if (pairs) atomicAdd(&s->pairs, pairs);
-        if (t.evals) atomicAdd(&s->evals, t.evals);
-        if (clamped) atomicAdd(&s->clamped, clamped);
+// The counters of a finished work item, summed over the warp and added by lane 0
+// to the instance's totals (integer atomics: the totals do not depend on order).
+__device__ __forceinline__ void count_item(Stats *s, unsigned cnt, unsigned nclamp, unsigned evals) {
+    const unsigned pairs = warp_sum(cnt), clamped = warp_sum(nclamp);
+    if ((threadIdx.x & 31) == 0) {
+        if (pairs) atomicAdd(&s->pairs, static_cast<unsigned long long>(pairs));
+        if (evals) atomicAdd(&s->evals, static_cast<unsigned long long>(evals));
+        if (clamped) atomicAdd(&s->clamped, static_cast<unsigned long long>(clamped));
     }
-    t.E = 0.0;
-    t.pairs = t.evals = t.clamped = 0;
 }
 
 // Two images of one (i, j) pair in the resident band, evaluated together: slot s
@@ -587,10 +576,6 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
     __syncthreads();  // the only block barrier: table band and item counts ready
     const unsigned int n_items = min(s_prefix[pl.ninst], sh.item_limit);
 
-    WarpTotals tot;
-    tot.E = 0.0;
-    tot.pairs = tot.evals = tot.clamped = 0;
-    tot.inst = -1;
 
     for (unsigned int iter = 0;; ++iter) {
         if (iter >= sh.max_iters) {
@@ -603,10 +588,6 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
         if (item >= n_items) break;
         int k = 0;
         while (k + 1 < pl.ninst && item >= s_prefix[k + 1]) ++k;
-        if (k != tot.inst) {
-            flush(tot, pl, !POT);
-            tot.inst = k;
-        }
         const PairParams &pp = pl.inst[k];
         const unsigned int local = item - s_prefix[k];
         const int C = s_C[k];
@@ -639,13 +620,7 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
         const float cull[3] = {pp.cull_h2[0], pp.cull_h2[1], pp.cull_h2[2]};
         (void)h2f;
         Cut cut;
-        cut.rc2d = pp.rc2;
-        cut.h2d[0] = pp.h2[0];
-        cut.h2d[1] = pp.h2[1];
-        cut.h2d[2] = pp.h2[2];
-        cut.g2d[0] = pp.g2x[0];
-        cut.g2d[1] = pp.g2x[1];
-        cut.g2d[2] = pp.g2x[2];
+        cut.pp = &pp;
         cut.lo = static_cast<float>(pp.rc2) * (1.0f - 1e-5f);
         cut.hi = static_cast<float>(pp.rc2) * (1.0f + 1e-5f);
         const float rc2_box = static_cast<float>(pp.rc2) * 1.0002f + 1e-6f;
@@ -675,6 +650,7 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
         }
         double A64 = 0.0, U64 = 0.0;
         unsigned int cnt = 0, nclamp = 0;
+        unsigned int item_evals = 0;  // (j point, image) steps of this item (times ni_act at the end)
         for (int J = J0; J < J1; ++J) {
             const int jb = J * kTile;
             const int jn = min(kTile, n_act - jb);
@@ -772,7 +748,7 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
                 for (int jj = 0; jj < jn; ++jj) {
                     unsigned m = __shfl_sync(0xffffffffu, jm, jj);
                     if (m == 0u) continue;
-                    tot.evals += static_cast<unsigned long long>(__popc(m)) * static_cast<unsigned long long>(ni_act);
+                    item_evals += static_cast<unsigned>(__popc(m));
                     const P pj = sp[jj];
                     const R nj = sn[jj];
                     // weights: off-diagonal tiles count every pair for i and for j; in the
@@ -838,26 +814,23 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
                 }
             }
         }
-        if (act) {
-            if (POT) {
-                if (A64 != 0.0) atomicAdd(pp.A + ig, A64);
-                if (U64 != 0.0) atomicAdd(pp.U + ig, static_cast<double>(ni) * U64);
-            }
-            tot.pairs += cnt;
-            tot.clamped += nclamp;
+        if (act && POT) {
+            if (A64 != 0.0) atomicAdd(pp.A + ig, A64);
+            if (U64 != 0.0) atomicAdd(pp.U + ig, static_cast<double>(ni) * U64);
         }
+        count_item(pp.stats, act ? cnt : 0u, act ? nclamp : 0u, item_evals * static_cast<unsigned>(ni_act));
         if (!POT) {
-            // the item's energy partial, summed over lanes in a fixed order
+            // the item's energy partial, summed over lanes in a fixed order (items
+            // beyond the partials' capacity are added atomically)
             const double e = warp_sum(act ? static_cast<double>(ni) * A64 : 0.0);
             if (lane == 0) {
                 if (sh.item_E && item < sh.item_cap)
                     sh.item_E[item] = e;
-                else
-                    tot.E += e;
+                else if (e != 0.0)
+                    atomicAdd(&pp.stats->E_pair, e);
             }
         }
     }
-    flush(tot, pl, !POT);
 }
 
 // Fixed-order sum of an instance's energy-mode item partials (block k: instance k).
