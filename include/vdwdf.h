@@ -30,6 +30,15 @@
  *    returning; the others return without waiting.
  *  - Scratch device memory is taken with cudaMallocAsync on the call's stream
  *    and freed on it before return; the library owns it.
+ *  - Fault injection for tests (host side only; no device fault is caused):
+ *    with the environment variable VDWDF_FAIL_ALLOC=1 every scratch
+ *    allocation fails (VDWDF_EALLOC); with VDWDF_MAX_ITERS=k the persistent
+ *    pair kernels stop after k work items per CTA, as their iteration guard
+ *    does, and the call returns VDWDF_ETIMEOUT.  The next call without them
+ *    works as before.
+ *  - vdwdf_energy and vdwdf_potential return VDWDF_EINVAL when the energy
+ *    comes out non-finite (an Inf density value, or a NaN next to an active
+ *    point).
  *  - Cells: the rows of vdwdf_grid.cell are the lattice vectors M_0, M_1,
  *    M_2 (section 2: equidistant grid, axes need not be orthogonal); grid
  *    point (i_0, i_1, i_2) sits at sum_a (i_a / n_a) M_a.  A singular cell is

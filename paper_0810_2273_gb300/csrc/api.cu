@@ -37,6 +37,31 @@ namespace vdwdf {
 namespace {
 
 std::atomic<long long> g_launches{0};
+
+// Fault injection for tests, on the host only (no device fault is ever caused):
+//   VDWDF_FAIL_ALLOC=1  every scratch allocation of a call fails (VDWDF_EALLOC);
+//   VDWDF_MAX_ITERS=k   the persistent pair kernels stop after k work items per
+//                       CTA, as their iteration guard would, so the call returns
+//                       VDWDF_ETIMEOUT.
+bool fail_alloc_requested() {
+    const char *e = std::getenv("VDWDF_FAIL_ALLOC");
+    return e && e[0] == '1';
+}
+unsigned int max_iters_override(unsigned int v) {
+    const char *e = std::getenv("VDWDF_MAX_ITERS");
+    if (!e || !e[0]) return v;
+    const long long k = std::atoll(e);
+    return (k > 0 && static_cast<unsigned long long>(k) < v) ? static_cast<unsigned int>(k) : v;
+}
+// cudaMallocAsync / cudaMalloc of a call's scratch, with the fault-injection hook
+cudaError_t scratch_malloc_async(void **p, size_t bytes, cudaStream_t st) {
+    if (fail_alloc_requested()) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, bytes, st);
+}
+cudaError_t scratch_malloc(void **p, size_t bytes) {
+    if (fail_alloc_requested()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxImages = 64;
 
@@ -414,7 +439,7 @@ void fill_shared(const vdwdf_table *t, const double *d64, const float *d32, cons
     sh.ksn = ln.ksn;
     sh.jtiles_per_item = ln.jt;
     sh.item_limit = 0xFFFFFFFFu;
-    sh.max_iters = max_iters;
+    sh.max_iters = max_iters_override(max_iters);
     sh.queue = queue;
     sh.item_E = nullptr;
     sh.item_cap = 0;
@@ -511,7 +536,7 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
     const bool fp64 = precision == VDWDF_FP64;
     const size_t bytes = layout(G, nb, pot, fp64, nullptr, nullptr);
     unsigned char *base = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&base), bytes, st) != cudaSuccess) return VDWDF_EALLOC;
+    if (scratch_malloc_async(reinterpret_cast<void **>(&base), bytes, st) != cudaSuccess) return VDWDF_EALLOC;
     Work w;
     layout(G, nb, pot, fp64, &w, base);
     Timer tm;
@@ -539,7 +564,7 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
             fill_shared(table, d64, d32, ln, w.queue, static_cast<unsigned int>(items + 2), pl.sh);
             if (!pot) {
                 // one energy partial per work item, summed afterwards in a fixed order
-                if (cudaMallocAsync(reinterpret_cast<void **>(&item_buf), sizeof(double) * items, st) != cudaSuccess)
+                if (scratch_malloc_async(reinterpret_cast<void **>(&item_buf), sizeof(double) * items, st) != cudaSuccess)
                     return VDWDF_EALLOC;
                 pl.sh.item_E = item_buf;
                 pl.sh.item_cap = static_cast<unsigned int>(items);
@@ -567,6 +592,9 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
     if (item_buf) cudaFreeAsync(item_buf, st);
     cudaFreeAsync(base, st);
     if (rc == VDWDF_OK && hs.guard_trips) rc = VDWDF_ETIMEOUT;
+    // non-finite input values (an Inf, or a NaN next to an active point) show up as
+    // a non-finite sum; report them instead of returning NaN
+    if (rc == VDWDF_OK && !std::isfinite(hs.E_pair)) rc = VDWDF_EINVAL;
     if (rc == VDWDF_OK && out) {
         std::memset(out, 0, sizeof(*out));
         fill_result(hs, G, table, out);
@@ -872,7 +900,7 @@ int vdwdf_semilocal(const vdwdf_grid *grid, const double *n_dev, const double *g
     const long long launches0 = g_launches.load();
     const size_t nd = static_cast<size_t>(semilocal_scratch_doubles());
     double *scratch = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&scratch), nd * sizeof(double), st) != cudaSuccess)
+    if (scratch_malloc_async(reinterpret_cast<void **>(&scratch), nd * sizeof(double), st) != cudaSuccess)
         return VDWDF_EALLOC;
     Timer tm;
     double sums[6] = {0, 0, 0, 0, 0, 0};
@@ -915,7 +943,7 @@ int vdwdf_phi0_eval(const vdwdf_table *table, const double *voxel, int64_t nq, c
     std::vector<double> xw;
     phi0_rule(xw);
     double *xw_dev = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&xw_dev), sizeof(double) * (xw.size() + 8 * nq), st) !=
+    if (scratch_malloc_async(reinterpret_cast<void **>(&xw_dev), sizeof(double) * (xw.size() + 8 * nq), st) !=
         cudaSuccess)
         return VDWDF_EALLOC;
     Launch ln;
@@ -961,7 +989,7 @@ int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *
                  o_sums = c.take<double>(2), o_qg = c.take<double>(nq), o_tab = c.take<double>(nq),
                  o_xw = c.take<double>(xw.size()), o_op = c.take<double>(8 * static_cast<size_t>(nq));
     unsigned char *base = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&base), c.off, st) != cudaSuccess) return VDWDF_EALLOC;
+    if (scratch_malloc_async(reinterpret_cast<void **>(&base), c.off, st) != cudaSuccess) return VDWDF_EALLOC;
     double *q0 = reinterpret_cast<double *>(base + o_q0);
     unsigned long long *mm = reinterpret_cast<unsigned long long *>(base + o_mm);
     double *part = reinterpret_cast<double *>(base + o_part), *sums = reinterpret_cast<double *>(base + o_sums);
@@ -1109,14 +1137,14 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
             }
             const size_t bytes = layout(geo[k], nb, false, precision == VDWDF_FP64, nullptr, nullptr);
             unsigned char *b = nullptr;
-            if (cudaMalloc(&b, bytes) != cudaSuccess) {
+            if (scratch_malloc(reinterpret_cast<void **>(&b), bytes) != cudaSuccess) {
                 delete bp;
                 return VDWDF_EALLOC;
             }
             bp->bufs.push_back(b);
             layout(geo[k], nb, false, precision == VDWDF_FP64, &bp->work[k], b);
         }
-        if (cudaMalloc(&bp->queues, sizeof(unsigned int) * ngroups) != cudaSuccess) {
+        if (scratch_malloc(reinterpret_cast<void **>(&bp->queues), sizeof(unsigned int) * ngroups) != cudaSuccess) {
             delete bp;
             return VDWDF_EALLOC;
         }
@@ -1132,7 +1160,7 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
             long long items = 0;
             for (int k = k0; k < k1; ++k) items += pair_items(geo[k].N, ln.jt);
             double *b = nullptr;
-            if (cudaMalloc(&b, sizeof(double) * std::max<long long>(items, 1)) != cudaSuccess) {
+            if (scratch_malloc(reinterpret_cast<void **>(&b), sizeof(double) * std::max<long long>(items, 1)) != cudaSuccess) {
                 delete bp;
                 return VDWDF_EALLOC;
             }
@@ -1218,7 +1246,7 @@ int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, do
     const bool fp64 = precision == VDWDF_FP64;
     const size_t bytes = layout(G, nb, false, fp64, nullptr, nullptr);
     unsigned char *base = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&base), bytes, st) != cudaSuccess) return VDWDF_EALLOC;
+    if (scratch_malloc_async(reinterpret_cast<void **>(&base), bytes, st) != cudaSuccess) return VDWDF_EALLOC;
     Work w;
     layout(G, nb, false, fp64, &w, base);
     rc = prepare(G, n_dev, nullptr, n_cut, false, w, st);
