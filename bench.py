@@ -105,6 +105,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def combine_ranks(ms, e2e, pairs, device):
+    """Replicas, one per rank with no data exchange (the path does not shard): the
+    slowest rank's step and end-to-end times, and the pair interactions summed over
+    the ranks (weak scaling).  At one rank, or without a process group, the inputs."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(e2e), float(pairs)
+    t = torch.tensor([ms, e2e, float(pairs)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    tot = t.clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(mx[1]), float(tot[2])
+
+
 def build_table(V):
     """The standard 400 x 200 table (0 <= D <= 30), cached under .cache/."""
     path = os.path.join(ROOT, ".cache", "vdwdf_table_400x200_D30_q1.npz")
@@ -198,17 +214,7 @@ def run_gpu(args):
         semi_ms.append(semi["ms"])
     semi_t = float(np.median(semi_ms[1:]))
 
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, e2e, float(pairs)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        tot = t.clone()
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        ms, e2e = float(mx[0]), float(mx[1])
-        total_pairs = float(tot[2])
-    else:
-        total_pairs = float(pairs)
+    ms, e2e, total_pairs = combine_ranks(ms, e2e, pairs, dev)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
