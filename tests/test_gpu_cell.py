@@ -132,3 +132,22 @@ def test_hex_semilocal(V, dev, oracle_mod):
     for k in ("Ex_lda", "Ec_lda", "Ex_pbe", "Ec_pbe", "Ex_revpbe"):
         assert abs(got[k] - ref[k]) <= 1e-12 * abs(ref[k]), k
     assert got["n_points"] == ref["n_points"]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_many_images_skewed_potential(V, dev, gtable, oracle_mod, oracle_spline, prec, tol):
+    """A small, strongly skewed cell periodic along all axes with a cutoff of about
+    twice the cell: more than 32 candidate images per tile pair, so the image
+    lists are processed in chunks; energy, v and U against the oracle."""
+    rng = np.random.default_rng(12)
+    cell = np.array([[4.0, 0.0, 0.0], [2.6, 3.3, 0.0], [0.5, -0.7, 4.4]])
+    n = 10 ** rng.uniform(-2.5, -0.5, size=(6, 7, 8))
+    P = oracle_mod.Problem(n, None, (1, 1, 1), 5e-3, 8.5, oracle_spline, cell=cell)
+    e = P.energy()
+    vo = P.potential(e["A"], e["U"])
+    E, v, res, A, U = V.potential(_t(n, dev), cell, (1, 1, 1), 5e-3, 8.5, gtable, prec, want_AU=True)
+    assert res["pairs"] == e["pairs"]
+    assert abs(E - e["E"]) <= (tol if prec == "fp64" else 1e-6) * abs(e["E"])
+    assert np.max(np.abs(v.cpu().numpy() - vo)) <= tol * np.max(np.abs(vo))
+    flat = n.ravel() >= 5e-3
+    assert np.max(np.abs(U.cpu().numpy().ravel()[flat] - e["U"])) <= tol * np.max(np.abs(e["U"]))
