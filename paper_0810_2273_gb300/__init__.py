@@ -114,6 +114,12 @@ def grid(lengths, dims, periodic=(False, False, False)):
     return g
 
 
+def _cell_volume(lengths):
+    """Volume of the orthorhombic cell lengths, or of the general cell (3x3 rows)."""
+    cell = np.asarray(lengths, dtype=np.float64)
+    return abs(float(np.linalg.det(cell))) if cell.shape == (3, 3) else float(np.prod(cell))
+
+
 def _torch():
     import torch
     return torch
@@ -359,7 +365,7 @@ def _make_function():
         def forward(ctx, n, spec):
             E, v, _ = potential(n, spec["lengths"], spec["periodic"], spec["n_cut"], spec["r_cut"],
                                 spec["table"], spec.get("precision", "fp32"), spec.get("tuning"))
-            dV = float(np.prod(spec["lengths"])) / float(n.numel())
+            dV = _cell_volume(spec["lengths"]) / float(n.numel())
             ctx.save_for_backward(v)
             ctx.dV = dV
             return torch.tensor(E, dtype=torch.float64, device=n.device)
