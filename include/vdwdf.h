@@ -300,6 +300,21 @@ int vdwdf_phi0_eval(const vdwdf_table *table, const double *voxel, int64_t nq, c
 int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
                      const vdwdf_table *table, int nphi0, vdwdf_diag_result *out, void *cuda_stream);
 
+/* The change of v = (1/dV) dE/dn when the table self term is replaced by the
+ * voxel diagonal of vdwdf_diag_voxel, written to dv_dev [N] FP64 (device):
+ * with the active mask frozen,
+ *   dv_m = dV [chi_m (A_m + U_m dq0/dn_m) + sum_a (G_a^T w_a)_m],
+ *   A_m = n_m (phi0(q0_m) - phi(0, 0)),  U_m = 1/2 n_m^2 phi0'(q0_m),
+ *   w_a = chi U dq0/dgrad_a n,
+ * the same form as the pair sum's adjoint (phi0' from the derivative of the
+ * interpolant in ln q).  v (vdwdf_potential) + dv is the potential of
+ * E - E_diag_table + E_diag_voxel.  Library gradient stencil (the adjoint needs
+ * it).  out as in vdwdf_diag_voxel.  Synchronises the stream.
+ * Errors: as vdwdf_diag_voxel; VDWDF_EINVAL for a NULL dv_dev. */
+int vdwdf_diag_voxel_potential(const vdwdf_grid *grid, const double *n_dev, double n_cut,
+                               const vdwdf_table *table, int nphi0, double *dv_dev, vdwdf_diag_result *out,
+                               void *cuda_stream);
+
 /* vdwdf_energy that allocates nothing.  The paper has no counterpart: JuNoLo
  * allocates its arrays once per run.  This entry point is for callers that
  * cannot allocate device memory while they run, for example:

@@ -18,7 +18,7 @@ from ._native import (VDWDF_FP32, VDWDF_FP64, VdwdfError, vdwdf_diag_result, vdw
                       vdwdf_semilocal_result, vdwdf_tuning)
 
 __all__ = ["Table", "grid", "energy", "energy_noalloc", "potential", "energy_batched", "q0", "kernel_eval",
-           "semilocal", "total_energy_nl", "phi0_eval", "diag_voxel",
+           "semilocal", "total_energy_nl", "phi0_eval", "diag_voxel", "diag_voxel_potential",
            "autotune", "launch_count", "NonlocalEnergy", "nonlocal_energy", "VdwdfError",
            "VDWDF_FP32", "VDWDF_FP64"]
 
@@ -236,6 +236,24 @@ def diag_voxel(n, lengths, periodic, n_cut, table, nphi0=0, grad=None):
                                   float(n_cut), table.handle, int(nphi0), ctypes.byref(res), _stream(n))
     _native.check(st, "vdwdf_diag_voxel")
     return res.as_dict()
+
+
+def diag_voxel_potential(n, lengths, periodic, n_cut, table, nphi0=0):
+    """(result dict, dv): the voxel diagonal as diag_voxel and the change dv of the
+    potential when it replaces the table self term (v + dv belongs to
+    E - E_diag_table + E_diag_voxel)."""
+    _check_tensor(n, "n")
+    torch = _torch()
+    lib = _native.load()
+    g = grid(lengths, n.shape, periodic)
+    res = vdwdf_diag_result()
+    dv = torch.empty_like(n)
+    with torch.cuda.device(n.device):
+        st = lib.vdwdf_diag_voxel_potential(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()), float(n_cut),
+                                            table.handle, int(nphi0), ctypes.c_void_p(dv.data_ptr()),
+                                            ctypes.byref(res), _stream(n))
+    _native.check(st, "vdwdf_diag_voxel_potential")
+    return res.as_dict(), dv
 
 
 def total_energy_nl(E_tot_dft, semi, E_c_nl, exchange="pbe"):

@@ -77,6 +77,8 @@ PROTOTYPES = {
     "vdwdf_phi0_eval": (_c_i, [_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p]),
     "vdwdf_diag_voxel": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_d, _c_p, _c_i,
                                 ctypes.POINTER(vdwdf_diag_result), _c_p]),
+    "vdwdf_diag_voxel_potential": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_d, _c_p, _c_i, _c_p,
+                                          ctypes.POINTER(vdwdf_diag_result), _c_p]),
     "vdwdf_energy_noalloc": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_d, _c_d, _c_p, _c_i,
                                     ctypes.POINTER(vdwdf_result), _c_p]),
     "vdwdf_autotune": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_d, _c_d, _c_p, _c_i,

@@ -959,8 +959,15 @@ int vdwdf_phi0_eval(const vdwdf_table *table, const double *voxel, int64_t nq, c
     return rc;
 }
 
-int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
-                     const vdwdf_table *table, int nphi0, vdwdf_diag_result *out, void *cuda_stream) {
+}  // extern "C"
+
+namespace vdwdf {
+namespace {
+
+// The voxel diagonal; with dv_dev, also the change of v from replacing the table
+// self term by it (library stencil only).
+int diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
+               const vdwdf_table *table, int nphi0, double *dv_dev, vdwdf_diag_result *out, void *cuda_stream) {
     Geom G;
     int rc = check_grid(grid, G);
     if (rc) return rc;
@@ -984,10 +991,14 @@ int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *
     std::vector<double> xw;
     phi0_rule(xw);
     // scratch: q0 [N], range (3), block sums (2 x 608), sums (2), q grid and table [nq], rule nodes
+    const bool pot = dv_dev != nullptr;
     Carve c;
     const size_t o_q0 = c.take<double>(G.N), o_mm = c.take<unsigned long long>(3), o_part = c.take<double>(2 * 608),
                  o_sums = c.take<double>(2), o_qg = c.take<double>(nq), o_tab = c.take<double>(nq),
                  o_xw = c.take<double>(xw.size()), o_op = c.take<double>(8 * static_cast<size_t>(nq));
+    const size_t o_qn = pot ? c.take<double>(G.N) : 0, o_qgr = pot ? c.take<double>(3 * G.N) : 0,
+                 o_slot = pot ? c.take<int>(G.N) : 0, o_A = pot ? c.take<double>(G.N) : 0,
+                 o_U = pot ? c.take<double>(G.N) : 0;
     unsigned char *base = nullptr;
     if (scratch_malloc_async(reinterpret_cast<void **>(&base), c.off, st) != cudaSuccess) return VDWDF_EALLOC;
     double *q0 = reinterpret_cast<double *>(base + o_q0);
@@ -995,6 +1006,11 @@ int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *
     double *part = reinterpret_cast<double *>(base + o_part), *sums = reinterpret_cast<double *>(base + o_sums);
     double *qg = reinterpret_cast<double *>(base + o_qg), *tab = reinterpret_cast<double *>(base + o_tab);
     double *xw_dev = reinterpret_cast<double *>(base + o_xw), *opart = reinterpret_cast<double *>(base + o_op);
+    double *qn = pot ? reinterpret_cast<double *>(base + o_qn) : nullptr;
+    double *qgr = pot ? reinterpret_cast<double *>(base + o_qgr) : nullptr;
+    int *slot = pot ? reinterpret_cast<int *>(base + o_slot) : nullptr;
+    double *Ad = pot ? reinterpret_cast<double *>(base + o_A) : nullptr;
+    double *Ud = pot ? reinterpret_cast<double *>(base + o_U) : nullptr;
     Timer tm;
     unsigned long long hmm[3] = {0, 0, 0};
     double hs[2] = {0.0, 0.0};
@@ -1002,8 +1018,9 @@ int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *
     double lnq0 = 0.0, dlnq = 1.0;
     auto body = [&]() -> int {
         tm.mark(0, st);
-        int r = launch_grad_q0(G.dims, G.am, n_dev, grad_dev, q0, nullptr, nullptr, st);
+        int r = launch_grad_q0(G.dims, G.am, n_dev, grad_dev, q0, qn, qgr, st);
         if (r) return r;
+        if (pot) VDWDF_CUDA_TRY(cudaMemsetAsync(dv_dev, 0, sizeof(double) * G.N, st));
         VDWDF_CUDA_TRY(cudaMemsetAsync(mm, 0xFF, sizeof(unsigned long long), st));
         VDWDF_CUDA_TRY(cudaMemsetAsync(mm + 1, 0, 2 * sizeof(unsigned long long), st));
         r = launch_diag_range(G.N, n_dev, q0, n_cut, mm, st);
@@ -1030,6 +1047,12 @@ int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *
         if (r) return r;
         r = launch_diag_sum(G.N, n_dev, q0, n_cut, tab, nq, lnq0, dlnq, part, sums, st);
         if (r) return r;
+        if (pot) {
+            r = launch_diag_AU(G.N, n_dev, q0, n_cut, tab, nq, lnq0, dlnq, table->nodes[0], slot, Ad, Ud, st);
+            if (r) return r;
+            r = launch_assemble(G.dims, G.am, G.dV, slot, Ad, Ud, qn, qgr, dv_dev, nullptr, nullptr, st);
+            if (r) return r;
+        }
         tm.mark(1, st);
         VDWDF_CUDA_TRY(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st));
         VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1051,6 +1074,23 @@ int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *
     }
     out->launches = static_cast<int32_t>(g_launches.load() - launches0);
     return VDWDF_OK;
+}
+
+}  // namespace
+}  // namespace vdwdf
+
+extern "C" {
+
+int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
+                     const vdwdf_table *table, int nphi0, vdwdf_diag_result *out, void *cuda_stream) {
+    return vdwdf::diag_voxel(grid, n_dev, grad_dev, n_cut, table, nphi0, nullptr, out, cuda_stream);
+}
+
+int vdwdf_diag_voxel_potential(const vdwdf_grid *grid, const double *n_dev, double n_cut,
+                               const vdwdf_table *table, int nphi0, double *dv_dev, vdwdf_diag_result *out,
+                               void *cuda_stream) {
+    if (!dv_dev) return VDWDF_EINVAL;
+    return vdwdf::diag_voxel(grid, n_dev, nullptr, n_cut, table, nphi0, dv_dev, out, cuda_stream);
 }
 
 int vdwdf_energy(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,

@@ -167,6 +167,43 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_sum(long long N, const do
     }
 }
 
+// Per grid point, for the potential of the voxel diagonal: with the active mask
+// frozen, d/dn of 1/2 dV^2 sum_i n_i^2 (phi0(q_i) - phi(0,0)) has the form of the
+// pair sum's adjoint with A_m = n_m (phi0(q_m) - phi00) and U_m = 1/2 n_m^2
+// phi0'(q_m), so k_assemble turns these into the change of v.  phi0 and its
+// derivative come from the 4-point Lagrange interpolant in ln q; slot[m] = m on
+// active points, -1 elsewhere.
+__global__ void k_diag_AU(long long N, const double *__restrict__ n, const double *__restrict__ q0,
+                          double n_cut, const double *__restrict__ tab, int nq, double lnq0, double dlnq,
+                          double phi00, int *__restrict__ slot, double *__restrict__ A, double *__restrict__ U) {
+    for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < N;
+         m += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double nn = n[m];
+        if (!(nn >= n_cut)) {
+            slot[m] = -1;
+            A[m] = 0.0;
+            U[m] = 0.0;
+            continue;
+        }
+        const double q = q0[m];
+        const double x = (log(q) - lnq0) / dlnq;
+        int k = static_cast<int>(floor(x));
+        k = max(1, min(nq - 3, k));
+        const double u = x - k;
+        const double lm = -u * (u - 1.0) * (u - 2.0) / 6.0, l0 = (u + 1.0) * (u - 1.0) * (u - 2.0) / 2.0,
+                     l1 = -(u + 1.0) * u * (u - 2.0) / 2.0, l2 = (u + 1.0) * u * (u - 1.0) / 6.0;
+        // d/du of the four Lagrange weights
+        const double dm = -(3.0 * u * u - 6.0 * u + 2.0) / 6.0, d0 = (3.0 * u * u - 4.0 * u - 1.0) / 2.0,
+                     d1 = -(3.0 * u * u - 2.0 * u - 2.0) / 2.0, d2 = (3.0 * u * u - 1.0) / 6.0;
+        const double p0 = lm * tab[k - 1] + l0 * tab[k] + l1 * tab[k + 1] + l2 * tab[k + 2];
+        const double dpdu = dm * tab[k - 1] + d0 * tab[k] + d1 * tab[k + 1] + d2 * tab[k + 2];
+        const double dpdq = dpdu / (dlnq * q);  // du/dq = 1 / (q dlnq)
+        slot[m] = static_cast<int>(m);
+        A[m] = nn * (p0 - phi00);
+        U[m] = 0.5 * nn * nn * dpdq;
+    }
+}
+
 __global__ void k_diag_final(const double *__restrict__ part, int nb, double *__restrict__ sums) {
     if (threadIdx.x < 2) {
         double v = 0.0;
@@ -191,6 +228,16 @@ int launch_diag_sum(long long N, const double *n, const double *q0, double n_cut
     k_diag_sum<<<kDiagBlocks, kDiagThreads, 0, st>>>(N, n, q0, n_cut, tab, nq, lnq0, dlnq, part);
     k_diag_final<<<1, 32, 0, st>>>(part, kDiagBlocks, sums);
     count_launches(2);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
+}
+
+int launch_diag_AU(long long N, const double *n, const double *q0, double n_cut, const double *tab, int nq,
+                   double lnq0, double dlnq, double phi00, int *slot, double *A, double *U, cudaStream_t st) {
+    long long nb = (N + 255) / 256;
+    if (nb > 1 << 20) nb = 1 << 20;
+    k_diag_AU<<<static_cast<int>(nb), 256, 0, st>>>(N, n, q0, n_cut, tab, nq, lnq0, dlnq, phi00, slot, A, U);
+    count_launches(1);
     VDWDF_CUDA_TRY(cudaGetLastError());
     return VDWDF_OK;
 }

@@ -156,6 +156,8 @@ int launch_diag_range(long long N, const double *n, const double *q0, double n_c
                       unsigned long long *mm, cudaStream_t st);
 int launch_diag_sum(long long N, const double *n, const double *q0, double n_cut, const double *tab,
                     int nq, double lnq0, double dlnq, double *part, double *sums, cudaStream_t st);
+int launch_diag_AU(long long N, const double *n, const double *q0, double n_cut, const double *tab, int nq,
+                   double lnq0, double dlnq, double phi00, int *slot, double *A, double *U, cudaStream_t st);
 int launch_kernel_eval(int precision, const PairShared &sh, int64_t npts, const double *r,
                        const double *qi, const double *qj, double *phi, double *rdphi,
                        cudaStream_t st);

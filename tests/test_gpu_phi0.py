@@ -75,3 +75,57 @@ def test_diag_voxel_matches_oracle(V, dev, gtable, oracle_mod, oracle_spline, na
     # more table points move the result by no more than the interpolation error
     fine = V.diag_voxel(n, geom, w["periodic"], n_cut, gtable, nphi0=400)
     assert abs(fine["E_diag_voxel"] - got["E_diag_voxel"]) <= 1e-6 * abs(got["E_diag_voxel"])
+
+
+def test_diag_voxel_potential_is_derivative(V, dev, gtable, oracle_mod, oracle_spline):
+    """dv = (1/dV) d(E_diag_voxel - E_diag_table)/dn at points with n >= 2 n_cut (mask
+    unchanged) whose stencil neighbourhoods are not at the q0 extremes (table range
+    unchanged): against central differences of the GPU's own FP64 sums, and at two
+    points against central differences of the oracle's diagonal."""
+    import torch
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.xe_monolayer_hex((12, 12, 30))
+    cell, n_cut = w["cell"], 0.01
+    n = w["density"].copy()
+    res, dv = V.diag_voxel_potential(_t(n, dev), cell, w["periodic"], n_cut, gtable)
+    dv = dv.cpu().numpy()
+    dV = abs(np.linalg.det(cell)) / n.size
+    q0 = V.q0(_t(n, dev), cell)[0].cpu().numpy()
+    act = n >= n_cut
+    qa = q0[act]
+    lo, hi = np.sort(qa)[3], np.sort(qa)[-4]
+    rng = np.random.default_rng(3)
+    cand = [m for m in rng.permutation(n.size) if n.flat[m] >= 2 * n_cut]
+    picked = []
+    for m in cand:
+        i = np.unravel_index(m, n.shape)
+        nb = [tuple((np.array(i) + d) % np.array(n.shape)) for d in
+              [np.eye(3, dtype=int)[a] * s for a in range(3) for s in (-2, -1, 0, 1, 2)]]
+        if all(lo < q0[j] < hi for j in nb):
+            picked.append(m)
+        if len(picked) == 4:
+            break
+    vmax = np.max(np.abs(dv))
+
+    def e_diag(nn):
+        r = V.diag_voxel(_t(nn, dev), cell, w["periodic"], n_cut, gtable)
+        return r["E_diag_voxel"] - r["E_diag_table"]
+
+    for m in picked:
+        h = 1e-4 * n.flat[m]
+        npl, nmi = n.copy(), n.copy()
+        npl.flat[m] += h
+        nmi.flat[m] -= h
+        fd = (e_diag(npl) - e_diag(nmi)) / (2 * h * dV)
+        assert abs(fd - dv.flat[m]) <= 1e-6 * vmax + 1e-8 * abs(dv.flat[m]), (m, fd, dv.flat[m])
+    for m in picked[:2]:
+        h = 1e-4 * n.flat[m]
+        vals = []
+        for s in (1, -1):
+            nn = n.copy()
+            nn.flat[m] += s * h
+            P = oracle_mod.Problem(nn, None, w["periodic"], n_cut, w["r_cut"], oracle_spline, cell=cell)
+            d = P.diag_voxel(6, 8)
+            vals.append(d["E_diag_voxel"] - d["E_diag_table"])
+        fd = (vals[0] - vals[1]) / (2 * h * dV)
+        assert abs(fd - dv.flat[m]) <= 1e-3 * abs(dv.flat[m]) + 1e-5 * vmax, (m, fd, dv.flat[m])
