@@ -203,11 +203,13 @@ __device__ __forceinline__ void interp(const Table<R> &tb, int k, int l, const R
 }
 
 // The delta-dependent part of a pair, shared by all its periodic images: the
-// delta cell and weights, and the signs of d(delta)/dd1, d(delta)/dd2.
-// With ds = (q_i - q_j)/(q_i + q_j): dds/dd1 = (1 - ds)/(2D), dds/dd2 = -(1 + ds)/(2D).
+// delta cell and weights, the scale from r to the table's D coordinate, and the
+// factors that turn the delta-derivative into r dphi/dd1 and r dphi/dd2.
+// With ds = (q_i - q_j)/(q_i + q_j): dds/dd1 = (1 - ds)/(2D), dds/dd2 = -(1 + ds)/(2D),
+// so b1 = cd sign(ds) (1 - ds)/(q_i + q_j) and b2 = -cd sign(ds) (1 + ds)/(q_i + q_j).
 template <typename R>
 struct Delta {
-    R sq, isq, sgn1, sgn2;
+    R sqcD, b1, b2;  // (q_i + q_j) cD; the delta-derivative factors
     R wd[4], dwd[4];
     int l;
     bool cl;  // delta beyond the last node (weights continued linearly)
@@ -215,13 +217,13 @@ struct Delta {
 
 template <bool POT, typename R>
 __device__ __forceinline__ void delta_part(R qi, R qj, const Consts<R> &K, Delta<R> &d) {
-    d.sq = qi + qj;
+    const R sq = qi + qj;
     const R dq = qi - qj;
-    d.isq = recip(d.sq);
+    const R isq = recip(sq);
     // beyond the last node the spline continues linearly with its end slope (it has
     // zero curvature there): the weights become w(u) + e w'(u), e the distance past
     // the node in cells.  No index leaves the table.
-    const R dl = fabs(dq) * d.isq;
+    const R dl = fabs(dq) * isq;
     const R td0 = dl * K.cd;
     d.cl = td0 > K.tdmax;
     const R td = fmin(fmax(td0, R(0)), K.tdclamp);
@@ -239,8 +241,62 @@ __device__ __forceinline__ void delta_part(R qi, R qj, const Consts<R> &K, Delta
 #pragma unroll
         for (int n = 0; n < 4; ++n) d.wd[n] += e * d.dwd[n];
     }
-    d.sgn1 = dq > R(0) ? (R(1) - dl) : -(R(1) + dl);  // sign(ds) (1 - ds)
-    d.sgn2 = dq > R(0) ? (R(1) + dl) : -(R(1) - dl);  // sign(ds) (1 + ds)
+    const R bq = isq * K.cd;
+    d.sqcD = sq * K.cD;
+    d.b1 = bq * (dq > R(0) ? (R(1) - dl) : -(R(1) + dl));   // sign(ds) (1 - ds)
+    d.b2 = -bq * (dq > R(0) ? (R(1) + dl) : -(R(1) - dl));  // sign(ds) (1 + ds)
+}
+
+// The delta parts of two pairs (i, j0) and (i, j1) in the two halves of packed
+// FP32 values: the arithmetic of delta_part, two lanes per instruction.
+struct Delta2 {
+    float2 sqcD, b1, b2;
+    float2 wd[4], dwd[4];
+    int l0, l1;
+};
+
+template <bool POT>
+__device__ __forceinline__ void delta_part2(float qi, float2 qj, const Consts<float> &K, Delta2 &d,
+                                            bool &cl0, bool &cl1) {
+    const float2 sq = add2(f2(qi), qj);
+    const float2 dq = fma2(qj, f2(-1.0f), f2(qi));  // q_i - q_j, one rounding
+    const float2 isq = make_float2(recip(sq.x), recip(sq.y));
+    const float2 dl = mul2(make_float2(fabsf(dq.x), fabsf(dq.y)), isq);
+    const float2 td0 = mul2(dl, f2(K.cd));
+    cl0 = td0.x > K.tdmax;
+    cl1 = td0.y > K.tdmax;
+    const float2 td = make_float2(fminf(fmaxf(td0.x, 0.0f), K.tdclamp), fminf(fmaxf(td0.y, 0.0f), K.tdclamp));
+    const float2 u = floor_split2(td, d.l0, d.l1);
+    bw2(u, d.wd);
+    if (POT || cl0 || cl1) bdw2(u, d.dwd);
+    if (cl0 || cl1) {
+        const float2 e = fma2(td, f2(-1.0f), td0);  // 0 in a half that is not past the node
+#pragma unroll
+        for (int n = 0; n < 4; ++n) d.wd[n] = fma2(e, d.dwd[n], d.wd[n]);
+    }
+    const float2 bq = mul2(isq, f2(K.cd));
+    const float2 one = f2(1.0f);
+    const float2 om = fma2(dl, f2(-1.0f), one), op = add2(dl, one);  // 1 - |ds|, 1 + |ds|
+    d.sqcD = mul2(sq, f2(K.cD));
+    d.b1 = mul2(bq, make_float2(dq.x > 0.0f ? om.x : -op.x, dq.y > 0.0f ? om.y : -op.y));
+    d.b2 = mul2(bq, make_float2(dq.x > 0.0f ? -op.x : om.x, dq.y > 0.0f ? -op.y : om.y));
+}
+
+// Half s of a packed delta part as a scalar one (register renaming only).
+template <int S>
+__device__ __forceinline__ Delta<float> delta_half(const Delta2 &d) {
+    Delta<float> r;
+    r.sqcD = S ? d.sqcD.y : d.sqcD.x;
+    r.b1 = S ? d.b1.y : d.b1.x;
+    r.b2 = S ? d.b2.y : d.b2.x;
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        r.wd[n] = S ? d.wd[n].y : d.wd[n].x;
+        r.dwd[n] = S ? d.dwd[n].y : d.dwd[n].x;
+    }
+    r.l = S ? d.l1 : d.l0;
+    r.cl = false;
+    return r;
 }
 
 // The distance-dependent part: phi and (POT) r dphi/dd1, r dphi/dd2 at r^2.
@@ -249,7 +305,7 @@ __device__ __forceinline__ void dist_part(R r2, R qi, R qj, R inv_qi, R qi2, con
                                           const Consts<R> &K, const Table<R> &tb, R &phi, R &rd,
                                           R &rd2) {
     const R r = rlen(r2);
-    R tD = r * d.sq * K.cD;
+    R tD = r * d.sqcD;
     // the table is read only for 0 <= tD <= nD - 1 (false for NaN as well)
     if (tD >= R(0) && tD <= K.tDmax) {
         tD = fmin(tD, K.tDclamp);
@@ -265,9 +321,9 @@ __device__ __forceinline__ void dist_part(R r2, R qi, R qj, R inv_qi, R qi2, con
         R pt = 0, pu = 0;
         interp<POT, R>(tb, k, d.l, wD, dwD, d.wd, d.dwd, phi, pt, pu);
         if (POT) {
-            const R a = r * K.cD * pt, b = d.isq * K.cd * pu;
-            rd = a + b * d.sgn1;
-            rd2 = a - b * d.sgn2;
+            const R a = r * K.cD * pt;
+            rd = a + pu * d.b1;
+            rd2 = a + pu * d.b2;
         }
     } else {
         const R r4 = r2 * r2;
@@ -281,9 +337,9 @@ __device__ __forceinline__ void dist_part(R r2, R qi, R qj, R inv_qi, R qi2, con
         if (POT) {
             const R drho = d.dwd[1] * (c1 - c0) + d.dwd[2] * (c2 - c0) + d.dwd[3] * (c3 - c0);
             const R is2 = recip(s2);
-            const R b = p17 * d.isq * K.cd * drho;
-            rd = rho * (R(-2) * p17 * (inv_qi + qi * is2)) + b * d.sgn1;
-            rd2 = rho * (R(-2) * p17 * (recip(qj) + qj * is2)) - b * d.sgn2;
+            const R b = p17 * drho;
+            rd = rho * (R(-2) * p17 * (inv_qi + qi * is2)) + b * d.b1;
+            rd2 = rho * (R(-2) * p17 * (recip(qj) + qj * is2)) + b * d.b2;
         }
     }
 }
@@ -400,12 +456,12 @@ __device__ __forceinline__ void count_item(Stats *s, unsigned cnt, unsigned ncla
     }
 }
 
-// Two images of one (i, j) pair in the resident band, evaluated together: slot s
-// has cell coordinate tD.s (a slot that is not wanted carries a valid dummy).
-// wdb, dwdb: the pair's delta weights in both halves.  Returns phi and, with
-// POT, the cell-coordinate derivatives pt (along D) and pu (along delta).
+// Two evaluations in the resident band at once: half s at cell coordinate tD.s and
+// delta row l_s (a half that is not wanted reads no coefficient and returns 0).
+// wd, dwd: the delta weights of the two halves.  Returns phi and, with POT, the
+// cell-coordinate derivatives pt (along D) and pu (along delta).
 template <bool POT>
-__device__ __forceinline__ void band_pair2(const Table<float> &tb, float2 tD, int l, bool use0,
+__device__ __forceinline__ void band_pair2(const Table<float> &tb, float2 tD, int l0, int l1, bool use0,
                                            bool use1, const float2 wdb[4], const float2 dwdb[4],
                                            float2 &p, float2 &pt, float2 &pu) {
     int k0, k1;
@@ -413,8 +469,8 @@ __device__ __forceinline__ void band_pair2(const Table<float> &tb, float2 tD, in
     float2 wD[4], dwD[4];
     bw2(t, wD);
     if (POT) bdw2(t, dwD);
-    const uint32_t a0 = tb.s + 4u * static_cast<uint32_t>((k0 - tb.k0) * tb.SB + l);
-    const uint32_t a1 = tb.s + 4u * static_cast<uint32_t>((k1 - tb.k0) * tb.SB + l);
+    const uint32_t a0 = tb.s + 4u * static_cast<uint32_t>((k0 - tb.k0) * tb.SB + l0);
+    const uint32_t a1 = tb.s + 4u * static_cast<uint32_t>((k1 - tb.k0) * tb.SB + l1);
     const uint32_t rs = 4u * static_cast<uint32_t>(tb.SB);
     p = f2(0.0f);
     pt = f2(0.0f);
@@ -423,100 +479,122 @@ __device__ __forceinline__ void band_pair2(const Table<float> &tb, float2 tD, in
     for (int m = 0; m < 4; ++m) {
         float2 c[4];
 #pragma unroll
-        for (int n = 0; n < 4; ++n)  // an unused slot reads nothing
+        for (int n = 0; n < 4; ++n)  // an unused half reads nothing
             c[n] = make_float2(use0 ? lds32(a0 + m * rs + 4u * n) : 0.0f, use1 ? lds32(a1 + m * rs + 4u * n) : 0.0f);
         const float2 row = fma2(wdb[3], c[3], fma2(wdb[2], c[2], fma2(wdb[1], c[1], mul2(wdb[0], c[0]))));
         p = fma2(wD[m], row, p);
         if (POT) {
-            // delta derivative from exact coefficient differences (see combine)
-            const float2 c0n = mul2(c[0], f2(-1.0f));
-            const float2 drow = fma2(dwdb[3], add2(c[3], c0n), fma2(dwdb[2], add2(c[2], c0n), mul2(dwdb[1], add2(c[1], c0n))));
+            // delta derivative from exact coefficient differences (see combine);
+            // fma(c0, -1, c_n) is c_n - c0 with one rounding
+            const float2 m1 = f2(-1.0f);
+            const float2 drow = fma2(dwdb[3], fma2(c[0], m1, c[3]),
+                                     fma2(dwdb[2], fma2(c[0], m1, c[2]), mul2(dwdb[1], fma2(c[0], m1, c[1]))));
             pt = fma2(dwD[m], row, pt);
             pu = fma2(wD[m], drow, pu);
         }
     }
 }
 
-// The images of mask m for one (i, j) pair (FP32): two at a time with packed
-// arithmetic where both lie in the resident band, one at a time otherwise.
-// Adds sum_images phi, r dphi/dd1, r dphi/dd2 to sA, sU, cU; counts the inside
-// evaluations (ins) and those with r > 0 (hits).
-template <bool POT, bool SKEW, typename P>
-__device__ __forceinline__ void images_f32(unsigned m, const P *simg, float xi, float yi, float zi,
-                                           float qi, float inv_qi, float qi2, const P &pj,
-                                           const float h2[3], const float g2x[3], bool lane_ok, bool use_cut,
-                                           const Cut &cut, const Delta<float> &dp,
-                                           const Consts<float> &K, const Table<float> &tb,
-                                           float band_lo, float band_hi, float &sA, float &sU,
-                                           float &cU, unsigned &ins, unsigned &hits) {
-    float2 wdb[4], dwdb[4];
-#pragma unroll
-    for (int n = 0; n < 4; ++n) {
-        wdb[n] = f2(dp.wd[n]);
-        if (POT) dwdb[n] = f2(dp.dwd[n]);
-    }
-    const float2 sqcD = f2(dp.sq * K.cD);
-    const float bq = dp.isq * K.cd;
-    const float2 b1 = f2(bq * dp.sgn1), b2 = f2(-bq * dp.sgn2);
-    float2 A2 = f2(0.0f), U2 = f2(0.0f), V2 = f2(0.0f);
+// The images of two j points j0, j1 for one i point (FP32): half 0 runs over the
+// images of mask m0 (those of j0), half 1 over m1 (those of j1), one image of each
+// per step; a half whose mask is spent idles.  ex, ey, ez: x_i - x_j per half in
+// index units (integers, so every shifted difference is exact).  ok0, ok1: the
+// pair counts for this lane.  Adds sum_images phi, r dphi/dd1, r dphi/dd2 per half
+// to A2, U2, V2 and counts per half the inside evaluations (ins) and those with
+// r > 0 (hits).
+template <bool POT, bool SKEW>
+__device__ __forceinline__ void images2_f32(unsigned m0, unsigned m1, const float4 *simg, float2 ex, float2 ey,
+                                            float2 ez, float qi, float inv_qi, float qi2, float2 qj,
+                                            const float h2[3], const float g2x[3], bool ok0, bool ok1,
+                                            bool use_cut, const Cut &cut, const Delta2 &dp,
+                                            const Consts<float> &K, const Table<float> &tb, float band_lo,
+                                            float band_hi, float2 &A2, float2 &U2, float2 &V2,
+                                            unsigned &ins0, unsigned &ins1, unsigned &hit0, unsigned &hit1) {
+    const float2 H0 = f2(h2[0]), H1 = f2(h2[1]), H2 = f2(h2[2]);
+    const float2 cD2 = f2(K.cD);
+    A2 = f2(0.0f);
+    U2 = f2(0.0f);
+    V2 = f2(0.0f);
+    // band evaluations: r dphi/dd1 = cD r pt + b1 pu with b1, b2 fixed for the j point,
+    // so the sums of r pt and of pu over the images are scaled once at the end
+    float2 Srpt = f2(0.0f), Spu = f2(0.0f);
     do {
-        const int i0 = __ffs(m) - 1;
-        m &= m - 1u;
-        const bool two = m != 0u;
-        int i1 = i0;
-        if (two) {
-            i1 = __ffs(m) - 1;
-            m &= m - 1u;
-        }
-        const P s0 = simg[i0], s1 = simg[i1];
-        const float dx0 = (xi + s0.x) - pj.x, dy0 = (yi + s0.y) - pj.y, dz0 = (zi + s0.z) - pj.z;
-        const float dx1 = (xi + s1.x) - pj.x, dy1 = (yi + s1.y) - pj.y, dz1 = (zi + s1.z) - pj.z;
-        float r20 = h2[0] * (dx0 * dx0) + h2[1] * (dy0 * dy0) + h2[2] * (dz0 * dz0);
-        float r21 = h2[0] * (dx1 * dx1) + h2[1] * (dy1 * dy1) + h2[2] * (dz1 * dz1);
+        const bool u0 = m0 != 0u, u1 = m1 != 0u;
+        const int i0 = u0 ? __ffs(m0) - 1 : 0;  // a spent half reads a valid slot
+        const int i1 = u1 ? __ffs(m1) - 1 : 0;
+        m0 &= m0 - 1u;
+        m1 &= m1 - 1u;
+        const float4 s0 = simg[i0], s1 = simg[i1];
+        const float2 dx = add2(ex, make_float2(s0.x, s1.x));
+        const float2 dy = add2(ey, make_float2(s0.y, s1.y));
+        const float2 dz = add2(ez, make_float2(s0.z, s1.z));
+        float2 r2 = mul2(H2, mul2(dz, dz));
+        r2 = fma2(H1, mul2(dy, dy), r2);
+        r2 = fma2(H0, mul2(dx, dx), r2);
         if (SKEW) {
-            r20 += g2x[0] * (dx0 * dy0) + g2x[1] * (dx0 * dz0) + g2x[2] * (dy0 * dz0);
-            r21 += g2x[0] * (dx1 * dy1) + g2x[1] * (dx1 * dz1) + g2x[2] * (dy1 * dz1);
+            r2 = fma2(f2(g2x[0]), mul2(dx, dy), r2);
+            r2 = fma2(f2(g2x[1]), mul2(dx, dz), r2);
+            r2 = fma2(f2(g2x[2]), mul2(dy, dz), r2);
         }
-        const bool in0 = lane_ok && !(use_cut && beyond<SKEW>(r20, dx0, dy0, dz0, cut));
-        const bool in1 = two && lane_ok && !(use_cut && beyond<SKEW>(r21, dx1, dy1, dz1, cut));
+        const bool in0 = u0 && ok0 && !(use_cut && beyond<SKEW>(r2.x, dx.x, dy.x, dz.x, cut));
+        const bool in1 = u1 && ok1 && !(use_cut && beyond<SKEW>(r2.y, dx.y, dy.y, dz.y, cut));
         if (!(in0 || in1)) continue;
-        ins += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
-        hits += ((in0 && r20 > 0.0f) ? 1u : 0u) + ((in1 && r21 > 0.0f) ? 1u : 0u);
-        const float2 rr = make_float2(rlen(r20), rlen(r21));
-        const float2 tD = mul2(rr, sqcD);
+        ins0 += in0 ? 1u : 0u;
+        ins1 += in1 ? 1u : 0u;
+        hit0 += (in0 && r2.x > 0.0f) ? 1u : 0u;
+        hit1 += (in1 && r2.y > 0.0f) ? 1u : 0u;
+        const float2 rr = mul2(r2, make_float2(rsqrtf(fmaxf(r2.x, 1e-30f)), rsqrtf(fmaxf(r2.y, 1e-30f))));
+        const float2 tD = mul2(rr, dp.sqcD);
         const bool f0 = !in0 || (tD.x >= band_lo && tD.x < band_hi);
         const bool f1 = !in1 || (tD.y >= band_lo && tD.y < band_hi);
         if (f0 && f1) {
+            // both halves in the resident band; an idle half reads nothing: p, pt,
+            // pu are 0 there and add nothing
             const float2 tq = make_float2(in0 ? tD.x : band_lo, in1 ? tD.y : band_lo);
             float2 p, pt, pu;
-            band_pair2<POT>(tb, tq, dp.l, in0, in1, wdb, dwdb, p, pt, pu);
-            const float2 w = make_float2(in0 ? 1.0f : 0.0f, in1 ? 1.0f : 0.0f);
-            A2 = fma2(p, w, A2);
+            band_pair2<POT>(tb, tq, dp.l0, dp.l1, in0, in1, dp.wd, dp.dwd, p, pt, pu);
+            A2 = add2(A2, p);
             if (POT) {
-                const float2 a = mul2(mul2(rr, f2(K.cD)), pt);
-                U2 = fma2(fma2(pu, b1, a), w, U2);
-                V2 = fma2(fma2(pu, b2, a), w, V2);
+                Srpt = fma2(rr, pt, Srpt);
+                Spu = add2(Spu, pu);
             }
         } else {
             if (in0) {
                 float phi, rd = 0.0f, rd2 = 0.0f;
-                dist_part<POT, float>(r20, qi, pj.w, inv_qi, qi2, dp, K, tb, phi, rd, rd2);
+                dist_part<POT, float>(r2.x, qi, qj.x, inv_qi, qi2, delta_half<0>(dp), K, tb, phi, rd, rd2);
                 A2.x += phi;
                 U2.x += rd;
                 V2.x += rd2;
             }
             if (in1) {
                 float phi, rd = 0.0f, rd2 = 0.0f;
-                dist_part<POT, float>(r21, qi, pj.w, inv_qi, qi2, dp, K, tb, phi, rd, rd2);
+                dist_part<POT, float>(r2.y, qi, qj.y, inv_qi, qi2, delta_half<1>(dp), K, tb, phi, rd, rd2);
                 A2.y += phi;
                 U2.y += rd;
                 V2.y += rd2;
             }
         }
-    } while (m != 0u);
-    sA = A2.x + A2.y;
-    sU = U2.x + U2.y;
-    cU = V2.x + V2.y;
+    } while ((m0 | m1) != 0u);
+    if (POT) {
+        const float2 a = mul2(Srpt, cD2);
+        U2 = add2(U2, fma2(Spu, dp.b1, a));
+        V2 = add2(V2, fma2(Spu, dp.b2, a));
+    }
+}
+
+// Warp sums of four values: the total of v_k ends in lanes 8k .. 8k+7.  Two
+// halving exchanges (each lane keeps half of its values and sends the other
+// half) and three butterflies: 8 shuffles instead of 20 for four plain sums.
+__device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v3) {
+    const unsigned lane = threadIdx.x & 31u;
+    const bool h16 = (lane & 16u) != 0u, h8 = (lane & 8u) != 0u;
+    const float w0 = (h16 ? v2 : v0) + __shfl_xor_sync(0xffffffffu, h16 ? v0 : v2, 16);
+    const float w1 = (h16 ? v3 : v1) + __shfl_xor_sync(0xffffffffu, h16 ? v1 : v3, 16);
+    float x = (h8 ? w1 : w0) + __shfl_xor_sync(0xffffffffu, h8 ? w0 : w1, 8);
+    x += __shfl_xor_sync(0xffffffffu, x, 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    return x;
 }
 
 // MODE 0: energy (unordered pairs), MODE 1: potential (A, U per point).
@@ -745,63 +823,111 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
                 }
                 R a_acc = 0, u_acc = 0;  // i side (this lane's i)
                 R ja = 0, ju = 0;        // j side: lane L collects j = jb + L
-                for (int jj = 0; jj < jn; ++jj) {
-                    unsigned m = __shfl_sync(0xffffffffu, jm, jj);
-                    if (m == 0u) continue;
-                    item_evals += static_cast<unsigned>(__popc(m));
-                    const P pj = sp[jj];
-                    const R nj = sn[jj];
-                    // weights: off-diagonal tiles count every pair for i and for j; in the
-                    // diagonal tile j > i counts for both, j == i (self and self-images) for i only
-                    const bool both = !diag || jj > lane;
-                    const bool lane_ok = act && (both || jj == lane);
-                    Delta<R> dp;
-                    delta_part<POT, R>(qi, pj.w, K, dp);
-                    R sA = 0, sU = 0, cA = 0, cU = 0;
-                    unsigned ins = 0, hits = 0;
-                    if constexpr (sizeof(R) == 4) {
-                        images_f32<POT, SKEW, P>(m, simg, xi, yi, zi, qi, inv_qi, qi2, pj, h2, g2f, lane_ok,
-                                                 use_cut, cut, dp, K, tb, band_lo, band_hi, sA, sU, cU, ins,
-                                                 hits);
-                        cA = sA;
-                    } else do {
-                        const int b = __ffs(m) - 1;
-                        m &= m - 1u;
-                        const P sft = simg[b];
-                        const R dx = (xi + sft.x) - pj.x, dy = (yi + sft.y) - pj.y, dz = (zi + sft.z) - pj.z;
-                        R r2 = h2[0] * (dx * dx) + h2[1] * (dy * dy) + h2[2] * (dz * dz);
-                        if (SKEW) r2 += g2x[0] * (dx * dy) + g2x[1] * (dx * dz) + g2x[2] * (dy * dz);
-                        if (lane_ok && !(use_cut && beyond<SKEW>(r2, dx, dy, dz, cut))) {
-                            R phi, rd = 0, rd2 = 0;
-                            dist_part<POT, R>(r2, qi, pj.w, inv_qi, qi2, dp, K, tb, phi, rd, rd2);
-                            sA += phi;
-                            if (POT) {
-                                sU += rd;
-                                cA += phi;
-                                cU += rd2;
+                if constexpr (sizeof(R) == 4) {
+                    // two j points per pass (packed halves), in order of their lanes
+                    unsigned jset = __ballot_sync(0xffffffffu, jm != 0u);
+                    while (jset != 0u) {
+                        const int j0 = __ffs(jset) - 1;
+                        jset &= jset - 1u;
+                        const bool has1 = jset != 0u;
+                        const int j1 = has1 ? __ffs(jset) - 1 : j0;
+                        jset &= jset - 1u;
+                        const unsigned m0 = __shfl_sync(0xffffffffu, jm, j0);
+                        const unsigned m1s = __shfl_sync(0xffffffffu, jm, j1);
+                        const unsigned m1 = has1 ? m1s : 0u;
+                        item_evals += static_cast<unsigned>(__popc(m0) + __popc(m1));
+                        const float4 p0 = sp[j0], p1 = sp[j1];
+                        // weights: off-diagonal tiles count every pair for i and for j; in
+                        // the diagonal tile j > i counts for both, j == i (self and
+                        // self-images) for i only
+                        const bool both0 = !diag || j0 > lane, both1 = !diag || j1 > lane;
+                        const bool ok0 = act && (both0 || j0 == lane);
+                        const bool ok1 = has1 && act && (both1 || j1 == lane);
+                        Delta2 dp;
+                        bool cl0, cl1;
+                        const float2 qj = make_float2(p0.w, p1.w);
+                        delta_part2<POT>(qi, qj, K, dp, cl0, cl1);
+                        float2 A2, U2, V2;
+                        unsigned ins0 = 0, ins1 = 0, hit0 = 0, hit1 = 0;
+                        images2_f32<POT, SKEW>(m0, m1, simg, make_float2(xi - p0.x, xi - p1.x),
+                                               make_float2(yi - p0.y, yi - p1.y), make_float2(zi - p0.z, zi - p1.z),
+                                               qi, inv_qi, qi2, qj, h2, g2f, ok0, ok1, use_cut, cut, dp, K, tb,
+                                               band_lo, band_hi, A2, U2, V2, ins0, ins1, hit0, hit1);
+                        const unsigned wt0 = both0 ? 2u : 1u, wt1 = both1 ? 2u : 1u;  // ordered pairs
+                        cnt += hit0 * wt0 + hit1 * wt1;
+                        nclamp += (cl0 ? ins0 * wt0 : 0u) + (cl1 ? ins1 * wt1 : 0u);
+                        const float n0 = sn[j0], n1 = sn[j1];
+                        if (POT) {
+                            a_acc += n0 * A2.x + n1 * A2.y;
+                            u_acc += n0 * U2.x + n1 * U2.y;
+                            const float cA0 = both0 ? ni * A2.x : 0.0f, cU0 = both0 ? ni * V2.x : 0.0f;
+                            const float cA1 = both1 ? ni * A2.y : 0.0f, cU1 = both1 ? ni * V2.y : 0.0f;
+                            if (__any_sync(0xffffffffu, cA0 != 0.0f || cU0 != 0.0f || cA1 != 0.0f || cU1 != 0.0f)) {
+                                const float tot = warp_sum4(cA0, cU0, cA1, cU1);
+                                const bool second = has1 && lane == j1;
+                                const float gA = __shfl_sync(0xffffffffu, tot, second ? 16 : 0);
+                                const float gU = __shfl_sync(0xffffffffu, tot, second ? 24 : 8);
+                                if (lane == j0 || second) {
+                                    ja += gA;
+                                    ju += gU;
+                                }
                             }
-                            ins += 1u;
-                            hits += (r2 > R(0)) ? 1u : 0u;
+                        } else {
+                            a_acc += static_cast<float>(wt0) * n0 * A2.x + static_cast<float>(wt1) * n1 * A2.y;
                         }
-                    } while (m != 0u);
-                    const unsigned wt = both ? 2u : 1u;  // ordered pairs represented
-                    cnt += hits * wt;
-                    nclamp += dp.cl ? ins * wt : 0u;
-                    if (POT) {
-                        a_acc += nj * sA;
-                        u_acc += nj * sU;
-                    } else {
-                        a_acc += static_cast<R>(wt) * nj * sA;
                     }
-                    if (POT) {
-                        cA = both ? ni * cA : R(0);
-                        cU = both ? ni * cU : R(0);
-                        if (__any_sync(0xffffffffu, cA != R(0) || cU != R(0))) {
-                            cA = warp_sum(cA);
-                            cU = warp_sum(cU);
-                            if (lane == jj) {
-                                ja += cA;
-                                ju += cU;
+                } else {
+                    for (int jj = 0; jj < jn; ++jj) {
+                        unsigned m = __shfl_sync(0xffffffffu, jm, jj);
+                        if (m == 0u) continue;
+                        item_evals += static_cast<unsigned>(__popc(m));
+                        const P pj = sp[jj];
+                        const R nj = sn[jj];
+                        const bool both = !diag || jj > lane;
+                        const bool lane_ok = act && (both || jj == lane);
+                        Delta<R> dp;
+                        delta_part<POT, R>(qi, pj.w, K, dp);
+                        R sA = 0, sU = 0, cA = 0, cU = 0;
+                        unsigned ins = 0, hits = 0;
+                        do {
+                            const int b = __ffs(m) - 1;
+                            m &= m - 1u;
+                            const P sft = simg[b];
+                            const R dx = (xi + sft.x) - pj.x, dy = (yi + sft.y) - pj.y, dz = (zi + sft.z) - pj.z;
+                            R r2 = h2[0] * (dx * dx) + h2[1] * (dy * dy) + h2[2] * (dz * dz);
+                            if (SKEW) r2 += g2x[0] * (dx * dy) + g2x[1] * (dx * dz) + g2x[2] * (dy * dz);
+                            if (lane_ok && !(use_cut && beyond<SKEW>(r2, dx, dy, dz, cut))) {
+                                R phi, rd = 0, rd2 = 0;
+                                dist_part<POT, R>(r2, qi, pj.w, inv_qi, qi2, dp, K, tb, phi, rd, rd2);
+                                sA += phi;
+                                if (POT) {
+                                    sU += rd;
+                                    cA += phi;
+                                    cU += rd2;
+                                }
+                                ins += 1u;
+                                hits += (r2 > R(0)) ? 1u : 0u;
+                            }
+                        } while (m != 0u);
+                        const unsigned wt = both ? 2u : 1u;  // ordered pairs represented
+                        cnt += hits * wt;
+                        nclamp += dp.cl ? ins * wt : 0u;
+                        if (POT) {
+                            a_acc += nj * sA;
+                            u_acc += nj * sU;
+                        } else {
+                            a_acc += static_cast<R>(wt) * nj * sA;
+                        }
+                        if (POT) {
+                            cA = both ? ni * cA : R(0);
+                            cU = both ? ni * cU : R(0);
+                            if (__any_sync(0xffffffffu, cA != R(0) || cU != R(0))) {
+                                cA = warp_sum(cA);
+                                cU = warp_sum(cU);
+                                if (lane == jj) {
+                                    ja += cA;
+                                    ju += cU;
+                                }
                             }
                         }
                     }

@@ -151,6 +151,46 @@ def test_potential_small(V, dev, gtable, oracle_mod, oracle_spline, prec, tol):
         assert res["pairs"] == e["pairs"]
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_potential_far_pairs(V, dev, gtable, oracle_mod, oracle_spline, prec, tol):
+    """A metal-like slab under a 20 bohr cutoff on a coarse 24x20x40 grid: dense
+    layers (q0 up to ~4) put almost half of the pairs at D above 30 258/399 (past
+    the table rows the FP32 kernel keeps in shared memory) and a tenth past the
+    table (D > 30, eq. 17 times rho).  E, A, U and v against the oracle."""
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.slab_adsorbate((24, 20, 40))
+    P = _problem(oracle_mod, oracle_spline, w)
+    # the case does reach those D: a sample of 300 i points against every j and image
+    rng = np.random.default_rng(12)
+    dims = np.array(P.dims)
+    h = np.array(w["lengths"]) / dims
+    idx = np.array([P.i0, P.i1, P.i2], dtype=np.float64).T
+    I = rng.choice(P.n_active, 300, replace=False)
+    Ds = []
+    for m0 in range(-2, 3):
+        for m1 in range(-2, 3):
+            d = (idx[I][:, None, :] - idx[None, :, :] + np.array([m0, m1, 0]) * dims) * h
+            r = np.sqrt((d * d).sum(2))
+            Ds.append((0.5 * r * (P.qa[I][:, None] + P.qa[None, :]))[r <= w["r_cut"]])
+    D = np.concatenate(Ds)
+    assert np.mean(D > 30.0 * 258 / 399) > 0.3 and np.mean(D > 30.0) > 0.05
+    e = P.energy()
+    vo = P.potential(e["A"], e["U"])
+    E, v, res, A, U = V.potential(_t(w["density"], dev), w["lengths"], w["periodic"], w["n_cut"],
+                                  w["r_cut"], gtable, prec, want_AU=True)
+    assert _relerr(E, e["E"]) < (tol if prec == "fp64" else 1e-6), (E, e["E"])
+    flat = w["density"].ravel() >= w["n_cut"]
+    Ag = A.cpu().numpy().ravel()[flat]
+    Ug = U.cpu().numpy().ravel()[flat]
+    assert np.max(np.abs(Ag - e["A"])) < tol * np.max(np.abs(e["A"]))
+    assert np.max(np.abs(Ug - e["U"])) < tol * np.max(np.abs(e["U"]))
+    assert np.max(np.abs(v.cpu().numpy() - vo)) < tol * np.max(np.abs(vo))
+    assert res["pairs"] == e["pairs"]
+    Ee, rese = V.energy(_t(w["density"], dev), w["lengths"], w["periodic"], w["n_cut"], w["r_cut"],
+                        gtable, prec)
+    assert _relerr(Ee, e["E"]) < (tol if prec == "fp64" else 1e-6) and rese["pairs"] == e["pairs"]
+
+
 def test_edge_cases(V, dev, gtable, oracle_mod, oracle_spline):
     """No active point; one active point; grid sides not multiples of 4; huge cutoff."""
     rng = np.random.default_rng(8)
