@@ -113,6 +113,9 @@ typedef struct {
     float ms_pairs;          /* device time: pair kernel(s)                         */
     float ms_post;           /* device time: potential assembly and reductions      */
     int32_t launches;        /* kernels launched by this call                      */
+    int32_t smem_row0;       /* FP32 pair kernel: first table row held in shared
+                                memory (given, or chosen from the call's pairs);
+                                -1 on the FP64 path                                */
 } vdwdf_result;
 
 /* Optional launch shape of the pair kernel (NULL = defaults / tuned). */
@@ -121,8 +124,11 @@ typedef struct {
     int32_t items_per_sm; /* target work items per SM for load balance (0 = default) */
     int32_t smem_rows;    /* FP32 path: table rows resident in shared memory
                              (0 = as many as fit, -1 = none)                          */
-    int32_t smem_row0;    /* FP32 path: first resident table row (-1 = chosen from a
-                             sampled histogram of D over the call's pairs)           */
+    int32_t smem_row0;    /* FP32 path: first resident table row (-1 = chosen on the
+                             device from a sampled histogram of the table's D cell
+                             over the call's pair evaluations: the start whose rows
+                             hold the most; a NULL tuning chooses the same way;
+                             problems under 16384 active points keep row 0)         */
 } vdwdf_tuning;
 
 /* --------------------------------------------------------------------- */

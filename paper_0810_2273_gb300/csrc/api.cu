@@ -293,6 +293,7 @@ struct Work {
     double *A = nullptr, *U = nullptr;
     Stats *stats = nullptr;
     unsigned int *queue = nullptr;
+    unsigned int *hist = nullptr;  // kBandBins counters: the band-start histogram
 };
 
 size_t layout(const Geom &G, int nb, bool pot, bool fp64, Work *w, unsigned char *base) {
@@ -317,6 +318,7 @@ size_t layout(const Geom &G, int nb, bool pot, bool fp64, Work *w, unsigned char
     const size_t o_U = pot ? c.take<double>(N) : 0;
     const size_t o_st = c.take<Stats>(1);
     const size_t o_q = c.take<unsigned int>(1);
+    const size_t o_h = c.take<unsigned int>(kBandBins);
     if (w && base) {
         w->base = base;
         w->q0 = reinterpret_cast<double *>(base + o_q0);
@@ -337,6 +339,7 @@ size_t layout(const Geom &G, int nb, bool pot, bool fp64, Work *w, unsigned char
         w->U = pot ? reinterpret_cast<double *>(base + o_U) : nullptr;
         w->stats = reinterpret_cast<Stats *>(base + o_st);
         w->queue = reinterpret_cast<unsigned int *>(base + o_q);
+        w->hist = reinterpret_cast<unsigned int *>(base + o_h);
     }
     return c.off;
 }
@@ -466,10 +469,17 @@ Launch choose_launch(int precision, bool pot, const vdwdf_tuning *tu, const vdwd
         int rows = std::min(avail, t->nD + 2);
         if (tu && tu->smem_rows < 0) rows = 0;
         if (tu && tu->smem_rows > 0) rows = std::min(rows, tu->smem_rows);
-        int r0 = (tu && tu->smem_row0 > 0) ? tu->smem_row0 : 0;
-        r0 = std::min(r0, t->nD + 2 - rows);
-        ln.ks0 = std::max(0, r0);
         ln.ksn = rows;
+        // the band start is chosen on the device from the call's pairs (launch_band_choose);
+        // below kBandAutoMin active points the choice would cost more than it can save
+        constexpr long long kBandAutoMin = 16384;
+        if ((!tu || tu->smem_row0 < 0) && rows >= 4 && rows < t->nD + 2 && t->nD - 1 <= kBandBins &&
+            n_active >= kBandAutoMin) {
+            ln.ks0 = -1;
+        } else {
+            const int r0 = (tu && tu->smem_row0 > 0) ? tu->smem_row0 : 0;
+            ln.ks0 = std::max(0, std::min(r0, t->nD + 2 - rows));
+        }
     }
     return ln;
 }
@@ -543,6 +553,7 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
     Stats hs;
     std::memset(&hs, 0, sizeof(hs));
     double *item_buf = nullptr;
+    int row0 = 0;  // the band start given to the pair kernel (-1: chosen on the device)
     auto body = [&]() -> int {
         tm.mark(0, st);
         int r = prepare(G, n_dev, grad_dev, n_cut, pot, w, st);
@@ -571,6 +582,11 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
             }
             pl.ninst = 1;
             fill_params(G, w, pl.inst[0]);
+            if (ln.ks0 < 0) {
+                r = launch_band_choose(pl, w.hist, st);
+                if (r) return r;
+            }
+            row0 = ln.ks0;
             r = launch_pair(precision, pot, G.skew, ln.threads, pl, ln.nctas, st);
             if (r) return r;
             r = launch_reduce_items(pl, st);
@@ -602,6 +618,7 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
         out->ms_pairs = tm.ms(1, 2);
         out->ms_post = tm.ms(2, 3);
         out->launches = static_cast<int32_t>(g_launches.load() - launches0);
+        out->smem_row0 = precision == VDWDF_FP32 ? (row0 >= 0 ? row0 : hs.band_row0) : -1;
     }
     if (rc == VDWDF_OK) {
         cudaError_t e = cudaStreamSynchronize(st);
@@ -627,6 +644,7 @@ struct BatchPlan {
     cudaGraphExec_t exec = nullptr;
     int device = 0;
     int launches_per_replay = 0;
+    int row0 = 0;                    // band start of the first launch (-1: chosen on the device)
     ~BatchPlan() {
         if (exec) cudaGraphExecDestroy(exec);
         for (auto *b : bufs) cudaFree(b);
@@ -672,6 +690,11 @@ int record_batch(BatchPlan &bp, int ninst, const double *const *n_dev, double n_
         for (int k = k0; k < k1; ++k) {
             fill_params(bp.geo[k], bp.work[k], pl.inst[k - k0]);
             skew = skew || bp.geo[k].skew;
+        }
+        if (g == 0) bp.row0 = ln.ks0;
+        if (ln.ks0 < 0) {
+            int rc = launch_band_choose(pl, bp.work[k0].hist, st);
+            if (rc) return rc;
         }
         int rc = launch_pair(precision, false, skew, ln.threads, pl, ln.nctas, st);
         if (rc) return rc;
@@ -1260,6 +1283,7 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
         *out = tot;
         out->ms_pairs = tm.ms(0, 1);
         out->launches = static_cast<int32_t>(g_launches.load() - launches0);
+        out->smem_row0 = precision == VDWDF_FP32 ? (bp->row0 >= 0 ? bp->row0 : hs[0].band_row0) : -1;
     }
     return status;
 }
@@ -1296,10 +1320,10 @@ int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, do
         rc = VDWDF_ECUDA;
     if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
     constexpr int kCand = 7;
-    vdwdf_tuning cand[kCand] = {{256, 24, 0, 0}, {384, 24, 0, 0}, {512, 24, 0, 0}, {1024, 24, 0, 0},
-                                {512, 8, 0, 0},  {512, 64, 0, 0}, {512, 24, -1, 0}};
+    vdwdf_tuning cand[kCand] = {{256, 24, 0, -1}, {384, 24, 0, -1}, {512, 24, 0, -1}, {1024, 24, 0, -1},
+                                {512, 8, 0, -1},  {512, 64, 0, -1}, {512, 24, -1, 0}};
     double best_rate = -1.0;
-    vdwdf_tuning choice = {512, 24, 0, 0};
+    vdwdf_tuning choice = {512, 24, 0, -1};
     Timer tm;
     for (int ci = 0; ci < kCand && rc == VDWDF_OK && hs.n_active > 0; ++ci) {
         if (fp64 && cand[ci].smem_rows != 0) continue;
@@ -1318,6 +1342,7 @@ int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, do
             pl.sh.item_limit = static_cast<unsigned int>(4 * ln.nctas);
             pl.ninst = 1;
             fill_params(G, w, pl.inst[0]);
+            if (rc == VDWDF_OK && ln.ks0 < 0) rc = launch_band_choose(pl, w.hist, st);
             tm.mark(0, st);
             if (rc == VDWDF_OK) rc = launch_pair(precision, false, G.skew, ln.threads, pl, ln.nctas, st);
             tm.mark(1, st);
@@ -1477,8 +1502,10 @@ int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const doub
     std::memset(&hs, 0, sizeof(hs));
     VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
     VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+    int row0 = 0;
     if (hs.n_active > 0) {
         Launch ln = choose_launch(precision, false, nullptr, table, hs.n_active, G.skew);
+        row0 = ln.ks0;
         VDWDF_CUDA_TRY(cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st));  // work-queue head
         PairLaunch pl;
         std::memset(&pl, 0, sizeof(pl));
@@ -1490,6 +1517,10 @@ int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const doub
         pl.sh.item_cap = static_cast<unsigned int>(std::min<long long>(items, item_space));
         pl.ninst = 1;
         fill_params(G, w, pl.inst[0]);
+        if (ln.ks0 < 0) {
+            rc = launch_band_choose(pl, w.hist, st);
+            if (rc) return rc;
+        }
         rc = launch_pair(precision, false, G.skew, ln.threads, pl, ln.nctas, st);
         if (rc) return rc;
         rc = launch_reduce_items(pl, st);
@@ -1502,6 +1533,7 @@ int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const doub
         std::memset(out, 0, sizeof(*out));
         fill_result(hs, G, table, out);
         out->launches = static_cast<int32_t>(g_launches.load() - launches0);
+        out->smem_row0 = precision == VDWDF_FP32 ? (row0 >= 0 ? row0 : hs.band_row0) : -1;
     }
     return VDWDF_OK;
 }

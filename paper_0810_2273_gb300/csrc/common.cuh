@@ -40,6 +40,8 @@ struct Stats {
     unsigned int guard_trips;  // work loops that hit their iteration cap
     unsigned int qmin_bits, qmax_bits;  // q0 range of active points (FP32 bits; q0 > 0)
     int n_active;
+    int band_row0;             // FP32 pair kernel: first table row of the shared band when
+                               // chosen on the device (the first instance of a launch)
 };
 
 // Derivatives along the grid axes to Cartesian components: the gradient is
@@ -88,7 +90,8 @@ struct PairShared {
     int nD, nd;
     double cD, cd;        // tD = r (q_i + q_j) cD,  td = |q_i - q_j|/(q_i + q_j) cd
     double C_asym;
-    int ks0, ksn;         // FP32: table rows [ks0, ks0 + ksn) resident in shared memory
+    int ks0, ksn;         // FP32: table rows [ks0, ks0 + ksn) resident in shared memory;
+                          // ks0 < 0: ks0 is inst[0].stats->band_row0 (set by launch_band_choose)
     int jtiles_per_item;  // j tiles per work item
     unsigned int item_limit;  // process only the first item_limit items (autotuning)
     unsigned int max_iters;   // cap on the work loop of one CTA
@@ -125,6 +128,13 @@ int launch_pair(int precision, bool potential, bool skew, int threads, const Pai
 // consecutive rows falls in distinct banks.
 __host__ __device__ inline int band_stride(int S) { return S | 1; }
 int pair_smem_bytes(int precision, int threads, int ksn, int S);
+// The shared band's first row from the pairs of a launch: a sampled histogram
+// of the table's D cell over the (i, j, image) evaluations of every instance
+// (kBandBins counters in hist), then the start whose ksn rows hold the most
+// sampled stencils, written to inst[0].stats->band_row0.  Tables with more than
+// kBandBins + 1 rows along D keep row 0.
+constexpr int kBandBins = 1024;
+int launch_band_choose(const PairLaunch &pl, unsigned int *hist, cudaStream_t st);
 // Sum the energy-mode item partials of every instance in a fixed order into its
 // Stats::E_pair (one block per instance).
 int launch_reduce_items(const PairLaunch &pl, cudaStream_t st);

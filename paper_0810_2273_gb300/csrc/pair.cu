@@ -628,10 +628,10 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
     if constexpr (sizeof(R) == 4) {
         float *band = reinterpret_cast<float *>(smem_raw + (2 * sizeof(P) + sizeof(R)) * kTile * NW);
         tb.s = static_cast<uint32_t>(__cvta_generic_to_shared(band));
-        tb.k0 = sh.ks0;
+        tb.k0 = sh.ks0 >= 0 ? sh.ks0 : pl.inst[0].stats->band_row0;
         tb.kn = sh.ksn;
         const int S = sh.S, SB = tb.SB;
-        const float *src = sh.tab32 + static_cast<size_t>(sh.ks0) * S;
+        const float *src = sh.tab32 + static_cast<size_t>(tb.k0) * S;
         for (int row = warp; row < sh.ksn; row += NW)
             for (int col = lane; col < S; col += 32) band[row * SB + col] = __ldg(src + row * S + col);
     }
@@ -959,6 +959,100 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
     }
 }
 
+// The splitmix64 output function (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", 2014): a counter-based stream for sampling.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+constexpr int kBandSamples = 8;  // samples per thread of k_band_hist
+
+// Sampled histogram of the table's D cell over the evaluations of one problem:
+// uniform (i, j, image) triples (image index uniform in [-M_a, M_a] per periodic
+// axis), kept where r <= r_cut, binned by the stencil's first row floor(tD);
+// evaluations past the table (tD > nD - 1) read no row and are not counted.
+// The counts depend only on the sample indices: the result is reproducible.
+__global__ void k_band_hist(const __grid_constant__ PairShared sh, const __grid_constant__ PairParams pp,
+                            unsigned int *__restrict__ hist, unsigned int salt) {
+    __shared__ unsigned int h[kBandBins];
+    for (int b = threadIdx.x; b < kBandBins; b += blockDim.x) h[b] = 0u;
+    __syncthreads();
+    const int na = pp.stats->n_active;
+    const int kmax = sh.nD - 2;
+    if (na > 0 && kmax < kBandBins) {
+        const float h0 = static_cast<float>(pp.h2[0]), h1 = static_cast<float>(pp.h2[1]),
+                    h2 = static_cast<float>(pp.h2[2]);
+        const float g0 = static_cast<float>(pp.g2x[0]), g1 = static_cast<float>(pp.g2x[1]),
+                    g2 = static_cast<float>(pp.g2x[2]);
+        const float rc2 = static_cast<float>(pp.rc2), cD = static_cast<float>(sh.cD),
+                    tmax = static_cast<float>(sh.nD - 1);
+        const unsigned long long t0 =
+            (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) * kBandSamples;
+        for (int s = 0; s < kBandSamples; ++s) {
+            const unsigned long long x = mix64((static_cast<unsigned long long>(salt) << 40) + t0 + s);
+            const unsigned long long y = mix64(x ^ 0x9e3779b97f4a7c15ull);
+            const int i = static_cast<int>((x & 0xffffffffull) % static_cast<unsigned>(na));
+            const int j = static_cast<int>((x >> 32) % static_cast<unsigned>(na));
+            int m[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                m[a] = pp.M[a] > 0 ? static_cast<int>((y >> (21 * a)) % (2u * pp.M[a] + 1u)) - pp.M[a] : 0;
+            const float4 pi = __ldg(pp.p32 + i), pj = __ldg(pp.p32 + j);
+            const float dx = (pi.x - pj.x) + static_cast<float>(m[0] * pp.dims[0]);
+            const float dy = (pi.y - pj.y) + static_cast<float>(m[1] * pp.dims[1]);
+            const float dz = (pi.z - pj.z) + static_cast<float>(m[2] * pp.dims[2]);
+            const float r2 = h0 * dx * dx + h1 * dy * dy + h2 * dz * dz + g0 * dx * dy + g1 * dx * dz + g2 * dy * dz;
+            if (pp.use_cut && r2 > rc2) continue;
+            const float t = sqrtf(fmaxf(r2, 0.0f)) * (pi.w + pj.w) * cD;
+            if (!(t <= tmax)) continue;
+            atomicAdd(&h[min(static_cast<int>(t), kmax)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kBandBins; b += blockDim.x)
+        if (h[b]) atomicAdd(hist + b, h[b]);
+}
+
+// The band start r0 in [0, nD + 2 - ksn] whose stencils [r0, r0 + ksn - 4] hold the
+// most sampled evaluations; among starts within 0.2 % of the total of the best,
+// the last (evaluations that miss the band then have small D, where a warp's lanes
+// tend to miss together).  The block stages the histogram in shared memory; one
+// thread then slides the window over at most kBandBins rows.
+__global__ void k_band_choose(const __grid_constant__ PairShared sh, const unsigned int *__restrict__ hist,
+                              Stats *out) {
+    __shared__ unsigned int h[kBandBins];
+    for (int b = threadIdx.x; b < kBandBins; b += blockDim.x) h[b] = hist[b];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const int nk = sh.nD - 1;              // stencil starts 0 .. nD - 2
+    const int span = sh.ksn - 3;           // stencil starts a band of ksn rows holds
+    const int r0max = sh.nD + 2 - sh.ksn;  // last start that keeps the band in the table
+    int choice = 0;
+    if (nk <= kBandBins && span > 0 && r0max > 0) {
+        unsigned long long total = 0, cov = 0;
+        for (int k = 0; k < nk; ++k) total += h[k];
+        for (int k = 0; k < min(span, nk); ++k) cov += h[k];
+        unsigned long long best = cov, c = cov;
+        for (int r0 = 1; r0 <= r0max; ++r0) {
+            c -= h[r0 - 1];
+            if (r0 + span - 1 < nk) c += h[r0 + span - 1];
+            best = c > best ? c : best;
+        }
+        const unsigned long long tol = total / 500;
+        c = cov;
+        for (int r0 = 0; r0 <= r0max; ++r0) {
+            if (r0 > 0) {
+                c -= h[r0 - 1];
+                if (r0 + span - 1 < nk) c += h[r0 + span - 1];
+            }
+            if (c + tol >= best) choice = r0;
+        }
+    }
+    out->band_row0 = choice;
+}
+
 // Fixed-order sum of an instance's energy-mode item partials (block k: instance k).
 __global__ void k_reduce_items(const __grid_constant__ PairLaunch pl) {
     const int k = blockIdx.x;
@@ -1106,6 +1200,19 @@ int launch_pair(int precision, bool potential, bool skew, int threads, const Pai
                          : launch_nt<double, 0>(threads, skew, pl, nctas, smem, st);
     return potential ? launch_nt<float, 1>(threads, skew, pl, nctas, smem, st)
                      : launch_nt<float, 0>(threads, skew, pl, nctas, smem, st);
+}
+
+int launch_band_choose(const PairLaunch &pl, unsigned int *hist, cudaStream_t st) {
+    VDWDF_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kBandBins, st));
+    int dev = 0, sms = 0;
+    VDWDF_CUDA_TRY(cudaGetDevice(&dev));
+    VDWDF_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    for (int k = 0; k < pl.ninst; ++k)
+        k_band_hist<<<2 * (sms > 0 ? sms : 1), 256, 0, st>>>(pl.sh, pl.inst[k], hist, static_cast<unsigned>(k));
+    k_band_choose<<<1, 256, 0, st>>>(pl.sh, hist, pl.inst[0].stats);
+    count_launches(pl.ninst + 1);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
 }
 
 int launch_reduce_items(const PairLaunch &pl, cudaStream_t st) {
