@@ -281,6 +281,57 @@ def gradient_T_cell(w, cell):
     return out
 
 
+def _recip_rows(cell_or_lengths, shape):
+    """Reciprocal rows B_a (B_a . M_b = delta_ab) of a cell given as 3 lengths
+    (orthorhombic) or as 3x3 rows of lattice vectors."""
+    c = _f64(cell_or_lengths)
+    cell = np.diag(c) if c.shape == (3,) else c.reshape(3, 3)
+    return np.linalg.inv(cell).T
+
+
+def _spectral_multipliers(shape):
+    """2 pi i m_a along each axis for the DFT frequencies m_a in (-N/2, N/2); the
+    Nyquist frequency m_a = N_a/2 of an even axis gets 0 (it is its own mirror
+    image, so a real field has no odd part there: the real part of the inverse
+    transform drops it)."""
+    mult = []
+    for a, N in enumerate(shape):
+        m = np.fft.fftfreq(N, 1.0 / N)
+        k = 2j * np.pi * m
+        if N % 2 == 0:
+            k[N // 2] = 0.0
+        sh = [1, 1, 1]
+        sh[a] = N
+        mult.append(k.reshape(sh))
+    return mult
+
+
+def gradient_spectral(f, cell_or_lengths):
+    """The FFT gradient (section 3 of the paper, the FFTW option): df/du_a by
+    multiplying the discrete Fourier transform along u_a (fractional coordinate,
+    period 1) by 2 pi i m_a, then grad f = sum_a (df/du_a) B_a.  Returns [3][...]."""
+    f = _f64(f)
+    B = _recip_rows(cell_or_lengths, f.shape)
+    F = np.fft.fftn(f)
+    d = [np.real(np.fft.ifftn(k * F)) for k in _spectral_multipliers(f.shape)]
+    return np.stack([sum(B[a, c] * d[a] for a in range(3)) for c in range(3)])
+
+
+def gradient_spectral_T(w, cell_or_lengths):
+    """Transpose of gradient_spectral applied to w [3][...]: sum_c D_c^T w_c.  With
+    F the DFT, D_c = F^-1 Lambda_c F for purely imaginary Lambda_c, so
+    D_c^T = F^-1 conj(Lambda_c) F; written with the conjugate multipliers."""
+    w = _f64(w)
+    shape = w.shape[1:]
+    B = _recip_rows(cell_or_lengths, shape)
+    mult = _spectral_multipliers(shape)
+    out = np.zeros(shape)
+    for a in range(3):
+        Wa = sum(B[a, c] * w[c] for c in range(3))
+        out += np.real(np.fft.ifftn(np.conj(mult[a]) * np.fft.fftn(Wa)))
+    return out
+
+
 def q0(n, g):
     """q0 and its partials dq0/dn, dq0/dgrad n at every grid point."""
     n = _f64(n)
@@ -356,7 +407,7 @@ class Problem:
     of the library-style stencil.
     """
 
-    def __init__(self, density, lengths, periodic, n_cut, rc, spline, cell=None, g=None):
+    def __init__(self, density, lengths, periodic, n_cut, rc, spline, cell=None, g=None, gradient="fd"):
         self.n = _f64(density)
         self.dims = self.n.shape
         self.periodic = tuple(int(bool(p)) for p in periodic)
@@ -373,8 +424,14 @@ class Problem:
             self.lengths = None
             self.h = None
             self.dV = abs(float(np.linalg.det(self.cell))) / float(np.prod(self.dims))
+        if gradient not in ("fd", "spectral"):
+            raise ValueError("gradient: 'fd' or 'spectral'")
+        self.gradient_kind = gradient
+        geom = self.lengths if self.cell is None else self.cell
         if g is not None:
             self.g = _f64(g).reshape((3,) + self.dims)
+        elif gradient == "spectral":
+            self.g = gradient_spectral(self.n, geom)
         else:
             self.g = gradient(self.n, self.h) if self.cell is None else gradient_cell(self.n, self.cell)
         self.q0, self.dq0dn, self.dq0dg = q0(self.n, self.g)
@@ -434,7 +491,10 @@ class Problem:
         Ag[self.active] = A
         Ug[self.active] = U
         w = self.dq0dg.reshape(3, -1) * Ug[None, :]
-        if self.cell is None:
+        if self.gradient_kind == "spectral":
+            geom = self.lengths if self.cell is None else self.cell
+            div = gradient_spectral_T(w.reshape((3,) + self.dims), geom).ravel()
+        elif self.cell is None:
             div = gradient_T(w.reshape((3,) + self.dims), self.h).ravel()
         else:
             div = gradient_T_cell(w.reshape((3,) + self.dims), self.cell).ravel()
@@ -445,7 +505,10 @@ class Problem:
 
     def potential_at(self, points):
         """v at flat grid indices ``points`` from A, U at only the active points
-        in their stencil neighbourhoods (each point and +-1, +-2 along each axis)."""
+        in their stencil neighbourhoods (each point and +-1, +-2 along each axis).
+        Finite-difference gradient only (the spectral one couples whole lines)."""
+        if self.gradient_kind != "fd":
+            raise NotImplementedError("potential_at: finite-difference gradient only")
         points = np.asarray(points, dtype=np.int64)
         d = self.dims
         need = set()
