@@ -242,6 +242,9 @@ def gradient(f, h):
     return g
 
 
+_gradient_fd = gradient  # Problem's keyword ``gradient`` shadows the name there
+
+
 def gradient_T(w, h):
     """sum over axes of the transposed stencil applied to w (3, n0, n1, n2)."""
     w = _f64(w)
@@ -433,7 +436,7 @@ class Problem:
         elif gradient == "spectral":
             self.g = gradient_spectral(self.n, geom)
         else:
-            self.g = gradient(self.n, self.h) if self.cell is None else gradient_cell(self.n, self.cell)
+            self.g = _gradient_fd(self.n, self.h) if self.cell is None else gradient_cell(self.n, self.cell)
         self.q0, self.dq0dn, self.dq0dg = q0(self.n, self.g)
         flat = self.n.ravel()
         self.active = np.nonzero(flat >= self.n_cut)[0]          # row-major order
