@@ -71,14 +71,33 @@ extern "C" {
 #define VDWDF_FP32 0  /* FP32 pair arithmetic and interpolation, FP64 accumulation */
 #define VDWDF_FP64 1  /* FP64 throughout                                         */
 
+/* How the library differentiates the density (section 3: the gradient comes
+ * from an FFT, from real-space finite differences, or from the caller).  Both
+ * treat every axis of the grid as periodic.
+ *   VDWDF_GRAD_FD: 4th-order central differences along each grid axis,
+ *     (n_{-2} - 8 n_{-1} + 8 n_{+1} - n_{+2})/12 per index step;
+ *   VDWDF_GRAD_SPECTRAL: the band-limited (FFT) derivative along each grid axis:
+ *     the discrete Fourier transform times 2 pi i m, m in (-N/2, N/2), with the
+ *     Nyquist frequency of an even axis mapped to zero (the real part of the
+ *     inverse transform), applied as its circulant matrix; axes up to 12800
+ *     points.
+ * Either gives d/du_a along the fractional coordinates, and grad n = sum_a
+ * (d/du_a n) B_a with the reciprocal rows B_a.  The potential uses the transpose
+ * of the same operator. */
+#define VDWDF_GRAD_FD 0
+#define VDWDF_GRAD_SPECTRAL 1
+
 /* The grid: cell rows a, b, c in bohr (grid point (i,j,k) sits at
  * i/n0 a + j/n1 b + k/n2 c), points per axis, and per-axis periodicity
  * (section 2: "equidistant division in all three spatial dimensions";
- * Appendix A input: perx, pery, perz).  The density array is [n0][n1][n2]. */
+ * Appendix A input: perx, pery, perz).  The density array is [n0][n1][n2].
+ * gradient: VDWDF_GRAD_FD (0, the default of a zeroed struct) or
+ * VDWDF_GRAD_SPECTRAL; other values are VDWDF_EINVAL. */
 typedef struct {
     double cell[3][3];
     int32_t n[3];
     int32_t periodic[3];
+    int32_t gradient;
 } vdwdf_grid;
 
 /* Opaque kernel table: phi on the node grid D_k = Dmax k/(nD-1),
@@ -176,13 +195,19 @@ int vdwdf_kernel_eval(const vdwdf_table *t, int precision, int64_t npts,
 
 /* q0 = -(4 pi/3) [eps_c^LDA + eps_x^LDA (1 - (Zab/9) s^2)],
  * s = |grad n|/(2 k_F n), with eps_c^LDA of Perdew-Wang 1992, at every grid
- * point; points with n <= 0 give 0.  grad_dev: NULL (library stencil: 4th
- * order periodic central differences) or a [3][N] FP64 device array.
+ * point; points with n <= 0 give 0.  grad_dev: NULL (the library's gradient of
+ * the kind grid->gradient names) or a [3][N] FP64 device array (Cartesian).
  * Outputs q0_dev [N] and, when not NULL, dq0dn_dev [N], dq0dg_dev [3][N].
  * n_cut is not used (reserved). Asynchronous. */
 int vdwdf_q0(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev,
              double n_cut, double *q0_dev, double *dq0dn_dev, double *dq0dg_dev,
              void *cuda_stream);
+
+/* The library's gradient of n_dev ([N] FP64) of the kind grid->gradient names,
+ * into grad_dev ([3][N] FP64, Cartesian components, caller-owned).  The
+ * spectral kind allocates N0 + N1 + N2 doubles of stream-ordered scratch.
+ * VDWDF_EINVAL for null pointers or a bad grid.  Asynchronous. */
+int vdwdf_gradient(const vdwdf_grid *grid, const double *n_dev, double *grad_dev, void *cuda_stream);
 
 /* --------------------------------------------------------------------- */
 /* The double sum (paper section 2 eq. (2), section 3)                     */
@@ -205,8 +230,9 @@ int vdwdf_energy(const vdwdf_grid *grid, const double *n_dev, const double *grad
  * active points frozen), written to v_dev [N] FP64:
  *   v_m = dV [chi_m (A_m + U_m dq0/dn_m) - sum_axes D_h(U dq0/dgrad n)_m],
  *   A_i = sum_{j,L} n_j phi_ijL,  U_i = n_i sum_{j,L} n_j r dphi/dd1,
- * chi the active mask and D_h the library's gradient stencil (so the
- * gradient is always computed by the library here).  A_dev, U_dev: NULL or
+ * chi the active mask and D_h the library's gradient of the kind
+ * grid->gradient names (so the gradient is always computed by the library
+ * here; D_h is antisymmetric for both kinds, so its transpose is -D_h).  A_dev, U_dev: NULL or
  * [N] FP64 grid arrays that receive A and U (0 at inactive points).
  * Synchronises the stream. Errors as vdwdf_energy. */
 int vdwdf_potential(const vdwdf_grid *grid, const double *n_dev, double n_cut, double r_cut,
@@ -314,8 +340,8 @@ int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *
  *   w_a = chi U dq0/dgrad_a n,
  * the same form as the pair sum's adjoint (phi0' from the derivative of the
  * interpolant in ln q).  v (vdwdf_potential) + dv is the potential of
- * E - E_diag_table + E_diag_voxel.  Library gradient stencil (the adjoint needs
- * it).  out as in vdwdf_diag_voxel.  Synchronises the stream.
+ * E - E_diag_table + E_diag_voxel.  The library's gradient of the kind
+ * grid->gradient names (the adjoint needs it).  out as in vdwdf_diag_voxel.  Synchronises the stream.
  * Errors: as vdwdf_diag_voxel; VDWDF_EINVAL for a NULL dv_dev. */
 int vdwdf_diag_voxel_potential(const vdwdf_grid *grid, const double *n_dev, double n_cut,
                                const vdwdf_table *table, int nphi0, double *dv_dev, vdwdf_diag_result *out,

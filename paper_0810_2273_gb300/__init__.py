@@ -98,10 +98,18 @@ class Table:
             pass
 
 
-def grid(lengths, dims, periodic=(False, False, False)):
+_GRADIENTS = {"fd": 0, "spectral": 1}
+
+
+def grid(lengths, dims, periodic=(False, False, False), gradient="fd"):
     """vdwdf_grid for an orthorhombic cell lengths[0] x lengths[1] x lengths[2] bohr, or,
-    when ``lengths`` is 3x3, for the general cell whose rows are the lattice vectors."""
+    when ``lengths`` is 3x3, for the general cell whose rows are the lattice vectors.
+    gradient: "fd" (4th-order finite differences) or "spectral" (the band-limited,
+    FFT derivative), the library's gradient wherever it computes one."""
+    if gradient not in _GRADIENTS:
+        raise ValueError("gradient: 'fd' or 'spectral'")
     g = vdwdf_grid()
+    g.gradient = _GRADIENTS[gradient]
     cell = np.asarray(lengths, dtype=np.float64)
     for a in range(3):
         for b in range(3):
@@ -149,14 +157,14 @@ def _tuning(tu):
     return ctypes.byref(t)
 
 
-def energy(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", grad=None, tuning=None):
+def energy(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", grad=None, tuning=None, gradient="fd"):
     """E_c^nl (Hartree) of density n on the grid; returns (E, result dict)."""
     _check_tensor(n, "n")
     if grad is not None:
         _check_tensor(grad, "grad")
     torch = _torch()
     lib = _native.load()
-    g = grid(lengths, n.shape, periodic)
+    g = grid(lengths, n.shape, periodic, gradient)
     res = vdwdf_result()
     with torch.cuda.device(n.device):
         st = lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()),
@@ -167,7 +175,7 @@ def energy(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", grad=Non
     return res.E, res.as_dict()
 
 
-def energy_noalloc(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", grad=None):
+def energy_noalloc(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", grad=None, gradient="fd"):
     """As energy, through vdwdf_energy_noalloc: no allocation during the call (grids
     of at most 65536 points; the table must already be resident on n's device)."""
     _check_tensor(n, "n")
@@ -175,7 +183,7 @@ def energy_noalloc(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", 
         _check_tensor(grad, "grad")
     torch = _torch()
     lib = _native.load()
-    g = grid(lengths, n.shape, periodic)
+    g = grid(lengths, n.shape, periodic, gradient)
     res = vdwdf_result()
     with torch.cuda.device(n.device):
         st = lib.vdwdf_energy_noalloc(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()),
@@ -186,7 +194,7 @@ def energy_noalloc(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", 
     return res.E, res.as_dict()
 
 
-def semilocal(n, lengths, periodic, grad=None):
+def semilocal(n, lengths, periodic, grad=None, gradient="fd"):
     """E_x^LDA, E_c^LDA, E_x^PBE, E_c^PBE, E_x^revPBE (Hartree) of density n over all
     points with n > 0, through vdwdf_semilocal; returns the result dict."""
     _check_tensor(n, "n")
@@ -194,7 +202,7 @@ def semilocal(n, lengths, periodic, grad=None):
         _check_tensor(grad, "grad")
     torch = _torch()
     lib = _native.load()
-    g = grid(lengths, n.shape, periodic)
+    g = grid(lengths, n.shape, periodic, gradient)
     res = vdwdf_semilocal_result()
     with torch.cuda.device(n.device):
         st = lib.vdwdf_semilocal(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()),
@@ -219,7 +227,7 @@ def phi0_eval(table, voxel, q):
     return out
 
 
-def diag_voxel(n, lengths, periodic, n_cut, table, nphi0=0, grad=None):
+def diag_voxel(n, lengths, periodic, n_cut, table, nphi0=0, grad=None, gradient="fd"):
     """The voxel-averaged self term 1/2 dV^2 sum n_i^2 phi0(q0_i) over the points with
     n >= n_cut, and the table self term it replaces; returns the result dict.  E_c^nl
     with this diagonal is E - E_diag_table + E_diag_voxel."""
@@ -228,7 +236,7 @@ def diag_voxel(n, lengths, periodic, n_cut, table, nphi0=0, grad=None):
         _check_tensor(grad, "grad")
     torch = _torch()
     lib = _native.load()
-    g = grid(lengths, n.shape, periodic)
+    g = grid(lengths, n.shape, periodic, gradient)
     res = vdwdf_diag_result()
     with torch.cuda.device(n.device):
         st = lib.vdwdf_diag_voxel(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()),
@@ -238,14 +246,14 @@ def diag_voxel(n, lengths, periodic, n_cut, table, nphi0=0, grad=None):
     return res.as_dict()
 
 
-def diag_voxel_potential(n, lengths, periodic, n_cut, table, nphi0=0):
+def diag_voxel_potential(n, lengths, periodic, n_cut, table, nphi0=0, gradient="fd"):
     """(result dict, dv): the voxel diagonal as diag_voxel and the change dv of the
     potential when it replaces the table self term (v + dv belongs to
     E - E_diag_table + E_diag_voxel)."""
     _check_tensor(n, "n")
     torch = _torch()
     lib = _native.load()
-    g = grid(lengths, n.shape, periodic)
+    g = grid(lengths, n.shape, periodic, gradient)
     res = vdwdf_diag_result()
     dv = torch.empty_like(n)
     with torch.cuda.device(n.device):
@@ -270,12 +278,12 @@ def total_energy_nl(E_tot_dft, semi, E_c_nl, exchange="pbe"):
 
 
 def potential(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", tuning=None,
-              want_AU=False, out=None):
+              want_AU=False, out=None, gradient="fd"):
     """E_c^nl and v = dE/dn / dV on the grid; returns (E, v, result dict[, A, U])."""
     _check_tensor(n, "n")
     torch = _torch()
     lib = _native.load()
-    g = grid(lengths, n.shape, periodic)
+    g = grid(lengths, n.shape, periodic, gradient)
     v = out if out is not None else torch.empty_like(n)
     _check_tensor(v, "out")
     A = torch.empty_like(n) if want_AU else None
@@ -294,7 +302,7 @@ def potential(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", tunin
     return res.E, v, res.as_dict()
 
 
-def energy_batched(ns, lengths, periodic, n_cut, r_cut, table, precision="fp32", tuning=None):
+def energy_batched(ns, lengths, periodic, n_cut, r_cut, table, precision="fp32", tuning=None, gradient="fd"):
     """E_c^nl of several densities in one persistent launch (CUDA graph, replayed for the
     same tensors).  lengths / periodic: one entry per density.  Returns (E array, result)."""
     torch = _torch()
@@ -304,7 +312,7 @@ def energy_batched(ns, lengths, periodic, n_cut, r_cut, table, precision="fp32",
     ptrs = (ctypes.c_void_p * k)()
     for i, t in enumerate(ns):
         _check_tensor(t, "ns[%d]" % i)
-        grids[i] = grid(lengths[i], t.shape, periodic[i])
+        grids[i] = grid(lengths[i], t.shape, periodic[i], gradient)
         ptrs[i] = t.data_ptr()
     E = np.zeros(k)
     res = vdwdf_result()
@@ -316,12 +324,12 @@ def energy_batched(ns, lengths, periodic, n_cut, r_cut, table, precision="fp32",
     return E, res.as_dict()
 
 
-def q0(n, lengths, grad=None, want_partials=True):
+def q0(n, lengths, grad=None, want_partials=True, gradient="fd"):
     """q0 and (optionally) dq0/dn, dq0/dgrad n on the grid (Dion eqs. 11-12)."""
     _check_tensor(n, "n")
     torch = _torch()
     lib = _native.load()
-    g = grid(lengths, n.shape)
+    g = grid(lengths, n.shape, gradient=gradient)
     q = torch.empty_like(n)
     qn = torch.empty_like(n) if want_partials else None
     qg = torch.empty((3,) + tuple(n.shape), dtype=n.dtype, device=n.device) if want_partials else None
@@ -333,6 +341,22 @@ def q0(n, lengths, grad=None, want_partials=True):
                           ctypes.c_void_p(qg.data_ptr()) if want_partials else None, _stream(n))
     _native.check(st, "vdwdf_q0")
     return q, qn, qg
+
+
+def gradient(n, lengths, kind="fd"):
+    """The library's gradient of n (Cartesian, [3, *n.shape]) on the orthorhombic
+    cell ``lengths`` or the general cell (3x3 rows): kind "fd" (4th-order finite
+    differences) or "spectral" (the band-limited, FFT derivative)."""
+    _check_tensor(n, "n")
+    torch = _torch()
+    lib = _native.load()
+    g = grid(lengths, n.shape, gradient=kind)
+    out = torch.empty((3,) + tuple(n.shape), dtype=torch.float64, device=n.device)
+    with torch.cuda.device(n.device):
+        st = lib.vdwdf_gradient(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                _stream(n))
+    _native.check(st, "vdwdf_gradient")
+    return out
 
 
 def kernel_eval(table, r, qi, qj, precision="fp32"):
@@ -351,12 +375,12 @@ def kernel_eval(table, r, qi, qj, precision="fp32"):
     return phi, rd
 
 
-def autotune(n, lengths, periodic, n_cut, r_cut, table, precision="fp32"):
+def autotune(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", gradient="fd"):
     """Fastest launch shape of the pair kernel on this problem (a sampled energy pass)."""
     _check_tensor(n, "n")
     torch = _torch()
     lib = _native.load()
-    g = grid(lengths, n.shape, periodic)
+    g = grid(lengths, n.shape, periodic, gradient)
     best = vdwdf_tuning()
     with torch.cuda.device(n.device):
         st = lib.vdwdf_autotune(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()), float(n_cut), float(r_cut),
@@ -377,12 +401,13 @@ def _make_function():
         """E_c^nl as a differentiable function of the density tensor n.
 
         forward(n, spec) -> E (0-d FP64 tensor); backward gives grad * dE/dn_m =
-        grad * dV * v_m, from the library's fused pair pass and adjoint stencil."""
+        grad * dV * v_m, from the library's fused pair pass and the adjoint of its gradient."""
 
         @staticmethod
         def forward(ctx, n, spec):
             E, v, _ = potential(n, spec["lengths"], spec["periodic"], spec["n_cut"], spec["r_cut"],
-                                spec["table"], spec.get("precision", "fp32"), spec.get("tuning"))
+                                spec["table"], spec.get("precision", "fp32"), spec.get("tuning"),
+                                gradient=spec.get("gradient", "fd"))
             dV = _cell_volume(spec["lengths"]) / float(n.numel())
             ctx.save_for_backward(v)
             ctx.dV = dV
@@ -400,7 +425,8 @@ _FN = None
 
 
 def nonlocal_energy(n, spec):
-    """Differentiable E_c^nl(n); spec: dict(lengths, periodic, n_cut, r_cut, table[, precision])."""
+    """Differentiable E_c^nl(n); spec: dict(lengths, periodic, n_cut, r_cut, table[, precision,
+    tuning, gradient])."""
     global _FN
     if _FN is None:
         _FN = _make_function()

@@ -21,7 +21,7 @@ _c_p = ctypes.c_void_p
 
 
 class vdwdf_grid(ctypes.Structure):
-    _fields_ = [("cell", (_c_d * 3) * 3), ("n", _c_i32 * 3), ("periodic", _c_i32 * 3)]
+    _fields_ = [("cell", (_c_d * 3) * 3), ("n", _c_i32 * 3), ("periodic", _c_i32 * 3), ("gradient", _c_i32)]
 
 
 class vdwdf_result(ctypes.Structure):
@@ -64,6 +64,7 @@ PROTOTYPES = {
     "vdwdf_table_free": (None, [_c_p]),
     "vdwdf_kernel_eval": (_c_i, [_c_p, _c_i, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
     "vdwdf_q0": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_d, _c_p, _c_p, _c_p, _c_p]),
+    "vdwdf_gradient": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_p]),
     "vdwdf_energy": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_d, _c_d, _c_p, _c_i,
                             ctypes.POINTER(vdwdf_tuning), ctypes.POINTER(vdwdf_result), _c_p]),
     "vdwdf_potential": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_d, _c_d, _c_p, _c_i,

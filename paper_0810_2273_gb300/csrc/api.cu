@@ -178,6 +178,7 @@ struct Geom {
     bool skew;          // non-diagonal metric
     AxisMap am;         // grid-axis derivatives to Cartesian gradient
     CellRows vrow;      // M_a / N_a (float), for Cartesian tile boxes
+    bool spectral;      // gradient by the band-limited (FFT) derivative
 };
 
 // Smallest eigenvalue of the symmetric 3x3 matrix (a00, a11, a22, a01, a02, a12)
@@ -203,11 +204,14 @@ int check_grid(const vdwdf_grid *g, Geom &G) {
     for (int a = 0; a < 3; ++a) {
         if (g->n[a] < 1 || g->n[a] > (1 << 20)) return VDWDF_EINVAL;
         if (g->periodic[a] != 0 && g->periodic[a] != 1) return VDWDF_EINVAL;
+        if (g->n[a] > 12800 && g->gradient == VDWDF_GRAD_SPECTRAL) return VDWDF_EUNSUPPORTED;
         N *= g->n[a];
         for (int b = 0; b < 3; ++b)
             if (!std::isfinite(M[a][b])) return VDWDF_EINVAL;
     }
     if (N > (1LL << 31) - 1) return VDWDF_EINVAL;
+    if (g->gradient != VDWDF_GRAD_FD && g->gradient != VDWDF_GRAD_SPECTRAL) return VDWDF_EINVAL;
+    G.spectral = g->gradient == VDWDF_GRAD_SPECTRAL;
     const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
                        M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
                        M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
@@ -294,6 +298,7 @@ struct Work {
     Stats *stats = nullptr;
     unsigned int *queue = nullptr;
     unsigned int *hist = nullptr;  // kBandBins counters: the band-start histogram
+    double *gsp = nullptr, *coef = nullptr, *div = nullptr;  // spectral gradient only
 };
 
 size_t layout(const Geom &G, int nb, bool pot, bool fp64, Work *w, unsigned char *base) {
@@ -319,6 +324,9 @@ size_t layout(const Geom &G, int nb, bool pot, bool fp64, Work *w, unsigned char
     const size_t o_st = c.take<Stats>(1);
     const size_t o_q = c.take<unsigned int>(1);
     const size_t o_h = c.take<unsigned int>(kBandBins);
+    const size_t o_gsp = G.spectral ? c.take<double>(3 * N) : 0;
+    const size_t o_coef = G.spectral ? c.take<double>(G.dims[0] + G.dims[1] + G.dims[2]) : 0;
+    const size_t o_div = (G.spectral && pot) ? c.take<double>(N) : 0;
     if (w && base) {
         w->base = base;
         w->q0 = reinterpret_cast<double *>(base + o_q0);
@@ -340,6 +348,9 @@ size_t layout(const Geom &G, int nb, bool pot, bool fp64, Work *w, unsigned char
         w->stats = reinterpret_cast<Stats *>(base + o_st);
         w->queue = reinterpret_cast<unsigned int *>(base + o_q);
         w->hist = reinterpret_cast<unsigned int *>(base + o_h);
+        w->gsp = G.spectral ? reinterpret_cast<double *>(base + o_gsp) : nullptr;
+        w->coef = G.spectral ? reinterpret_cast<double *>(base + o_coef) : nullptr;
+        w->div = (G.spectral && pot) ? reinterpret_cast<double *>(base + o_div) : nullptr;
     }
     return c.off;
 }
@@ -351,6 +362,38 @@ int reset_stats(Stats *s, cudaStream_t st) {
     return VDWDF_OK;
 }
 
+Recip recip_of(const Geom &G) {
+    Recip R;
+    for (int k = 0; k < 9; ++k) R.B[k] = G.B[k];
+    return R;
+}
+
+// The gradient the q0 step reads: the caller's; else, on a grid with the spectral
+// option, the FFT gradient written to gsp (3 N) with coef (N0 + N1 + N2) as
+// scratch; else none (the q0 kernel's own finite differences).
+int q0_gradient(const Geom &G, const double *n_dev, const double *grad_dev, double *gsp, double *coef,
+                const double **use, cudaStream_t st) {
+    *use = grad_dev;
+    if (grad_dev || !G.spectral) return VDWDF_OK;
+    *use = gsp;
+    return launch_gradient_spectral(G.dims, recip_of(G), n_dev, gsp, coef, st);
+}
+
+// v (and the A, U grids) from A, U at the active points, with the transpose of
+// the grid's own gradient: the spectral one through W (3 N) and div (N), else
+// the stencil inside the assembly kernel.
+int assemble_v(const Geom &G, const int *slot, const double *A, const double *U, const double *qn,
+               const double *qg, double *W, double *div, double *coef, double *v, double *A_grid, double *U_grid,
+               cudaStream_t st) {
+    const double *dp = nullptr;
+    if (G.spectral) {
+        const int rc = launch_div_spectral(G.dims, recip_of(G), slot, U, qg, W, div, coef, st);
+        if (rc) return rc;
+        dp = div;
+    }
+    return launch_assemble(G.dims, G.am, G.dV, slot, A, U, qn, qg, dp, v, A_grid, U_grid, st);
+}
+
 // gradient, q0, trimming and tiles of one problem into w
 int prepare(const Geom &G, const double *n_dev, const double *grad_dev, double n_cut, bool pot,
             Work &w, cudaStream_t st) {
@@ -359,7 +402,10 @@ int prepare(const Geom &G, const double *n_dev, const double *grad_dev, double n
     if (rc) return rc;
     rc = reset_stats(w.stats, st);
     if (rc) return rc;
-    rc = launch_grad_q0(G.dims, G.am, n_dev, grad_dev, w.q0, w.qn, w.qg, st);
+    const double *g_use = nullptr;
+    rc = q0_gradient(G, n_dev, grad_dev, w.gsp, w.coef, &g_use, st);
+    if (rc) return rc;
+    rc = launch_grad_q0(G.dims, G.am, n_dev, g_use, w.q0, w.qn, w.qg, st);
     if (rc) return rc;
     rc = launch_compact(G.dims, n_dev, n_cut, w.q0, order, nb, w.cnt, w.off, pot ? w.slot : nullptr,
                         w.p32, w.n32, w.p64, w.n64, w.blo, w.bhi, w.stats, st);
@@ -594,7 +640,7 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
         }
         tm.mark(2, st);
         if (pot) {
-            r = launch_assemble(G.dims, G.am, G.dV, w.slot, w.A, w.U, w.qn, w.qg, v_dev, A_grid, U_grid, st);
+            r = assemble_v(G, w.slot, w.A, w.U, w.qn, w.qg, w.gsp, w.div, w.coef, v_dev, A_grid, U_grid, st);
             if (r) return r;
             r = launch_energy_from_A(static_cast<int>(G.N), w.A, w.n64, w.stats, st);
             if (r) return r;
@@ -909,8 +955,33 @@ int vdwdf_q0(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev
     int rc = check_grid(grid, G);
     if (rc) return rc;
     if (!n_dev || !q0_dev) return VDWDF_EINVAL;
-    return launch_grad_q0(G.dims, G.am, n_dev, grad_dev, q0_dev, dq0dn_dev, dq0dg_dev,
-                          static_cast<cudaStream_t>(cuda_stream));
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (grad_dev || !G.spectral) return launch_grad_q0(G.dims, G.am, n_dev, grad_dev, q0_dev, dq0dn_dev, dq0dg_dev, st);
+    double *buf = nullptr;
+    const size_t nd = 3 * static_cast<size_t>(G.N) + G.dims[0] + G.dims[1] + G.dims[2];
+    if (scratch_malloc_async(reinterpret_cast<void **>(&buf), nd * sizeof(double), st) != cudaSuccess)
+        return VDWDF_EALLOC;
+    const double *g_use = nullptr;
+    rc = q0_gradient(G, n_dev, nullptr, buf, buf + 3 * G.N, &g_use, st);
+    if (rc == VDWDF_OK) rc = launch_grad_q0(G.dims, G.am, n_dev, g_use, q0_dev, dq0dn_dev, dq0dg_dev, st);
+    cudaFreeAsync(buf, st);
+    return rc;
+}
+
+int vdwdf_gradient(const vdwdf_grid *grid, const double *n_dev, double *grad_dev, void *cuda_stream) {
+    Geom G;
+    int rc = check_grid(grid, G);
+    if (rc) return rc;
+    if (!n_dev || !grad_dev) return VDWDF_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (!G.spectral) return launch_gradient_fd(G.dims, G.am, n_dev, grad_dev, st);
+    double *coef = nullptr;
+    const size_t nc = static_cast<size_t>(G.dims[0] + G.dims[1] + G.dims[2]);
+    if (scratch_malloc_async(reinterpret_cast<void **>(&coef), nc * sizeof(double), st) != cudaSuccess)
+        return VDWDF_EALLOC;
+    rc = launch_gradient_spectral(G.dims, recip_of(G), n_dev, grad_dev, coef, st);
+    cudaFreeAsync(coef, st);
+    return rc;
 }
 
 int vdwdf_semilocal(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev,
@@ -922,13 +993,17 @@ int vdwdf_semilocal(const vdwdf_grid *grid, const double *n_dev, const double *g
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const long long launches0 = g_launches.load();
     const size_t nd = static_cast<size_t>(semilocal_scratch_doubles());
+    // the spectral gradient (when the grid asks for it and none is given) after the sums
+    const size_t nsp = (G.spectral && !grad_dev) ? 3 * static_cast<size_t>(G.N) + G.dims[0] + G.dims[1] + G.dims[2] : 0;
     double *scratch = nullptr;
-    if (scratch_malloc_async(reinterpret_cast<void **>(&scratch), nd * sizeof(double), st) != cudaSuccess)
+    if (scratch_malloc_async(reinterpret_cast<void **>(&scratch), (nd + nsp) * sizeof(double), st) != cudaSuccess)
         return VDWDF_EALLOC;
     Timer tm;
     double sums[6] = {0, 0, 0, 0, 0, 0};
     tm.mark(0, st);
-    rc = launch_semilocal(G.dims, G.am, n_dev, grad_dev, scratch, st);
+    const double *g_use = nullptr;
+    rc = q0_gradient(G, n_dev, grad_dev, scratch + nd, scratch + nd + 3 * G.N, &g_use, st);
+    if (rc == VDWDF_OK) rc = launch_semilocal(G.dims, G.am, n_dev, g_use, scratch, st);
     tm.mark(1, st);
     if (rc == VDWDF_OK &&
         cudaMemcpyAsync(sums, scratch + nd - 6, sizeof(sums), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -1022,6 +1097,10 @@ int diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
     const size_t o_qn = pot ? c.take<double>(G.N) : 0, o_qgr = pot ? c.take<double>(3 * G.N) : 0,
                  o_slot = pot ? c.take<int>(G.N) : 0, o_A = pot ? c.take<double>(G.N) : 0,
                  o_U = pot ? c.take<double>(G.N) : 0;
+    // spectral gradient: the gradient (then the potential's weights), coefficients, divergence
+    const size_t o_gsp = G.spectral ? c.take<double>(3 * G.N) : 0,
+                 o_coef = G.spectral ? c.take<double>(G.dims[0] + G.dims[1] + G.dims[2]) : 0,
+                 o_div = (G.spectral && pot) ? c.take<double>(G.N) : 0;
     unsigned char *base = nullptr;
     if (scratch_malloc_async(reinterpret_cast<void **>(&base), c.off, st) != cudaSuccess) return VDWDF_EALLOC;
     double *q0 = reinterpret_cast<double *>(base + o_q0);
@@ -1034,6 +1113,9 @@ int diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
     int *slot = pot ? reinterpret_cast<int *>(base + o_slot) : nullptr;
     double *Ad = pot ? reinterpret_cast<double *>(base + o_A) : nullptr;
     double *Ud = pot ? reinterpret_cast<double *>(base + o_U) : nullptr;
+    double *gsp = G.spectral ? reinterpret_cast<double *>(base + o_gsp) : nullptr;
+    double *coef = G.spectral ? reinterpret_cast<double *>(base + o_coef) : nullptr;
+    double *divb = (G.spectral && pot) ? reinterpret_cast<double *>(base + o_div) : nullptr;
     Timer tm;
     unsigned long long hmm[3] = {0, 0, 0};
     double hs[2] = {0.0, 0.0};
@@ -1041,7 +1123,10 @@ int diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
     double lnq0 = 0.0, dlnq = 1.0;
     auto body = [&]() -> int {
         tm.mark(0, st);
-        int r = launch_grad_q0(G.dims, G.am, n_dev, grad_dev, q0, qn, qgr, st);
+        const double *g_use = nullptr;
+        int r = q0_gradient(G, n_dev, grad_dev, gsp, coef, &g_use, st);
+        if (r) return r;
+        r = launch_grad_q0(G.dims, G.am, n_dev, g_use, q0, qn, qgr, st);
         if (r) return r;
         if (pot) VDWDF_CUDA_TRY(cudaMemsetAsync(dv_dev, 0, sizeof(double) * G.N, st));
         VDWDF_CUDA_TRY(cudaMemsetAsync(mm, 0xFF, sizeof(unsigned long long), st));
@@ -1073,7 +1158,7 @@ int diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
         if (pot) {
             r = launch_diag_AU(G.N, n_dev, q0, n_cut, tab, nq, lnq0, dlnq, table->nodes[0], slot, Ad, Ud, st);
             if (r) return r;
-            r = launch_assemble(G.dims, G.am, G.dV, slot, Ad, Ud, qn, qgr, dv_dev, nullptr, nullptr, st);
+            r = assemble_v(G, slot, Ad, Ud, qn, qgr, gsp, divb, coef, dv_dev, nullptr, nullptr, st);
             if (r) return r;
         }
         tm.mark(1, st);
@@ -1489,7 +1574,10 @@ int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const doub
     if (rc) return rc;
     rc = reset_stats(w.stats, st);  // counters start at zero (q0 minimum above all floats)
     if (rc) return rc;
-    rc = launch_grad_q0(G.dims, G.am, n_dev, grad_dev, w.q0, w.qn, w.qg, st);
+    const double *g_use = nullptr;
+    rc = q0_gradient(G, n_dev, grad_dev, w.gsp, w.coef, &g_use, st);
+    if (rc) return rc;
+    rc = launch_grad_q0(G.dims, G.am, n_dev, g_use, w.q0, w.qn, w.qg, st);
     if (rc) return rc;
     rc = launch_compact(G.dims, n_dev, n_cut, w.q0, order_dev, nb, w.cnt, w.off, nullptr, w.p32, w.n32,
                         w.p64, w.n64, w.blo, w.bhi, w.stats, st);

@@ -25,8 +25,8 @@ __device__ __forceinline__ int wrap(int i, int n) {
 __global__ void k_assemble(int n0, int n1, int n2, const AxisMap am, double dV,
                            const int *__restrict__ slot, const double *__restrict__ A,
                            const double *__restrict__ U, const double *__restrict__ qn,
-                           const double *__restrict__ qg, double *__restrict__ v,
-                           double *__restrict__ Ag, double *__restrict__ Ug) {
+                           const double *__restrict__ qg, const double *__restrict__ div_pre,
+                           double *__restrict__ v, double *__restrict__ Ag, double *__restrict__ Ug) {
     const long long N = static_cast<long long>(n0) * n1 * n2;
     for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < N;
          m += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -48,7 +48,7 @@ __global__ void k_assemble(int n0, int n1, int n2, const AxisMap am, double dV,
         auto ia = [&](int aa) { return static_cast<long long>(wrap(aa, n0)) * sa + static_cast<long long>(b) * n2 + c; };
         auto ib = [&](int bb) { return static_cast<long long>(a) * sa + static_cast<long long>(wrap(bb, n1)) * n2 + c; };
         auto ic = [&](int cc) { return static_cast<long long>(a) * sa + static_cast<long long>(b) * n2 + wrap(cc, n2); };
-        const double div =
+        const double div = div_pre ? div_pre[m] :
             (8.0 * (w(ia(a + 1), 0) - w(ia(a - 1), 0)) - (w(ia(a + 2), 0) - w(ia(a - 2), 0))) * f0 +
             (8.0 * (w(ib(b + 1), 1) - w(ib(b - 1), 1)) - (w(ib(b + 2), 1) - w(ib(b - 2), 1))) * f1 +
             (8.0 * (w(ic(c + 1), 2) - w(ic(c - 1), 2)) - (w(ic(c + 2), 2) - w(ic(c - 2), 2))) * f2;
@@ -244,13 +244,13 @@ int launch_diag_AU(long long N, const double *n, const double *q0, double n_cut,
 
 int launch_assemble(const int dims[3], const AxisMap &am, double dV, const int *slot,
                     const double *A, const double *U, const double *dq0dn, const double *dq0dg,
-                    double *v, double *A_grid, double *U_grid, cudaStream_t st) {
+                    const double *div_pre, double *v, double *A_grid, double *U_grid, cudaStream_t st) {
     const long long N = static_cast<long long>(dims[0]) * dims[1] * dims[2];
     const int bs = 256;
     long long nb = (N + bs - 1) / bs;
     if (nb > 1 << 20) nb = 1 << 20;
     k_assemble<<<static_cast<int>(nb), bs, 0, st>>>(dims[0], dims[1], dims[2], am, dV, slot, A, U, dq0dn,
-                                                     dq0dg, v, A_grid, U_grid);
+                                                     dq0dg, div_pre, v, A_grid, U_grid);
     count_launches(1);
     VDWDF_CUDA_TRY(cudaGetLastError());
     return VDWDF_OK;

@@ -115,6 +115,8 @@ int launch_semilocal(const int dims[3], const AxisMap &am, const double *n, cons
 // Cartesian bounding boxes of the tiles of a general cell (rows v_a = M_a / N_a).
 int launch_tiles_cart(const float4 *p32, const Stats *stats, const CellRows &vrow, float4 *clo, float4 *chi,
                       long long n_max, cudaStream_t st);
+// The 4th-order finite-difference gradient (Cartesian, 3 planes of N) of n.
+int launch_gradient_fd(const int dims[3], const AxisMap &am, const double *n, double *grad, cudaStream_t st);
 int launch_grad_q0(const int dims[3], const AxisMap &am, const double *n, const double *grad_in,
                    double *q0, double *dq0dn, double *dq0dg, cudaStream_t st);
 int launch_compact(const int dims[3], const double *n, double n_cut, const double *q0,
@@ -143,9 +145,24 @@ __host__ __device__ inline long long pair_items(long long n_active, int jt) {
     const long long nT = (n_active + kTile - 1) / kTile;
     return nT * ((nT + jt - 1) / jt);
 }
+// v = dV (chi (A + U dq0/dn) - div), div the divergence term: div_pre when given
+// (the spectral gradient's, from launch_div_spectral), else the 4th-order stencil's.
 int launch_assemble(const int dims[3], const AxisMap &am, double dV, const int *slot,
                     const double *A, const double *U, const double *dq0dn, const double *dq0dg,
-                    double *v, double *A_grid, double *U_grid, cudaStream_t st);
+                    const double *div_pre, double *v, double *A_grid, double *U_grid, cudaStream_t st);
+// Reciprocal rows of the cell, B[3a + c] = (B_a)_c with B_a . M_b = delta_ab.
+struct Recip {
+    double B[9];
+};
+// The spectral (FFT) gradient: grad (3 planes of N, Cartesian) of n; coef holds
+// N0 + N1 + N2 doubles of scratch.  VDWDF_EUNSUPPORTED beyond 12,800 points per axis.
+int launch_gradient_spectral(const int dims[3], const Recip &R, const double *n, double *grad, double *coef,
+                             cudaStream_t st);
+// The divergence term of the potential with the spectral gradient:
+// div = sum_a D_a W_a, W_a = sum_c (B_a)_c U dq0/dg_c (0 at inactive points), so
+// that v = dV (chi (A + U dq0/dn) - div).  W: 3 planes of N scratch.
+int launch_div_spectral(const int dims[3], const Recip &R, const int *slot, const double *U, const double *qg,
+                        double *W, double *div, double *coef, cudaStream_t st);
 int launch_energy_from_A(int n_max, const double *A, const double *n64, Stats *stats,
                          cudaStream_t st);
 // Voxel-averaged diagonal: voxel rows v (M_a / N_a), the small-D model below D1

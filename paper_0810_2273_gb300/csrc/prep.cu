@@ -379,6 +379,20 @@ __global__ void k_semilocal_sum(const double *__restrict__ part, int nblocks, do
     }
 }
 
+// The finite-difference gradient alone (Cartesian, 3 planes of N).
+__global__ void k_gradient_fd(int n0, int n1, int n2, const AxisMap am, const double *__restrict__ n,
+                              double *__restrict__ g) {
+    const long long N = static_cast<long long>(n0) * n1 * n2;
+    for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < N;
+         m += static_cast<long long>(gridDim.x) * blockDim.x) {
+        double gx, gy, gz;
+        grad_at(m, n0, n1, n2, am, n, nullptr, gx, gy, gz);
+        g[m] = gx;
+        g[N + m] = gy;
+        g[2 * N + m] = gz;
+    }
+}
+
 }  // namespace
 
 int semilocal_scratch_doubles() { return (kSemiBlocks + 1) * kSemiVals; }
@@ -396,6 +410,17 @@ int launch_tiles_cart(const float4 *p32, const Stats *stats, const CellRows &vro
                       long long n_max, cudaStream_t st) {
     const int tiles = static_cast<int>((n_max + kTile - 1) / kTile);
     k_tiles_cart<<<(tiles + 7) / 8, 256, 0, st>>>(p32, stats, vrow, clo, chi, tiles);
+    count_launches(1);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
+}
+
+int launch_gradient_fd(const int dims[3], const AxisMap &am, const double *n, double *grad, cudaStream_t st) {
+    const long long N = static_cast<long long>(dims[0]) * dims[1] * dims[2];
+    const int bs = 256;
+    long long nb = (N + bs - 1) / bs;
+    if (nb > 1 << 20) nb = 1 << 20;
+    k_gradient_fd<<<static_cast<int>(nb), bs, 0, st>>>(dims[0], dims[1], dims[2], am, n, grad);
     count_launches(1);
     VDWDF_CUDA_TRY(cudaGetLastError());
     return VDWDF_OK;

@@ -117,6 +117,17 @@ def test_host_side_argument_errors(native):
                                 None) == -1
     vox = (ctypes.c_double * 9)(*([0.3] * 9))
     assert lib.vdwdf_phi0_eval(None, vox, 1, ctypes.c_void_p(8), ctypes.c_void_p(8), None) == -6
+    # gradient kind: only finite differences (0) and spectral (1); spectral axes up to 12800
+    g.gradient = 2
+    assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1), 0, None,
+                            ctypes.byref(res), None) == -1
+    g.gradient = 1
+    g.n[2] = 12801
+    assert lib.vdwdf_gradient(ctypes.byref(g), ctypes.c_void_p(8), ctypes.c_void_p(8), None) == -2
+    g.n[2] = 8
+    assert lib.vdwdf_gradient(ctypes.byref(g), None, ctypes.c_void_p(8), None) == -1
+    assert lib.vdwdf_gradient(ctypes.byref(g), ctypes.c_void_p(8), None, None) == -1
+    g.gradient = 0
     # no-allocation energy: a grid larger than its static scratch holds is refused
     g.cell[0][1] = 0.0
     g.n[0], g.n[1], g.n[2] = 64, 64, 17
