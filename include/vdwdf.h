@@ -140,7 +140,7 @@ typedef struct {
 /* Optional launch shape of the pair kernel (NULL = defaults / tuned). */
 typedef struct {
     int32_t threads;      /* threads per CTA: 256, 384, 512 or 1024 (0 = default 512) */
-    int32_t items_per_sm; /* target work items per SM for load balance (0 = default) */
+    int32_t items_per_sm; /* target work items per warp slot for load balance (0 = 256) */
     int32_t smem_rows;    /* FP32 path: table rows resident in shared memory
                              (0 = as many as fit, -1 = none)                          */
     int32_t smem_row0;    /* FP32 path: first resident table row (-1 = chosen on the

@@ -494,8 +494,10 @@ void fill_shared(const vdwdf_table *t, const double *d64, const float *d32, cons
     sh.item_cap = 0;
 }
 
+// n_active: active points of one instance (the mean over a batch of ninst
+// instances, whose items share the queue: the item target is split among them).
 Launch choose_launch(int precision, bool pot, const vdwdf_tuning *tu, const vdwdf_table *t,
-                     long long n_active, bool skew) {
+                     long long n_active, bool skew, int ninst = 1) {
     Launch ln;
     const int S = t->nd + 2;
     if (!skew && tu && (tu->threads == 256 || tu->threads == 384 || tu->threads == 512 || tu->threads == 1024))
@@ -504,9 +506,9 @@ Launch choose_launch(int precision, bool pot, const vdwdf_tuning *tu, const vdwd
     ln.nctas = sms * ctas_per_sm(precision, pot, ln.threads, 0, S);
     // work items are (tile of kTile i points) x (jt j tiles); aim at ipsm items per
     // warp slot so that the dynamic queue balances uneven (culled) items
-    int ipsm = (tu && tu->items_per_sm > 0) ? tu->items_per_sm : 64;
+    int ipsm = (tu && tu->items_per_sm > 0) ? tu->items_per_sm : 256;
     const long long nT = std::max<long long>(1, (n_active + kTile - 1) / kTile);
-    const long long want = static_cast<long long>(ipsm) * sms * (ln.threads / 32);
+    const long long want = std::max<long long>(1, static_cast<long long>(ipsm) * sms * (ln.threads / 32) / std::max(1, ninst));
     long long C = std::max<long long>(1, (want + nT - 1) / nT);
     C = std::min<long long>(C, nT);
     ln.jt = static_cast<int>(std::max<long long>(1, (nT + C - 1) / C));
@@ -721,7 +723,7 @@ int record_batch(BatchPlan &bp, int ninst, const double *const *n_dev, double n_
         for (int k = k0; k < k1; ++k) gsum += bp.geo[k].N;
         bool gskew = false;
         for (int k = k0; k < k1; ++k) gskew = gskew || bp.geo[k].skew;
-        Launch ln = choose_launch(precision, false, tu, table, std::max<long long>(1, gsum / (k1 - k0)), gskew);
+        Launch ln = choose_launch(precision, false, tu, table, std::max<long long>(1, gsum / (k1 - k0)), gskew, k1 - k0);
         VDWDF_CUDA_TRY(cudaMemsetAsync(bp.queues + g, 0, sizeof(unsigned int), st));
         PairLaunch pl;
         std::memset(&pl, 0, sizeof(pl));
@@ -1304,7 +1306,8 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
                 gsum += geo[k].N;
                 gskew = gskew || geo[k].skew;
             }
-            const Launch ln = choose_launch(precision, false, tuning, table, std::max<long long>(1, gsum / (k1 - k0)), gskew);
+            const Launch ln = choose_launch(precision, false, tuning, table, std::max<long long>(1, gsum / (k1 - k0)), gskew,
+                                            k1 - k0);
             long long items = 0;
             for (int k = k0; k < k1; ++k) items += pair_items(geo[k].N, ln.jt);
             double *b = nullptr;
