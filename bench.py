@@ -251,7 +251,8 @@ def run_gpu(args):
                       "seconds": fp64_s},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T fp32-lane-ops/s",
                      "frac": achieved / peak, "traffic": prof_traffic,
-                     "kernel": "k_pair<float, potential, 512>", "ms_per_launch": pms,
+                     "kernel": "k_pair<float, potential, %d>" % results[-1][1]["pair_threads"],
+                     "ms_per_launch": pms,
                      "ops_per_pair": OPS_PER_PAIR_EV,
                      "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (max SM clock)" % (sms, FP32_LANES_PER_SM, clk)},
         "semilocal": {"ms_per_call": semi_t, "points": int(n.numel()),

@@ -135,11 +135,14 @@ typedef struct {
     int32_t smem_row0;       /* FP32 pair kernel: first table row held in shared
                                 memory (given, or chosen from the call's pairs);
                                 -1 on the FP64 path                                */
+    int32_t pair_threads;    /* the pair kernel's threads per CTA (0: not launched) */
 } vdwdf_result;
 
 /* Optional launch shape of the pair kernel (NULL = defaults / tuned). */
 typedef struct {
-    int32_t threads;      /* threads per CTA: 256, 384, 512 or 1024 (0 = default 512) */
+    int32_t threads;      /* threads per CTA: 256, 384, 512 or 1024 (0 = default: 384
+                             for FP32 E + v on orthogonal cells with a periodic axis,
+                             512 otherwise; skewed cells always 512)                 */
     int32_t items_per_sm; /* target work items per warp slot for load balance (0 = 256) */
     int32_t smem_rows;    /* FP32 path: table rows resident in shared memory
                              (0 = as many as fit, -1 = none)                          */

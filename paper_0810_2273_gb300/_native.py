@@ -28,7 +28,8 @@ class vdwdf_result(ctypes.Structure):
     _fields_ = [("E", _c_d), ("E_diag", _c_d), ("n_active", _c_i64), ("pairs", _c_i64),
                 ("pairs_evaluated", _c_i64), ("n_clamped", _c_i64), ("q0_min", _c_d),
                 ("q0_max", _c_d), ("ms_prep", ctypes.c_float), ("ms_pairs", ctypes.c_float),
-                ("ms_post", ctypes.c_float), ("launches", _c_i32), ("smem_row0", _c_i32)]
+                ("ms_post", ctypes.c_float), ("launches", _c_i32), ("smem_row0", _c_i32),
+                ("pair_threads", _c_i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
