@@ -140,9 +140,9 @@ typedef struct {
 
 /* Optional launch shape of the pair kernel (NULL = defaults / tuned). */
 typedef struct {
-    int32_t threads;      /* threads per CTA: 256, 384, 512 or 1024 (0 = default: 384
-                             for FP32 E + v on orthogonal cells with a periodic axis,
-                             512 otherwise; skewed cells always 512)                 */
+    int32_t threads;      /* threads per CTA: 256, 384, 448, 512 or 1024 (0 = default:
+                             FP32 E + v 448, or 384 on skewed cells; 512 otherwise);
+                             skewed cells take 384, 448 or 512                       */
     int32_t items_per_sm; /* target work items per warp slot for load balance (0 = 256) */
     int32_t smem_rows;    /* FP32 path: table rows resident in shared memory
                              (0 = as many as fit, -1 = none)                          */
@@ -389,7 +389,10 @@ int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const doub
                          vdwdf_result *out, void *cuda_stream);
 
 /* Time candidate launch shapes of the pair kernel on this problem (energy
- * path, a sample of the work) and write the fastest to *best. */
+ * path, a sample of the work) and write the fastest to *best.  The shape
+ * suits vdwdf_energy and the batched path; vdwdf_potential's default shape
+ * (448 threads, 384 on skewed cells) was the fastest for the potential pass
+ * on every workload measured. */
 int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, double r_cut,
                    const vdwdf_table *table, int precision, vdwdf_tuning *best,
                    void *cuda_stream);

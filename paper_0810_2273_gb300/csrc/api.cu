@@ -496,18 +496,19 @@ void fill_shared(const vdwdf_table *t, const double *d64, const float *d32, cons
 
 // n_active: active points of one instance (the mean over a batch of ninst
 // instances, whose items share the queue: the item target is split among them).
-// periodic: some axis is periodic, so a j point usually has several images.
 Launch choose_launch(int precision, bool pot, const vdwdf_tuning *tu, const vdwdf_table *t,
-                     long long n_active, bool skew, int ninst = 1, bool periodic = false) {
+                     long long n_active, bool skew, int ninst = 1) {
     Launch ln;
     const int S = t->nd + 2;
-    if (!skew && tu && (tu->threads == 256 || tu->threads == 384 || tu->threads == 512 || tu->threads == 1024))
-        ln.threads = tu->threads;  // skewed cells: the 512-thread kernel only
-    // Default shape: 512 threads, except FP32 E + v on orthogonal periodic cells.  There
-    // several images per j point make the image loop long, and 384 threads (170
-    // registers each) ran it 2 % faster; with one image per j point (open cells)
-    // or in energy mode the extra warps of 512 threads win.
-    if (!skew && (!tu || tu->threads == 0) && pot && periodic && precision == VDWDF_FP32) ln.threads = 384;
+    // Default shape: 512 threads, and for FP32 E + v 448 (384 on skewed cells).  The
+    // potential pass holds more live values: with 146 registers a thread it ran
+    // 1-2 % faster than with 128 (512 threads) or with fewer warps (384); the
+    // skewed instance, with its cross terms, was fastest at 384 and 8 % slower at
+    // 448.  Energy mode needs fewer registers and gains from the extra warps.
+    if (pot && precision == VDWDF_FP32) ln.threads = skew ? 384 : 448;
+    if (tu && (tu->threads == 384 || tu->threads == 448 || tu->threads == 512 ||
+               (!skew && (tu->threads == 256 || tu->threads == 1024))))
+        ln.threads = tu->threads;  // skewed cells: the 384-, 448- and 512-thread kernels only
     const int sms = sm_count();
     ln.nctas = sms * ctas_per_sm(precision, pot, ln.threads, 0, S);
     // work items are (tile of kTile i points) x (jt j tiles); aim at ipsm items per
@@ -621,8 +622,7 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
             VDWDF_CUDA_TRY(cudaMemsetAsync(w.U, 0, sizeof(double) * G.N, st));
         }
         if (hs.n_active > 0) {
-            Launch ln = choose_launch(precision, pot, tu, table, hs.n_active, G.skew, 1,
-                                      G.per[0] || G.per[1] || G.per[2]);
+            Launch ln = choose_launch(precision, pot, tu, table, hs.n_active, G.skew);
             VDWDF_CUDA_TRY(cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st));
             PairLaunch pl;
             std::memset(&pl, 0, sizeof(pl));
@@ -1422,11 +1422,11 @@ int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, do
     if (rc == VDWDF_OK && cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         rc = VDWDF_ECUDA;
     if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
-    constexpr int kCand = 7;
-    vdwdf_tuning cand[kCand] = {{256, 24, 0, -1}, {384, 24, 0, -1}, {512, 24, 0, -1}, {1024, 24, 0, -1},
-                                {512, 8, 0, -1},  {512, 64, 0, -1}, {512, 24, -1, 0}};
+    constexpr int kCand = 8;
+    vdwdf_tuning cand[kCand] = {{256, 256, 0, -1}, {384, 256, 0, -1}, {448, 256, 0, -1}, {512, 256, 0, -1},
+                                {1024, 256, 0, -1}, {512, 64, 0, -1}, {512, 1024, 0, -1}, {512, 256, -1, 0}};
     double best_rate = -1.0;
-    vdwdf_tuning choice = {512, 24, 0, -1};
+    vdwdf_tuning choice = {512, 256, 0, -1};
     Timer tm;
     for (int ci = 0; ci < kCand && rc == VDWDF_OK && hs.n_active > 0; ++ci) {
         if (fp64 && cand[ci].smem_rows != 0) continue;

@@ -1171,10 +1171,15 @@ int launch_one(const PairLaunch &pl, int nctas, size_t smem, cudaStream_t st) {
 // chosen for 512 threads when any instance is skewed).
 template <typename R, int MODE>
 int launch_nt(int threads, bool skew, const PairLaunch &pl, int nctas, size_t smem, cudaStream_t st) {
-    if (skew) return launch_one<R, MODE, 512, true>(pl, nctas, smem, st);
+    if (skew) {
+        if (threads == 448) return launch_one<R, MODE, 448, true>(pl, nctas, smem, st);
+        return threads == 384 ? launch_one<R, MODE, 384, true>(pl, nctas, smem, st)
+                              : launch_one<R, MODE, 512, true>(pl, nctas, smem, st);
+    }
     switch (threads) {
         case 256: return launch_one<R, MODE, 256, false>(pl, nctas, smem, st);
         case 384: return launch_one<R, MODE, 384, false>(pl, nctas, smem, st);
+        case 448: return launch_one<R, MODE, 448, false>(pl, nctas, smem, st);
         case 1024: return launch_one<R, MODE, 1024, false>(pl, nctas, smem, st);
         default: return launch_one<R, MODE, 512, false>(pl, nctas, smem, st);
     }
@@ -1193,7 +1198,7 @@ int pair_smem_bytes(int precision, int threads, int ksn, int S) {
 
 int launch_pair(int precision, bool potential, bool skew, int threads, const PairLaunch &pl, int nctas,
                 cudaStream_t st) {
-    if (skew && threads != 512) return VDWDF_EINVAL;  // the caller chooses 512 for skewed cells
+    if (skew && threads != 512 && threads != 448 && threads != 384) return VDWDF_EINVAL;  // skewed: 384, 448, 512
     const size_t smem = static_cast<size_t>(pair_smem_bytes(precision, threads, pl.sh.ksn, pl.sh.S));
     if (precision == VDWDF_FP64)
         return potential ? launch_nt<double, 1>(threads, skew, pl, nctas, smem, st)
