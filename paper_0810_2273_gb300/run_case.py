@@ -1,7 +1,8 @@
 """Run one standard workload through the library and print per-call timings.
 
     python -m paper_0810_2273_gb300.run_case --workload xe_monolayer \
-        [--dims 24 42 60] [--mode potential|energy] [--precision fp32|fp64] [--repeat 3]
+        [--dims 24 42 60] [--mode potential|energy|semilocal|diag|gradient]
+        [--precision fp32|fp64] [--gradient fd|spectral] [--repeat 3]
 
 Workloads are the seeded densities of ``paper_0810_2273_gb300.inputs``
 (kr_dimer, xe_monolayer, molecule24, slab_adsorbate); --dims regrids the
@@ -18,7 +19,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="xe_monolayer",
                     choices=["kr_dimer", "xe_monolayer", "xe_monolayer_hex", "molecule24", "slab_adsorbate"])
     ap.add_argument("--dims", type=int, nargs=3, default=None)
-    ap.add_argument("--mode", default="potential", choices=["potential", "energy", "semilocal", "diag"])
+    ap.add_argument("--mode", default="potential", choices=["potential", "energy", "semilocal", "diag", "gradient"])
+    ap.add_argument("--gradient", default="fd", choices=["fd", "spectral"], help="the library's density gradient")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--table", default=None)
@@ -44,28 +46,38 @@ def main(argv=None):
     for k in range(a.repeat):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        if a.mode == "gradient":
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g = V.gradient(n, cell, a.gradient)
+            e1.record()
+            torch.cuda.synchronize()
+            print(json.dumps(dict(call=k, ms=e0.elapsed_time(e1), wall_ms=1e3 * (time.perf_counter() - t0),
+                                  workload=a.workload, dims=list(n.shape), mode=a.mode, gradient=a.gradient,
+                                  max_abs=float(g.abs().max()))), flush=True)
+            continue
         if a.mode == "diag":
-            res = V.diag_voxel(n, cell, w["periodic"], w["n_cut"], T)
+            res = V.diag_voxel(n, cell, w["periodic"], w["n_cut"], T, gradient=a.gradient)
             torch.cuda.synchronize()
             res.update(call=k, wall_ms=1e3 * (time.perf_counter() - t0), workload=a.workload,
                        dims=list(n.shape), mode=a.mode)
             print(json.dumps(res), flush=True)
             continue
         if a.mode == "semilocal":
-            res = V.semilocal(n, cell, w["periodic"])
+            res = V.semilocal(n, cell, w["periodic"], gradient=a.gradient)
             torch.cuda.synchronize()
             res.update(call=k, wall_ms=1e3 * (time.perf_counter() - t0), workload=a.workload,
                        dims=list(n.shape), mode=a.mode, points_per_s=n.numel() / max(res["ms"] * 1e-3, 1e-12))
             print(json.dumps(res), flush=True)
             continue
         if a.mode == "potential":
-            E, _, res = V.potential(n, *args, precision=a.precision, tuning=tu)
+            E, _, res = V.potential(n, *args, precision=a.precision, tuning=tu, gradient=a.gradient)
         else:
-            E, res = V.energy(n, *args, precision=a.precision, tuning=tu)
+            E, res = V.energy(n, *args, precision=a.precision, tuning=tu, gradient=a.gradient)
         torch.cuda.synchronize()
         res = dict(res)
         res.update(call=k, E=E, wall_ms=1e3 * (time.perf_counter() - t0), workload=a.workload,
-                   dims=list(n.shape), mode=a.mode, precision=a.precision, tuning=tu,
+                   dims=list(n.shape), mode=a.mode, precision=a.precision, tuning=tu, gradient=a.gradient,
                    pairs_per_s=res["pairs"] / max(res["ms_pairs"] * 1e-3, 1e-12))
         print(json.dumps(res), flush=True)
 
