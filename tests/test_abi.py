@@ -176,3 +176,21 @@ def test_total_energy_assembly():
     assert Er == pytest.approx(E + (-1.12) - (-1.10), abs=1e-15)
     with pytest.raises(ValueError):
         V.total_energy_nl(-50.0, semi, 0.05, exchange="lda")
+
+
+def test_python_grid_and_tuning_marshalling():
+    """grid() carries the gradient kind and _tuning() the four launch fields, as the
+    header defines them; a bad kind is refused before any library call."""
+    from paper_0810_2273_gb300 import grid, _tuning, _native
+    g = grid((10.0, 11.0, 12.0), (8, 9, 10), (True, False, True))
+    assert g.gradient == 0 and list(g.periodic) == [1, 0, 1] and list(g.n) == [8, 9, 10]
+    assert g.cell[0][0] == 10.0 and g.cell[1][1] == 11.0 and g.cell[0][1] == 0.0
+    gs = grid(np.diag([3.0, 4.0, 5.0]), (4, 4, 4), gradient="spectral")
+    assert gs.gradient == 1 and gs.cell[2][2] == 5.0
+    with pytest.raises(ValueError):
+        grid((1.0, 1.0, 1.0), (2, 2, 2), gradient="fft")
+    t = _tuning({"threads": 448, "items_per_sm": 256, "smem_row0": -1})._obj
+    assert (t.threads, t.items_per_sm, t.smem_rows, t.smem_row0) == (448, 256, 0, -1)
+    assert _tuning(None) is None
+    r = _native.vdwdf_result()
+    assert "smem_row0" in r.as_dict() and "pair_threads" in r.as_dict()
