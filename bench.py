@@ -274,10 +274,16 @@ def run_gpu(args):
 
 
 def kernel_hash():
+    """Hash of the pair kernel's code (pair.cu and common.cuh without comments or
+    layout): the recorded DRAM traffic belongs to the code with this hash."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("pair.cu", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_0810_2273_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_0810_2273_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -16,14 +16,17 @@
 // r dphi17/dd1 = -2 phi17 (1/q_i + q_i/(q_i^2 + q_j^2)).
 //
 // Work decomposition: persistent CTAs keep a band of B-spline rows resident in
-// shared memory (FP32 path, staged once).  Each warp then works on its own:
+// shared memory (FP32 path, staged once; which rows is chosen on the device from
+// a sampled histogram of the call's D cells).  Each warp then works on its own:
 // it pulls work items (instance, tile of kTile i points, range of j tiles) from
 // one queue in global memory, culls every (j tile, image) against its i tile
 // by bounding boxes and then every (j point, image) against the i box, stages
 // surviving j tiles in a private shared-memory buffer (warp-synchronous, no
 // block barrier), and runs the pair loop with each lane owning one i, the j
-// points read as broadcasts and the images of a pair innermost.  FP32 partial
-// sums over one j tile are folded into FP64 accumulators.  The work loop is
+// points read as broadcasts and the images of a pair innermost.  In FP32 two j
+// points go through the loop together, one in each half of packed FP32x2
+// arithmetic.  FP32 partial sums over one j tile are folded into FP64
+// accumulators.  The work loop is
 // bounded (max_iters); nothing waits on another warp or CTA.
 #include <cuda_runtime.h>
 
@@ -604,8 +607,10 @@ __device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v
 // each lane marks, for its own j point, which of those images bring the i box
 // within the cutoff of that point.  The pair loop runs over j points (broadcast)
 // and, inside, over the marked images: the delta part of a pair is computed once
-// for all its images, and the j-side sums of the potential are reduced over the
-// warp once per j point.
+// for all its images.  FP32 takes the j points with images two at a time, half x
+// of every packed step on the images of the first and half y on those of the
+// second, and reduces the four j-side sums of the potential over the warp once
+// per such pair (warp_sum4); FP64 takes them one at a time.
 template <typename R, int MODE, int NT, bool SKEW>
 __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaunch pl) {
     constexpr bool POT = (MODE == 1);
