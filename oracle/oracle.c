@@ -41,9 +41,14 @@
  *   orc_gradient_T_cell             invariance of E, exact Fourier symbol of
  *                                   the skewed gradient, adjoint identity,
  *                                   brute-force pair counts
- *   orc_phi0_many                   pinned: large-voxel limit fixed by the
- *                                   kernel's D^3 moment, small-voxel
- *                                   logarithmic limit, Monte Carlo average
+ *   orc_phi0_many                   pinned: small-voxel logarithmic law,
+ *                                   scale duality phi0(s q; v) = phi0(q; s v),
+ *                                   Monte Carlo voxel average, quadrature
+ *                                   convergence
+ *   gradient_spectral(_T)           pinned: band-limited plane-wave sums on
+ *   (numpy, in __init__.py)         orthorhombic and skewed cells, Nyquist
+ *                                   mode, textbook circulant matrix, adjoint
+ *                                   identity, spectral accuracy
  *   paper-level energies            parity unpinned: the paper's Xe density
  *                                   file is not available
  */
