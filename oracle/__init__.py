@@ -39,58 +39,63 @@ _i = ctypes.c_int
 _p = ctypes.c_void_p
 
 
+def load_library(path):
+    """The oracle's C functions from the shared library at ``path``, with their
+    ctypes signatures (tests also load deliberately broken builds this way)."""
+    L = ctypes.CDLL(path)
+    L.orc_grid_size.restype = _i
+    L.orc_grid_size.argtypes = [_d, _d, _i, _i, _i]
+    L.orc_grid.restype = _i
+    L.orc_grid.argtypes = [_d, _d, _i, _i, _i, _p, _p]
+    L.orc_W.restype = _d
+    L.orc_W.argtypes = [_d, _d]
+    L.orc_phi_many.restype = _i
+    L.orc_phi_many.argtypes = [_i, _p, _p, _p, _d, _d, _i, _i, _i]
+    L.orc_phi_table.restype = _i
+    L.orc_phi_table.argtypes = [_i, _d, _i, _p, _d, _d, _i, _i, _i]
+    L.orc_spline_prepare.restype = _i
+    L.orc_spline_prepare.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _p, _p]
+    L.orc_spline_eval_many.restype = _i
+    L.orc_spline_eval_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p]
+    L.orc_kernel_many.restype = _i
+    L.orc_kernel_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p]
+    L.orc_pair_AU.restype = _i
+    L.orc_pair_AU.argtypes = ([_i, _p, _p, _p, _p, _p, _i, _i, _i, _d, _d, _d, _i, _i, _i, _d,
+                               _i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p])
+    L.orc_pair_brute.restype = _i
+    L.orc_pair_brute.argtypes = ([_i, _p, _p, _p, _p, _p, _i, _i, _i, _d, _d, _d, _i, _i, _i,
+                                  _d, _d, _d, _d, _d, _i, _i, _i, _p])
+    L.orc_gradient.restype = _i
+    L.orc_gradient.argtypes = [_i, _i, _i, _d, _d, _d, _p, _p]
+    L.orc_gradient_T.restype = _i
+    L.orc_gradient_T.argtypes = [_i, _i, _i, _d, _d, _d, _p, _p]
+    L.orc_eps_c.restype = _i
+    L.orc_eps_c.argtypes = [_i, _p, _p, _p]
+    L.orc_q0.restype = _i
+    L.orc_q0.argtypes = [_i, _p, _p, _p, _p, _p]
+    L.orc_pair_AU_cell.restype = _i
+    L.orc_pair_AU_cell.argtypes = ([_i, _p, _p, _p, _p, _p, _i, _i, _i, _p, _i, _i, _i, _d,
+                                    _i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p])
+    L.orc_gradient_cell.restype = _i
+    L.orc_gradient_cell.argtypes = [_i, _i, _i, _p, _p, _p]
+    L.orc_gradient_T_cell.restype = _i
+    L.orc_gradient_T_cell.argtypes = [_i, _i, _i, _p, _p, _p]
+    L.orc_phi0_many.restype = _i
+    L.orc_phi0_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _p, _i, _p, _p, _i, _i]
+    L.orc_fx_many.restype = _i
+    L.orc_fx_many.argtypes = [_i, _p, _d, _p]
+    L.orc_pbe_H_many.restype = _i
+    L.orc_pbe_H_many.argtypes = [_i, _p, _p, _p]
+    L.orc_semilocal.restype = _i
+    L.orc_semilocal.argtypes = [_i, _p, _p, _p, _p]
+    return L
+
+
 def lib():
     """Load (building first if needed) the oracle's shared library."""
     global _LIB
     if _LIB is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        L.orc_grid_size.restype = _i
-        L.orc_grid_size.argtypes = [_d, _d, _i, _i, _i]
-        L.orc_grid.restype = _i
-        L.orc_grid.argtypes = [_d, _d, _i, _i, _i, _p, _p]
-        L.orc_W.restype = _d
-        L.orc_W.argtypes = [_d, _d]
-        L.orc_phi_many.restype = _i
-        L.orc_phi_many.argtypes = [_i, _p, _p, _p, _d, _d, _i, _i, _i]
-        L.orc_phi_table.restype = _i
-        L.orc_phi_table.argtypes = [_i, _d, _i, _p, _d, _d, _i, _i, _i]
-        L.orc_spline_prepare.restype = _i
-        L.orc_spline_prepare.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _p, _p]
-        L.orc_spline_eval_many.restype = _i
-        L.orc_spline_eval_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p]
-        L.orc_kernel_many.restype = _i
-        L.orc_kernel_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p]
-        L.orc_pair_AU.restype = _i
-        L.orc_pair_AU.argtypes = ([_i, _p, _p, _p, _p, _p, _i, _i, _i, _d, _d, _d, _i, _i, _i, _d,
-                                   _i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p])
-        L.orc_pair_brute.restype = _i
-        L.orc_pair_brute.argtypes = ([_i, _p, _p, _p, _p, _p, _i, _i, _i, _d, _d, _d, _i, _i, _i,
-                                      _d, _d, _d, _d, _d, _i, _i, _i, _p])
-        L.orc_gradient.restype = _i
-        L.orc_gradient.argtypes = [_i, _i, _i, _d, _d, _d, _p, _p]
-        L.orc_gradient_T.restype = _i
-        L.orc_gradient_T.argtypes = [_i, _i, _i, _d, _d, _d, _p, _p]
-        L.orc_eps_c.restype = _i
-        L.orc_eps_c.argtypes = [_i, _p, _p, _p]
-        L.orc_q0.restype = _i
-        L.orc_q0.argtypes = [_i, _p, _p, _p, _p, _p]
-        L.orc_pair_AU_cell.restype = _i
-        L.orc_pair_AU_cell.argtypes = ([_i, _p, _p, _p, _p, _p, _i, _i, _i, _p, _i, _i, _i, _d,
-                                        _i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p])
-        L.orc_gradient_cell.restype = _i
-        L.orc_gradient_cell.argtypes = [_i, _i, _i, _p, _p, _p]
-        L.orc_gradient_T_cell.restype = _i
-        L.orc_gradient_T_cell.argtypes = [_i, _i, _i, _p, _p, _p]
-        L.orc_phi0_many.restype = _i
-        L.orc_phi0_many.argtypes = [_i, _d, _i, _d, _p, _p, _p, _p, _p, _p, _p, _i, _p, _p, _i, _i]
-        L.orc_fx_many.restype = _i
-        L.orc_fx_many.argtypes = [_i, _p, _d, _p]
-        L.orc_pbe_H_many.restype = _i
-        L.orc_pbe_H_many.argtypes = [_i, _p, _p, _p]
-        L.orc_semilocal.restype = _i
-        L.orc_semilocal.argtypes = [_i, _p, _p, _p, _p]
-        _LIB = L
+        _LIB = load_library(_build.build())
     return _LIB
 
 

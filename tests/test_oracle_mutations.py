@@ -1,0 +1,138 @@
+"""The oracle's pins catch plausible mistakes.  Each case plants one mistake in a
+copy of oracle/oracle.c (a flipped sign, a wrong index, a dropped term or
+factor, a mistyped constant, a shifted boundary), builds it with gcc into a
+temporary library, loads it in place of the oracle's own, and checks that the
+pin meant to guard that part now fails.  The oracle itself is never changed;
+the last cases do the same to the numpy FFT gradient by substituting
+functions for the duration of the test."""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+import test_oracle_cell as CELL
+import test_oracle_kernel as K
+import test_oracle_q0 as Q
+import test_oracle_semilocal as SEMI
+import test_oracle_spectral as SP
+import test_oracle_spline as SPL
+import test_oracle_sum as SUM
+
+ORACLE_C = os.path.join(ROOT, "oracle", "oracle.c")
+
+# (name, text in oracle.c, planted text, occurrence, pin, its further arguments:
+#  a string names a fixture, anything else is passed as it is)
+MUTATIONS = [
+    ("W: sign of the cos a cos b term",
+     "return 2.0 * (sa * ub + sb * ua - 3.0 * ua * ub);",
+     "return 2.0 * (sa * ub + sb * ua + 3.0 * ua * ub);", 0,
+     K.test_W_matches_printed_formula_high_precision, ()),
+    ("T: y + z written y + x",
+     "return 0.5 * (1.0 / (w + x) + 1.0 / (y + z)) *",
+     "return 0.5 * (1.0 / (w + x) + 1.0 / (y + x)) *", 0,
+     K.test_phi_symmetric_in_arguments, ()),
+    ("q0: s instead of s^2 in the gradient term",
+     "double exc0 = ec + ex * (1.0 - (Zab / 9.0) * s * s);",
+     "double exc0 = ec + ex * (1.0 - (Zab / 9.0) * s);", 0,
+     Q.test_q0_hand_values, ()),
+    ("gradient stencil: +-1 neighbours swapped",
+     "static const double orc_fd_c[5] = {1.0 / 12.0, -8.0 / 12.0, 0.0, 8.0 / 12.0, -1.0 / 12.0};",
+     "static const double orc_fd_c[5] = {1.0 / 12.0, 8.0 / 12.0, 0.0, -8.0 / 12.0, -1.0 / 12.0};", 0,
+     Q.test_gradient_fourier_symbol, ()),
+    ("transposed stencil: shifted the wrong way",
+     "jj[ax] = ((idx[ax] - o) % dims[ax] + dims[ax]) % dims[ax];",
+     "jj[ax] = ((idx[ax] + o) % dims[ax] + dims[ax]) % dims[ax];", 0,
+     Q.test_gradient_adjoint_identity, ()),
+    # (beta3, beta4 and alpha1 are fitted to the QMC energies, which resolve about
+    # 0.1 mHa; beta1 is fixed by the exact high-density constant c1)
+    ("PW92: beta1 mistyped 7.5597",
+     "PW_b1 = 7.5957", "PW_b1 = 7.5597", 0,
+     Q.test_lda_correlation_high_density_constant, ()),
+    ("pair sum: self term dropped",
+     "a += n[i] * phi00;", "a += 0.0 * phi00;", 0,
+     SUM.test_self_term_and_prefactor, ("oracle_spline",)),
+    ("pair sum: cutoff made exclusive",
+     "if (rc > 0.0 && r2 > rc * rc * (1.0 + 1e-12)) continue;",
+     "if (rc > 0.0 && r2 >= rc * rc * (1.0 - 1e-12)) continue;", 0,
+     SUM.test_periodic_cutoff_counts, ("oracle_spline",)),
+    ("spline: end condition row 2 M0 + M1 written 4 M0 + M1",
+     "sub = 0.0; diag = 2.0; sup = 1.0;", "sub = 0.0; diag = 4.0; sup = 1.0;", 0,
+     SPL.test_spline_exact_on_cubics_meeting_boundary_conditions, ()),
+    ("adjoint: the n_i factor of U dropped",
+     "U[t] = n[i] * u;", "U[t] = u;", 0,
+     SUM.test_potential_is_derivative_of_energy, ("oracle_spline", (0, 0, 0))),
+    ("kernel: d delta/d d1 with (1 + ds) for (1 - ds)",
+     "*rdphi1 = r * (0.5 * pD + (1.0 - ds) / (2.0 * D) * sgn * pd);",
+     "*rdphi1 = r * (0.5 * pD + (1.0 + ds) / (2.0 * D) * sgn * pd);", 0,
+     SPL.test_kernel_branches, ("oracle_spline",)),
+    ("general-cell gradient: reciprocal matrix transposed",
+     "for (int k = 0; k < 3; ++k) g[k * N + m] = du[0] * B[k] + du[1] * B[3 + k] + du[2] * B[6 + k];",
+     "for (int k = 0; k < 3; ++k) g[k * N + m] = du[0] * B[3 * k] + du[1] * B[3 * k + 1] + du[2] * B[3 * k + 2];",
+     0, CELL.test_gradient_cell_fourier_symbol, ((1, 2, 1),)),
+    ("GGA exchange: mu s instead of mu s^2",
+     "return 1.0 + kappa - kappa / (1.0 + pbe_mu() * s * s / kappa);",
+     "return 1.0 + kappa - kappa / (1.0 + pbe_mu() * s / kappa);", 0,
+     SEMI.test_enhancement_factor_limits, (0.804,)),
+]
+
+
+def _build_mutant(tmp_path, old, new, which):
+    src = open(ORACLE_C).read()
+    at = -1
+    for _ in range(which + 1):
+        at = src.index(old, at + 1)
+    mutated = src[:at] + new + src[at + len(old):]
+    c = os.path.join(tmp_path, "oracle_mutant.c")
+    so = os.path.join(tmp_path, "liboracle_mutant.so")
+    open(c, "w").write(mutated)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+                    "-o", so, c, "-lm"], check=True)
+    return so
+
+
+@pytest.mark.parametrize("case", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pin_catches_planted_mistake(oracle_mod, request, tmp_path, case):
+    name, old, new, which, pin, extra = case
+    so = _build_mutant(str(tmp_path), old, new, which)
+    fixtures = [request.getfixturevalue(f) if isinstance(f, str) else f for f in extra]
+    real = oracle_mod.lib()
+    # the pin passes on the oracle as it is ...
+    pin(oracle_mod, *fixtures)
+    # ... and fails with the mistake planted
+    oracle_mod._LIB = oracle_mod.load_library(so)
+    try:
+        with pytest.raises(AssertionError):
+            pin(oracle_mod, *fixtures)
+    finally:
+        oracle_mod._LIB = real
+
+
+def _mutated_function(module, name, old, new):
+    """module.name rebuilt from its own source with ``old`` replaced by ``new``."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(getattr(module, name)))
+    assert src.count(old) == 1, (name, old)
+    ns = dict(module.__dict__)
+    exec(compile(src.replace(old, new), "<mutant %s>" % name, "exec"), ns)
+    return ns[name]
+
+
+def test_spectral_pins_catch_planted_mistakes(oracle_mod, monkeypatch):
+    """The FFT gradient: frequencies 0..N-1 without aliasing the upper half to
+    negative ones, and the transpose without its conjugate multipliers."""
+    SP.test_plane_waves_exact(oracle_mod, (12, 10, 14), False)
+    SP.test_adjoint_identity(oracle_mod, True)
+    bad = _mutated_function(oracle_mod, "_spectral_multipliers", "m = np.fft.fftfreq(N, 1.0 / N)",
+                            "m = np.arange(N, dtype=np.float64)")
+    monkeypatch.setattr(oracle_mod, "_spectral_multipliers", bad)
+    with pytest.raises(AssertionError):
+        SP.test_plane_waves_exact(oracle_mod, (12, 10, 14), False)
+    monkeypatch.undo()
+    bad = _mutated_function(oracle_mod, "gradient_spectral_T", "np.conj(mult[a])", "mult[a]")
+    monkeypatch.setattr(oracle_mod, "gradient_spectral_T", bad)
+    with pytest.raises(AssertionError):
+        SP.test_adjoint_identity(oracle_mod, True)

@@ -10,7 +10,7 @@ def _rs(n):
 
 
 def test_lda_correlation_against_uniform_gas_energies(oracle_mod):
-    rows = [r for r in read_golden("lda_correlation.txt") if len(r) == 2 and r[0] != "c0"]
+    rows = [r for r in read_golden("lda_correlation.txt") if len(r) == 2 and r[0][0].isdigit()]
     rs = np.array([float(r[0]) for r in rows])
     ref = np.array([float(r[1]) for r in rows])
     e, _ = oracle_mod.eps_c(rs)
@@ -24,6 +24,15 @@ def test_lda_correlation_high_density_limit(oracle_mod):
     assert abs(slope - c0) < 2e-5 * c0
 
 
+def test_lda_correlation_high_density_constant(oracle_mod):
+    """eps_c - c0 ln rs -> -c1 as rs -> 0, with the slope c0 measured between
+    rs = 1e-11 and 1e-10 (where the next terms are ~1e-7)."""
+    g = golden_dict("lda_correlation.txt")
+    e, _ = oracle_mod.eps_c(np.array([1e-10, 1e-11]))
+    slope = (e[0] - e[1]) / np.log(10.0)
+    assert abs((e[0] - slope * np.log(1e-10)) + g["c1"]) < 2e-6
+
+
 def test_lda_correlation_derivative(oracle_mod):
     rs = np.array([0.3, 1.0, 4.0, 30.0, 300.0])
     h = 1e-6 * rs
@@ -35,16 +44,20 @@ def test_lda_correlation_derivative(oracle_mod):
 
 def test_q0_hand_values(oracle_mod):
     """n = 1/(3 pi^2) gives k_F = 1: without gradient q0 = 1 - (4 pi/3) eps_c; with
-    |grad n| = 2 n (s = 1) the gradient term adds -(Zab/9) k_F s^2 = 0.8491 / 9."""
+    |grad n| = 2 s n the gradient term adds -(Zab/9) k_F s^2 = 0.8491 s^2 / 9
+    (s = 1, 2 and 1/2, so that the power of s shows)."""
     g = golden_dict("dion_kernel.txt")
     n0 = 1.0 / (3.0 * np.pi ** 2)
-    n = np.full((1, 1, 2), n0)
-    grad = np.zeros((3, 1, 1, 2))
-    grad[1, 0, 0, 1] = 2.0 * n0
+    svals = (1.0, 2.0, 0.5)
+    n = np.full((1, 1, 1 + len(svals)), n0)
+    grad = np.zeros((3, 1, 1, 1 + len(svals)))
+    for k, sv in enumerate(svals):
+        grad[(k % 3), 0, 0, 1 + k] = 2.0 * sv * n0
     q, _, _ = oracle_mod.q0(n, grad)
     ec, _ = oracle_mod.eps_c(np.array([_rs(n0)]))
     assert abs(q[0, 0, 0] - (1.0 - 4.0 * np.pi / 3.0 * ec[0])) < 1e-14
-    assert abs((q[0, 0, 1] - q[0, 0, 0]) - (-g["Zab"] / 9.0)) < 1e-14
+    for k, sv in enumerate(svals):
+        assert abs((q[0, 0, 1 + k] - q[0, 0, 0]) - (-g["Zab"] / 9.0) * sv ** 2) < 1e-14
 
 
 def test_q0_partials_against_finite_differences(oracle_mod):
