@@ -15,6 +15,7 @@ from conftest import ROOT
 
 import test_oracle_cell as CELL
 import test_oracle_kernel as K
+import test_oracle_phi0 as PHI0
 import test_oracle_q0 as Q
 import test_oracle_semilocal as SEMI
 import test_oracle_spectral as SP
@@ -23,59 +24,73 @@ import test_oracle_sum as SUM
 
 ORACLE_C = os.path.join(ROOT, "oracle", "oracle.c")
 
-# (name, text in oracle.c, planted text, occurrence, pin, its further arguments:
-#  a string names a fixture, anything else is passed as it is)
+# (name, text in oracle.c, planted text, occurrence, pin, its arguments: a
+#  string names a fixture, anything else is passed as it is)
 MUTATIONS = [
     ("W: sign of the cos a cos b term",
      "return 2.0 * (sa * ub + sb * ua - 3.0 * ua * ub);",
      "return 2.0 * (sa * ub + sb * ua + 3.0 * ua * ub);", 0,
-     K.test_W_matches_printed_formula_high_precision, ()),
+     K.test_W_matches_printed_formula_high_precision, ("oracle_mod",)),
     ("T: y + z written y + x",
      "return 0.5 * (1.0 / (w + x) + 1.0 / (y + z)) *",
      "return 0.5 * (1.0 / (w + x) + 1.0 / (y + x)) *", 0,
-     K.test_phi_symmetric_in_arguments, ()),
+     K.test_phi_symmetric_in_arguments, ("oracle_mod",)),
     ("q0: s instead of s^2 in the gradient term",
      "double exc0 = ec + ex * (1.0 - (Zab / 9.0) * s * s);",
      "double exc0 = ec + ex * (1.0 - (Zab / 9.0) * s);", 0,
-     Q.test_q0_hand_values, ()),
+     Q.test_q0_hand_values, ("oracle_mod",)),
     ("gradient stencil: +-1 neighbours swapped",
      "static const double orc_fd_c[5] = {1.0 / 12.0, -8.0 / 12.0, 0.0, 8.0 / 12.0, -1.0 / 12.0};",
      "static const double orc_fd_c[5] = {1.0 / 12.0, 8.0 / 12.0, 0.0, -8.0 / 12.0, -1.0 / 12.0};", 0,
-     Q.test_gradient_fourier_symbol, ()),
+     Q.test_gradient_fourier_symbol, ("oracle_mod",)),
     ("transposed stencil: shifted the wrong way",
      "jj[ax] = ((idx[ax] - o) % dims[ax] + dims[ax]) % dims[ax];",
      "jj[ax] = ((idx[ax] + o) % dims[ax] + dims[ax]) % dims[ax];", 0,
-     Q.test_gradient_adjoint_identity, ()),
+     Q.test_gradient_adjoint_identity, ("oracle_mod",)),
     # (beta3, beta4 and alpha1 are fitted to the QMC energies, which resolve about
     # 0.1 mHa; beta1 is fixed by the exact high-density constant c1)
     ("PW92: beta1 mistyped 7.5597",
      "PW_b1 = 7.5957", "PW_b1 = 7.5597", 0,
-     Q.test_lda_correlation_high_density_constant, ()),
+     Q.test_lda_correlation_high_density_constant, ("oracle_mod",)),
     ("pair sum: self term dropped",
      "a += n[i] * phi00;", "a += 0.0 * phi00;", 0,
-     SUM.test_self_term_and_prefactor, ("oracle_spline",)),
+     SUM.test_self_term_and_prefactor, ("oracle_mod", "oracle_spline")),
     ("pair sum: cutoff made exclusive",
      "if (rc > 0.0 && r2 > rc * rc * (1.0 + 1e-12)) continue;",
      "if (rc > 0.0 && r2 >= rc * rc * (1.0 - 1e-12)) continue;", 0,
-     SUM.test_periodic_cutoff_counts, ("oracle_spline",)),
+     SUM.test_periodic_cutoff_counts, ("oracle_mod", "oracle_spline")),
     ("spline: end condition row 2 M0 + M1 written 4 M0 + M1",
      "sub = 0.0; diag = 2.0; sup = 1.0;", "sub = 0.0; diag = 4.0; sup = 1.0;", 0,
-     SPL.test_spline_exact_on_cubics_meeting_boundary_conditions, ()),
+     SPL.test_spline_exact_on_cubics_meeting_boundary_conditions, ("oracle_mod",)),
     ("adjoint: the n_i factor of U dropped",
      "U[t] = n[i] * u;", "U[t] = u;", 0,
-     SUM.test_potential_is_derivative_of_energy, ("oracle_spline", (0, 0, 0))),
+     SUM.test_potential_is_derivative_of_energy, ("oracle_mod", "oracle_spline", (0, 0, 0))),
     ("kernel: d delta/d d1 with (1 + ds) for (1 - ds)",
      "*rdphi1 = r * (0.5 * pD + (1.0 - ds) / (2.0 * D) * sgn * pd);",
      "*rdphi1 = r * (0.5 * pD + (1.0 + ds) / (2.0 * D) * sgn * pd);", 0,
-     SPL.test_kernel_branches, ("oracle_spline",)),
+     SPL.test_kernel_branches, ("oracle_mod", "oracle_spline")),
     ("general-cell gradient: reciprocal matrix transposed",
      "for (int k = 0; k < 3; ++k) g[k * N + m] = du[0] * B[k] + du[1] * B[3 + k] + du[2] * B[6 + k];",
      "for (int k = 0; k < 3; ++k) g[k * N + m] = du[0] * B[3 * k] + du[1] * B[3 * k + 1] + du[2] * B[3 * k + 2];",
-     0, CELL.test_gradient_cell_fourier_symbol, ((1, 2, 1),)),
+     0, CELL.test_gradient_cell_fourier_symbol, ("oracle_mod", (1, 2, 1))),
     ("GGA exchange: mu s instead of mu s^2",
      "return 1.0 + kappa - kappa / (1.0 + pbe_mu() * s * s / kappa);",
      "return 1.0 + kappa - kappa / (1.0 + pbe_mu() * s / kappa);", 0,
-     SEMI.test_enhancement_factor_limits, (0.804,)),
+     SEMI.test_enhancement_factor_limits, ("oracle_mod", 0.804)),
+    ("kernel: gamma of h(y) = 1 - exp(-gamma y^2) as 4 pi/3",
+     "const double gam = 4.0 * M_PI / 9.0;", "const double gam = 4.0 * M_PI / 3.0;", 0,
+     K.test_phi_large_D_asymptote, ("oracle_mod", 0.0)),
+    ("voxel diagonal: one tent factor (1 - |t|) dropped",
+     "double wt = w[i] * w[j] * w[k] * (1.0 - x[i]) * (1.0 - x[j]) * (1.0 - x[k]);",
+     "double wt = w[i] * w[j] * w[k] * (1.0 - x[i]) * (1.0 - x[j]);", 0,
+     PHI0.test_monte_carlo_voxel_average, ("oracle_spline", 2.0)),
+    ("general-cell pair sum: image shift with the transposed cell",
+     "d[c] = ri[c] - rj[c] + m0 * cell[c] + m1 * cell[3 + c] + m2 * cell[6 + c];",
+     "d[c] = ri[c] - rj[c] + m0 * cell[3 * c] + m1 * cell[3 * c + 1] + m2 * cell[3 * c + 2];", 0,
+     CELL.test_skewed_pair_counts_brute_force, ("oracle_mod", "oracle_spline")),
+    ("PBE correlation: A^2 t^4 written A t^4",
+     "double den = 1.0 + A * t2 + A * A * t2 * t2;", "double den = 1.0 + A * t2 + A * t2 * t2;", 0,
+     SEMI.test_pbe_gradient_correction_limits, ("oracle_mod",)),
 ]
 
 
@@ -95,17 +110,17 @@ def _build_mutant(tmp_path, old, new, which):
 
 @pytest.mark.parametrize("case", MUTATIONS, ids=[m[0] for m in MUTATIONS])
 def test_pin_catches_planted_mistake(oracle_mod, request, tmp_path, case):
-    name, old, new, which, pin, extra = case
+    name, old, new, which, pin, spec = case
     so = _build_mutant(str(tmp_path), old, new, which)
-    fixtures = [request.getfixturevalue(f) if isinstance(f, str) else f for f in extra]
+    args = [request.getfixturevalue(f) if isinstance(f, str) else f for f in spec]
     real = oracle_mod.lib()
     # the pin passes on the oracle as it is ...
-    pin(oracle_mod, *fixtures)
+    pin(*args)
     # ... and fails with the mistake planted
     oracle_mod._LIB = oracle_mod.load_library(so)
     try:
         with pytest.raises(AssertionError):
-            pin(oracle_mod, *fixtures)
+            pin(*args)
     finally:
         oracle_mod._LIB = real
 
