@@ -136,6 +136,39 @@ def _mutated_function(module, name, old, new):
     return ns[name]
 
 
+def _mutated_method(cls, name, old, new, module):
+    """cls.name rebuilt from its own source with ``old`` replaced by ``new``."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(getattr(cls, name)))
+    assert src.count(old) == 1, (name, old)
+    ns = dict(module.__dict__)
+    exec(compile(src.replace(old, new), "<mutant %s.%s>" % (cls.__name__, name), "exec"), ns)
+    return ns[name]
+
+
+PY_MUTATIONS = [
+    ("E: dV instead of dV^2", "energy", "E = 0.5 * self.dV ** 2 * float(np.dot(self.na, A))",
+     "E = 0.5 * self.dV * float(np.dot(self.na, A))", SUM.test_self_term_and_prefactor,
+     ("oracle_mod", "oracle_spline")),
+    ("v: divergence term added with the wrong sign", "potential",
+     "v = self.dV * (chi * (Ag + Ug * self.dq0dn.ravel()) + div)",
+     "v = self.dV * (chi * (Ag + Ug * self.dq0dn.ravel()) - div)", SUM.test_potential_is_derivative_of_energy,
+     ("oracle_mod", "oracle_spline", (0, 0, 0))),
+]
+
+
+@pytest.mark.parametrize("case", PY_MUTATIONS, ids=[m[0] for m in PY_MUTATIONS])
+def test_pin_catches_planted_mistake_in_assembly(oracle_mod, request, monkeypatch, case):
+    """The same for the grid-level assembly that the oracle does in Python."""
+    name, method, old, new, pin, spec = case
+    args = [request.getfixturevalue(f) if isinstance(f, str) else f for f in spec]
+    pin(*args)
+    monkeypatch.setattr(oracle_mod.Problem, method, _mutated_method(oracle_mod.Problem, method, old, new, oracle_mod))
+    with pytest.raises(AssertionError):
+        pin(*args)
+
+
 def test_spectral_pins_catch_planted_mistakes(oracle_mod, monkeypatch):
     """The FFT gradient: frequencies 0..N-1 without aliasing the upper half to
     negative ones, and the transpose without its conjugate multipliers."""
