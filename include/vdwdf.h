@@ -12,7 +12,8 @@
  * variables D and delta (section 2) and its large-D asymptote (Dion eq. 17).
  * q0 follows Dion eqs. 11-12 (LDA correlation plus gradient-corrected
  * exchange, Zab = -0.8491) from n and |grad n|, with grad n by 4th-order
- * central finite differences along the (orthogonal) axes (section 3).
+ * central finite differences along the grid axes or by FFT, the two options of
+ * section 3 (vdwdf_grid.gradient), or given by the caller.
  *
  * Units: Hartree atomic units (bohr, Hartree) at the boundary, FP64.
  *
