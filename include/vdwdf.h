@@ -139,7 +139,9 @@ typedef struct {
     int32_t pair_threads;    /* the pair kernel's threads per CTA (0: not launched) */
 } vdwdf_result;
 
-/* Optional launch shape of the pair kernel (NULL = defaults / tuned). */
+/* Optional launch shape of the pair kernel (NULL = defaults / tuned).  Values
+ * outside those listed are VDWDF_EINVAL; 256 or 1024 threads on a skewed cell
+ * are VDWDF_EUNSUPPORTED (both before any device work). */
 typedef struct {
     int32_t threads;      /* threads per CTA: 256, 384, 448, 512 or 1024 (0 = default:
                              FP32 E + v 448, or 384 on skewed cells; 512 otherwise);

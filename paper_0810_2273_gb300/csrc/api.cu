@@ -494,6 +494,17 @@ void fill_shared(const vdwdf_table *t, const double *d64, const float *d32, cons
     sh.item_cap = 0;
 }
 
+// A caller's launch shape: VDWDF_EINVAL outside the documented values,
+// VDWDF_EUNSUPPORTED for a thread count the skewed kernel is not built for.
+int check_tuning(const vdwdf_tuning *tu, bool skew) {
+    if (!tu) return VDWDF_OK;
+    const int t = tu->threads;
+    if (t != 0 && t != 256 && t != 384 && t != 448 && t != 512 && t != 1024) return VDWDF_EINVAL;
+    if (tu->items_per_sm < 0 || tu->smem_rows < -1 || tu->smem_row0 < -1) return VDWDF_EINVAL;
+    if (skew && (t == 256 || t == 1024)) return VDWDF_EUNSUPPORTED;
+    return VDWDF_OK;
+}
+
 // n_active: active points of one instance (the mean over a batch of ninst
 // instances, whose items share the queue: the item target is split among them).
 Launch choose_launch(int precision, bool pot, const vdwdf_tuning *tu, const vdwdf_table *t,
@@ -589,6 +600,8 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
     if (pot && !v_dev && !A_grid && !U_grid) return VDWDF_EINVAL;
     if (!table) return VDWDF_ENOTABLE;
     if (precision != VDWDF_FP32 && precision != VDWDF_FP64) return VDWDF_EINVAL;
+    rc = check_tuning(tu, G.skew);
+    if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long launches0 = g_launches.load();
     double *d64 = nullptr;
@@ -1245,6 +1258,8 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
         rc = check_cut(n_cut, r_cut, geo[k]);
         if (rc) return rc;
         if (!n_dev[k]) return VDWDF_EINVAL;
+        rc = check_tuning(tuning, geo[k].skew);
+        if (rc) return rc;
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     double *d64 = nullptr;
@@ -1430,6 +1445,7 @@ int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, do
     Timer tm;
     for (int ci = 0; ci < kCand && rc == VDWDF_OK && hs.n_active > 0; ++ci) {
         if (fp64 && cand[ci].smem_rows != 0) continue;
+        if (check_tuning(&cand[ci], G.skew) != VDWDF_OK) continue;  // no such kernel for this cell
         Launch ln = choose_launch(precision, false, &cand[ci], table, hs.n_active, G.skew);
         for (int rep = 0; rep < 2 && rc == VDWDF_OK; ++rep) {
             if (cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st) != cudaSuccess) rc = VDWDF_ECUDA;

@@ -128,6 +128,20 @@ def test_host_side_argument_errors(native):
     assert lib.vdwdf_gradient(ctypes.byref(g), None, ctypes.c_void_p(8), None) == -1
     assert lib.vdwdf_gradient(ctypes.byref(g), ctypes.c_void_p(8), None, None) == -1
     g.gradient = 0
+    # launch shapes outside the documented values, and thread counts without a skewed kernel
+    tu = native.vdwdf_tuning()
+    for field, value in (("threads", 300), ("items_per_sm", -1), ("smem_rows", -2), ("smem_row0", -5)):
+        tu = native.vdwdf_tuning()
+        setattr(tu, field, value)
+        assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1), 0,
+                                ctypes.byref(tu), ctypes.byref(res), None) == -1, field
+    tu = native.vdwdf_tuning()
+    tu.threads = 1024
+    g.cell[1][0] = 5.0  # skewed
+    assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1), 0,
+                            ctypes.byref(tu), ctypes.byref(res), None) == -2
+    tu.threads = 448
+    g.cell[1][0] = 0.0
     # no-allocation energy: a grid larger than its static scratch holds is refused
     g.cell[0][1] = 0.0
     g.n[0], g.n[1], g.n[2] = 64, 64, 17
