@@ -88,6 +88,16 @@ MUTATIONS = [
      "d[c] = ri[c] - rj[c] + m0 * cell[c] + m1 * cell[3 + c] + m2 * cell[6 + c];",
      "d[c] = ri[c] - rj[c] + m0 * cell[3 * c] + m1 * cell[3 * c + 1] + m2 * cell[3 * c + 2];", 0,
      CELL.test_skewed_pair_counts_brute_force, ("oracle_mod", "oracle_spline")),
+    ("kernel: nu(y) = y^2/h without the 1/2",
+     "return 0.5 * y * y / h;", "return y * y / h;", 0,
+     K.test_phi_large_D_asymptote, ("oracle_mod", 0.0)),
+    ("spline: the two linear basis weights swapped",
+     "double al[2] = {1.0 - t, t};", "double al[2] = {t, 1.0 - t};", 0,
+     SPL.test_spline_reproduces_nodes, ("oracle_mod",)),
+    ("past the table: d delta/d d1 with (1 + ds) for (1 - ds)",
+     "*rdphi1 = r * (rho * dp17 + p17 * drho * sgn * (1.0 - ds) / (2.0 * D));",
+     "*rdphi1 = r * (rho * dp17 + p17 * drho * sgn * (1.0 + ds) / (2.0 * D));", 0,
+     SPL.test_kernel_branches, ("oracle_mod", "oracle_spline")),
     ("PBE correlation: A^2 t^4 written A t^4",
      "double den = 1.0 + A * t2 + A * A * t2 * t2;", "double den = 1.0 + A * t2 + A * t2 * t2;", 0,
      SEMI.test_pbe_gradient_correction_limits, ("oracle_mod",)),
