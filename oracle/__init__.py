@@ -177,7 +177,9 @@ class Spline:
 
     Boundary conditions: zero slope at D = 0 and delta = 0, zero curvature at
     the last node of each axis.  ``kernel`` adds the D > Dmax branch: eq. (17)
-    times rho(delta), the 1-D spline through phi(Dmax, delta_l) / phi17(Dmax, delta_l).
+    times g = rho(delta*) + (1 - rho(0)) (1 - (Dmax/D)^2), rho the 1-D spline
+    through phi(Dmax, delta_l) / phi17(Dmax, delta_l) and
+    delta* = max(0, 1 - min(d1, d2)/Dmax).
     """
 
     def __init__(self, nodes, Dmax=30.0):

@@ -24,6 +24,11 @@
  *   orc_W, orc_phi, orc_phi_table  pinned: symmetry, zero integral, large-D
  *                                   asymptote, small-D logarithm, printed-W
  *                                   formula at high precision
+ *   kernel_pair (orc_kernel_many)   pinned: continuity at Dmax, the eq. (17)
+ *                                   limit at large D for any delta < 1,
+ *                                   direct quadrature of eq. (14) at D = 60,
+ *                                   120 past the table, r dphi/dd1 against
+ *                                   central differences in both branches
  *   orc_spline_*                    pinned: node reproduction, exact cubic
  *                                   reproduction, 1-D library spline
  *   orc_eps_c, orc_q0               pinned: k_F and gradient-term hand values,
@@ -468,14 +473,25 @@ int orc_spline_eval_many(int nD, double hD, int nd, double hd, const double *f,
 /*              so phi stays twice differentiable in delta;                */
 /*   D >  Dmax: Dion eq. (17), phi17 = -C / (d1^2 d2^2 (d1^2 + d2^2)),      */
 /*              C = 12 (4 pi / 9)^3, d1 = D (1 + delta), d2 = D (1 - delta),*/
-/*              times rho(delta), the cubic spline (same end conditions as  */
-/*              the table) through phi(Dmax, delta_l) / phi17(Dmax, delta_l).*/
-/* Reading: eq. (17) needs both d1 and d2 large, so at large delta it is off */
-/* by tens of percent at D = Dmax; rho (= 1 where it is accurate) makes phi  */
-/* continuous across Dmax, so that E is a continuous function of n.         */
+/*              times g = rho(delta*) + (1 - rho(0)) (1 - (Dmax / D)^2),    */
+/*              rho the cubic spline (same end conditions as the table)     */
+/*              through phi(Dmax, delta_l) / phi17(Dmax, delta_l), and      */
+/*              delta* = max(0, 1 - min(d1, d2) / Dmax): the delta at which */
+/*              the last table row has the same smaller argument.          */
+/* Reading: eq. (17) is the limit where both d1 and d2 are large; with d1   */
+/* large, phi / phi17 depends on the smaller argument alone (by quadrature */
+/* of eq. (14): at min(d1, d2) = 1.8 the ratio is 0.3614 at D = 30 and     */
+/* 0.3629 at D = 120).  So the ratio the table shows at D = Dmax is carried */
+/* to larger D along constant min(d1, d2), and it tends to 1 as that grows. */
+/* The second term takes out the table's own error at delta* = 0 (where    */
+/* eq. (17) is exact to 1e-8 at D = 30) over growing D.  At D = Dmax,      */
+/* g = rho(delta): phi is continuous there, so E is a continuous function   */
+/* of n.                                                                    */
 /* Returns phi, and r * dphi/dd1 for the pair (d1 = q_i r, d2 = q_j r),     */
 /* with signed ds = (q_i - q_j)/(q_i + q_j), dds/dd1 = (1 - ds)/(2 D):      */
-/*   dphi/dd1 = 1/2 phi_D + (1 - ds)/(2 D) phi_ds.                          */
+/*   dphi/dd1 = 1/2 phi_D + (1 - ds)/(2 D) phi_ds;                          */
+/* beyond Dmax, r dg/dd1 = -rho'(delta*) r / Dmax (only when d1 is the     */
+/* smaller argument and delta* > 0) + (1 - rho(0)) Dmax^2 r / D^3.          */
 /* ---------------------------------------------------------------------- */
 static void kernel_pair(const orc_spline *s, double Dmax, double r, double qi, double qj,
                         double *phi, double *rdphi1, int *clamped)
@@ -494,11 +510,26 @@ static void kernel_pair(const orc_spline *s, double Dmax, double r, double qi, d
         double d12 = d1 * d1, d22 = d2 * d2;
         double p17 = -C / (d12 * d22 * (d12 + d22));
         double dp17 = -p17 * (2.0 / d1 + 2.0 * d1 / (d12 + d22));
+        double dsmall = (d1 < d2) ? d1 : d2;
+        double dstar = 1.0 - dsmall / Dmax;
         double rho, drho;
-        spline1_eval(s->nd, s->hd, s->rho, s->rhoM, dl, &rho, &drho);
-        rho += drho * ext;
-        *phi = rho * p17;
-        *rdphi1 = r * (rho * dp17 + p17 * drho * sgn * (1.0 - ds) / (2.0 * D));
+        if (dstar > 0.0) {
+            double e = 0.0;   /* past the last delta node: linear continuation */
+            double dc = dstar;
+            if (dc > dlast) { e = dc - dlast; dc = dlast; }
+            spline1_eval(s->nd, s->hd, s->rho, s->rhoM, dc, &rho, &drho);
+            rho += drho * e;
+        } else {
+            rho = s->rho[0];  /* the spline through the nodes takes rho_0 at delta = 0 */
+            drho = 0.0;       /* and has zero slope there (end condition) */
+        }
+        double rho0 = s->rho[0];
+        double Dr = Dmax / D;
+        double g = rho + (1.0 - rho0) * (1.0 - Dr * Dr);
+        double rdg = (1.0 - rho0) * Dr * Dr * r / D;
+        if (d1 < d2 && dstar > 0.0) rdg -= drho * r / Dmax;
+        *phi = g * p17;
+        *rdphi1 = r * g * dp17 + p17 * rdg;
         return;
     }
     double p, pD, pd, pDd;

@@ -94,9 +94,15 @@ MUTATIONS = [
     ("spline: the two linear basis weights swapped",
      "double al[2] = {1.0 - t, t};", "double al[2] = {t, 1.0 - t};", 0,
      SPL.test_spline_reproduces_nodes, ("oracle_mod",)),
-    ("past the table: d delta/d d1 with (1 + ds) for (1 - ds)",
-     "*rdphi1 = r * (rho * dp17 + p17 * drho * sgn * (1.0 - ds) / (2.0 * D));",
-     "*rdphi1 = r * (rho * dp17 + p17 * drho * sgn * (1.0 + ds) / (2.0 * D));", 0,
+    ("past the table: the larger argument taken for the smaller",
+     "double dsmall = (d1 < d2) ? d1 : d2;", "double dsmall = (d1 < d2) ? d2 : d1;", 0,
+     SPL.test_kernel_past_table_matches_quadrature, ("oracle_mod", "oracle_spline", 60.0)),
+    ("past the table: the (1 - rho(0)) term dropped",
+     "double g = rho + (1.0 - rho0) * (1.0 - Dr * Dr);", "double g = rho;", 0,
+     SPL.test_kernel_tends_to_eq17_at_large_D, ("oracle_mod", "oracle_spline", 0.9)),
+    ("past the table: the rho'(delta*) term of r dphi/dd1 with the wrong sign",
+     "if (d1 < d2 && dstar > 0.0) rdg -= drho * r / Dmax;",
+     "if (d1 < d2 && dstar > 0.0) rdg += drho * r / Dmax;", 0,
      SPL.test_kernel_branches, ("oracle_mod", "oracle_spline")),
     ("PBE correlation: A^2 t^4 written A t^4",
      "double den = 1.0 + A * t2 + A * A * t2 * t2;", "double den = 1.0 + A * t2 + A * t2 * t2;", 0,

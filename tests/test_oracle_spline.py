@@ -70,22 +70,43 @@ def _rho_reference(oracle_mod, s):
     return sp.CubicSpline(dl, ratio, bc_type=((1, 0.0), (2, 0.0)))
 
 
+def _far_factor(oracle_mod, s, rho, d1, d2):
+    """The factor g that multiplies eq. (17) past the table, from its reading:
+    rho at delta* = max(0, 1 - min(d1, d2)/Dmax), the delta at which the last
+    table row has the same smaller argument, plus (1 - rho(0)) (1 - (Dmax/D)^2)."""
+    D = 0.5 * (d1 + d2)
+    dstar = max(0.0, 1.0 - min(d1, d2) / s.Dmax)
+    dlast = (s.nd - 1) * s.hd
+    if dstar > dlast:  # linear continuation past the last node
+        val = rho(dlast) + rho(dlast, 1) * (dstar - dlast)
+    else:
+        val = rho(dstar)
+    return val + (1.0 - rho(0.0)) * (1.0 - (s.Dmax / D) ** 2)
+
+
+# (r, q_i, q_j) past the table: delta* clamped at 0 (both arguments above Dmax);
+# delta* > 0 with d1 the smaller argument, then d2; delta* past the last node
+FAR_PAIRS = [(12.0, 3.1, 2.7), (10.0, 0.3, 6.0), (10.0, 6.0, 0.3), (5.0, 0.02, 12.1)]
+
+
 def test_kernel_branches(oracle_mod, oracle_spline):
-    """D > Dmax takes eq. (17) times rho(delta) with the analytic d1-derivative; below,
-    the spline; a delta above the last node is counted."""
+    """D > Dmax takes eq. (17) times g (see _far_factor) with the analytic
+    d1-derivative; below, the spline; a delta above the last node is counted."""
     s = oracle_spline
     rho = _rho_reference(oracle_mod, s)
-    r, qi, qj = 12.0, 3.1, 2.7         # D = 34.8
-    p, rd, ncl = s.kernel([r], [qi], [qj])
-    d1, d2 = qi * r, qj * r
-    dl = (qi - qj) / (qi + qj)
-    pa = rho(dl) * oracle_mod.phi_asym(d1, d2)
-    assert abs(p[0] - pa) < 1e-13 * abs(pa) and ncl == 0
-    # r dphi/dd1 by a central difference in q_i (d1 = q_i r moves, d2 fixed)
     e = 1e-6
-    pp, _, _ = s.kernel([r], [qi + e], [qj])
-    pm, _, _ = s.kernel([r], [qi - e], [qj])
-    assert abs((pp[0] - pm[0]) / (2 * e) - rd[0]) < 1e-7 * abs(rd[0])
+    for r, qi, qj in FAR_PAIRS:
+        assert 0.5 * r * (qi + qj) > s.Dmax
+        p, rd, ncl = s.kernel([r], [qi], [qj])
+        d1, d2 = qi * r, qj * r
+        pa = _far_factor(oracle_mod, s, rho, d1, d2) * oracle_mod.phi_asym(d1, d2)
+        assert abs(p[0] - pa) < 1e-12 * abs(pa), (r, qi, qj, p[0], pa)
+        # r dphi/dd1 by a central difference in q_i (d1 = q_i r moves, d2 fixed)
+        h = e * qi
+        pp, _, _ = s.kernel([r], [qi + h], [qj])
+        pm, _, _ = s.kernel([r], [qi - h], [qj])
+        fd = (pp[0] - pm[0]) / (2 * h)   # dphi/dq_i = r dphi/dd1
+        assert abs(fd - rd[0]) < 1e-6 * abs(rd[0]), (r, qi, qj, fd, rd[0])
     # inside the table: the same check
     r, qi, qj = 2.0, 1.3, 0.9
     p0, rd0, _ = s.kernel([r], [qi], [qj])
@@ -95,6 +116,39 @@ def test_kernel_branches(oracle_mod, oracle_spline):
     # clamping: delta = (8 - 0.01)/(8 + 0.01) > 0.995 with D = 0.5 * 0.5 * 8.01 < 30
     _, _, ncl = s.kernel([0.5], [8.0], [0.01])
     assert ncl == 1
+
+
+@pytest.mark.parametrize("dl", [0.0, 0.8, 0.9, 0.94])
+def test_kernel_tends_to_eq17_at_large_D(oracle_mod, oracle_spline, dl):
+    """Eq. (17) is the kernel's limit when both arguments are large (section 2: it
+    is used "for large D"): at fixed delta the kernel as used, divided by eq. (17)
+    written out here, tends to 1 as D grows, and is within 1e-5 of it at D = 1000."""
+    s = oracle_spline
+    C = 12.0 * (4.0 * np.pi / 9.0) ** 3
+    dev = []
+    for D in (100.0, 300.0, 1000.0):
+        qi, qj = 1.0 + dl, 1.0 - dl
+        r = D                                   # D = r (q_i + q_j) / 2
+        d1, d2 = qi * r, qj * r
+        p17 = -C / (d1 ** 2 * d2 ** 2 * (d1 ** 2 + d2 ** 2))
+        p, _, _ = s.kernel([r], [qi], [qj])
+        dev.append(abs(p[0] / p17 - 1.0))
+    assert dev[1] < dev[0] and dev[2] < dev[1], dev
+    assert dev[2] < 1e-5, dev
+
+
+@pytest.mark.parametrize("D", [60.0, 120.0])
+def test_kernel_past_table_matches_quadrature(oracle_mod, oracle_spline, D):
+    """Past the table the kernel as used agrees with direct quadrature of eq. (14)
+    at large delta, where eq. (17) alone is off by up to 97 % (min(d1, d2) of a few
+    bohr^-1 q): within 1 % for delta = 0.9, 0.95, 0.99 at D = 60 and 120."""
+    s = oracle_spline
+    for dl in (0.9, 0.95, 0.99):
+        qi, qj = 1.0 + dl, 1.0 - dl
+        r = D
+        p, _, _ = s.kernel([r], [qi], [qj])
+        pq = oracle_mod.phi([qi * r], [qj * r], oracle_mod.QUAD_REFERENCE)[0]
+        assert abs(p[0] / pq - 1.0) < 1e-2, (D, dl, p[0], pq)
 
 
 def test_kernel_continuous_at_table_edge(oracle_mod, oracle_spline):

@@ -46,8 +46,9 @@ def test_translation_invariance_periodic(oracle_mod, oracle_spline):
 
 def test_far_fragments_cross_term_is_asymptotic_sum(oracle_mod, oracle_spline):
     """Two compactly supported blobs so far apart that every cross pair has D > 30:
-    E_AB - E_A - E_B must equal dV^2 sum_{i in A, j in B} n_i n_j rho(delta) phi_17(q_i r, q_j r),
-    written out here with numpy and scipy (the factor 1/2 and the two orderings give 1)."""
+    E_AB - E_A - E_B must equal dV^2 sum_{i in A, j in B} n_i n_j g phi_17(q_i r, q_j r),
+    with the factor g of the kernel past the table, written out here with numpy and
+    scipy (the factor 1/2 and the two orderings give 1)."""
     sp = pytest.importorskip("scipy.interpolate")
     g = golden_dict("dion_kernel.txt")
     rng = np.random.default_rng(29)
@@ -74,8 +75,14 @@ def test_far_fragments_cross_term_is_asymptotic_sum(oracle_mod, oracle_spline):
     ratio = s.f[-1] / (-g["C_asym"] / ((s.Dmax * (1 + dln)) ** 2 * (s.Dmax * (1 - dln)) ** 2 *
                                       ((s.Dmax * (1 + dln)) ** 2 + (s.Dmax * (1 - dln)) ** 2)))
     rho = sp.CubicSpline(dln, ratio, bc_type=((1, 0.0), (2, 0.0)))
-    dl = np.minimum(np.abs(d1 - d2) / (d1 + d2), dln[-1])
-    phi = rho(dl) * (-g["C_asym"] / (d1 ** 2 * d2 ** 2 * (d1 ** 2 + d2 ** 2)))
+    # eq. (17) times g = rho(delta*) + (1 - rho(0)) (1 - (Dmax/D)^2), with
+    # delta* = max(0, 1 - min(d1, d2)/Dmax) (linear past the last delta node)
+    D = 0.5 * (d1 + d2)
+    dstar = np.maximum(0.0, 1.0 - np.minimum(d1, d2) / s.Dmax)
+    past = np.maximum(dstar - dln[-1], 0.0)
+    gfac = rho(np.minimum(dstar, dln[-1])) + rho(dln[-1], 1) * past
+    gfac = gfac + (1.0 - rho(0.0)) * (1.0 - (s.Dmax / D) ** 2)
+    phi = gfac * (-g["C_asym"] / (d1 ** 2 * d2 ** 2 * (d1 ** 2 + d2 ** 2)))
     cross = PA.dV ** 2 * np.sum(PA.na[:, None] * PB.na[None, :] * phi)
     assert abs((EAB - EA - EB) - cross) < 1e-6 * abs(cross)
     assert abs(EA) > 1e3 * abs(cross)
