@@ -142,10 +142,13 @@ typedef struct {
 /* Optional launch shape of the pair kernel (NULL = defaults / tuned).  Values
  * outside those listed are VDWDF_EINVAL; 256 or 1024 threads on a skewed cell
  * are VDWDF_EUNSUPPORTED (both before any device work). */
+#define VDWDF_TUNE_AUTO (-1)  /* threads: vdwdf_energy_batched only -- the autotuner
+                                 picks the shape (the other fields are ignored) */
 typedef struct {
     int32_t threads;      /* threads per CTA: 256, 384, 448, 512 or 1024 (0 = default:
                              FP32 E + v 448, or 384 on skewed cells; 512 otherwise);
-                             skewed cells take 384, 448 or 512                       */
+                             skewed cells take 384, 448 or 512; VDWDF_TUNE_AUTO in
+                             vdwdf_energy_batched                                    */
     int32_t items_per_sm; /* target work items per warp slot for load balance (0 = 256) */
     int32_t smem_rows;    /* FP32 path: table rows resident in shared memory
                              (0 = as many as fit, -1 = none)                          */
@@ -248,9 +251,15 @@ int vdwdf_potential(const vdwdf_grid *grid, const double *n_dev, double n_cut, d
 
 /* E_c^nl of ninst independent densities (grids[k], n_dev[k]) in one
  * persistent launch of the pair kernel, recorded once into a CUDA graph and
- * replayed on later calls with the same shapes and pointers (binding curves,
- * section 6.1).  E_out: host array of ninst doubles.  Synchronises the
- * stream.  Errors as vdwdf_energy. */
+ * replayed on later calls that would record the same graph: the same device,
+ * pointers, shapes, cells, periodicity, gradient kind, cutoffs, precision,
+ * tuning and table (binding curves, section 6.1).  Up to 8 recorded graphs are
+ * kept (the least recently used is dropped first, with its scratch); freeing a
+ * table drops the graphs that read it.  tuning->threads = VDWDF_TUNE_AUTO runs
+ * the autotuner (as vdwdf_autotune) on the largest instance when the graph is
+ * recorded and uses the shape it picks; out->pair_threads reports it.  E_out:
+ * host array of ninst doubles.  Synchronises the stream.  Errors as
+ * vdwdf_energy. */
 int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const *n_dev,
                          double n_cut, double r_cut, const vdwdf_table *table, int precision,
                          const vdwdf_tuning *tuning, double *E_out, vdwdf_result *out,
@@ -290,6 +299,20 @@ typedef struct {
  * Errors: VDWDF_EINVAL, VDWDF_ECUDA, VDWDF_EALLOC. */
 int vdwdf_semilocal(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev,
                     vdwdf_semilocal_result *out, void *cuda_stream);
+
+/* Exchange functional of eq. (3)'s bracket. */
+#define VDWDF_X_PBE 0     /* E_x^PBE: the PBE exchange stays                        */
+#define VDWDF_X_REVPBE 1  /* E_x^revPBE replaces it (the alternative after eq. 3)  */
+
+/* Eq. (3): the total energy with the nonlocal correlation, from the total energy
+ * of a PBE calculation, the semilocal terms of its density (vdwdf_semilocal)
+ * and E_c^nl (vdwdf_energy or vdwdf_potential), all in Hartree:
+ *   E_tot^NL = E_tot^DFT - E_x^PBE - E_c^PBE + (E_x + E_c^LDA + E_c^nl),
+ * E_x = E_x^PBE or E_x^revPBE as `exchange` says.  Host arithmetic only.
+ * Errors: VDWDF_EINVAL for a NULL pointer, another exchange value or a
+ * non-finite input (E_out is then untouched). */
+int vdwdf_total_energy_nl(double E_tot_dft, const vdwdf_semilocal_result *semi, double E_c_nl, int exchange,
+                          double *E_out);
 
 /* --------------------------------------------------------------------- */
 /* Voxel-averaged diagonal (the "phi0" step of the paper's Appendix A      */
@@ -357,8 +380,9 @@ int vdwdf_diag_voxel_potential(const vdwdf_grid *grid, const double *n_dev, doub
  * allocates its arrays once per run.  This entry point is for callers that
  * cannot allocate device memory while they run, for example:
  *  - a host code that has reserved the device memory for its own arrays;
- *  - a loop that must not synchronise the device (cudaMalloc and cudaFree
- *    can synchronise);
+ *  - code that must not wait on the whole device: cudaMalloc and cudaFree
+ *    can wait for work on every stream, while this call waits only for its
+ *    own stream (it blocks the calling thread until that is done);
  *  - a loop of many small grids (binding curves, geometry steps) where one
  *    allocation per call costs more than the pair sum.
  * Same arguments, results and errors as vdwdf_energy, with library default
@@ -380,8 +404,9 @@ int vdwdf_diag_voxel_potential(const vdwdf_grid *grid, const double *n_dev, doub
  *    resident allocates.  Otherwise the call returns VDWDF_ENOTABLE.
  *  - Overlap: calls overlapping in time would race on the one scratch array.
  *    The library therefore holds a process-wide lock for the whole call, and
- *    the call synchronises its stream before returning.  Other code must not
- *    write the array.
+ *    the call synchronises its stream before every return that follows its
+ *    first device work, errors included, so none of its work is still queued
+ *    when the next call starts.  Other code must not write the array.
  *  - Zeroing: everything that must start at zero (the counters and the
  *    work-queue head) is cleared by the call itself on the stream.  Every
  *    per-item energy partial is written before it is read.
@@ -392,7 +417,9 @@ int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const doub
                          vdwdf_result *out, void *cuda_stream);
 
 /* Time candidate launch shapes of the pair kernel on this problem (energy
- * path, a sample of the work) and write the fastest to *best.  The shape
+ * path, on every k-th work item: about 16 items per warp slot spread over the
+ * whole pair triangle) and write the fastest to *best: the one with the most
+ * pair evaluations per millisecond of its second timed run.  The shape
  * suits vdwdf_energy and the batched path; vdwdf_potential's default shape
  * (448 threads, 384 on skewed cells) was the fastest for the potential pass
  * on every workload measured. */

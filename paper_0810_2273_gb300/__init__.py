@@ -265,16 +265,21 @@ def diag_voxel_potential(n, lengths, periodic, n_cut, table, nphi0=0, gradient="
 
 
 def total_energy_nl(E_tot_dft, semi, E_c_nl, exchange="pbe"):
-    """Eq. 3: the total energy with the nonlocal correlation, from the DFT total
-    energy of a PBE calculation, the semilocal terms of that density (the dict of
-    semilocal()) and E_c^nl:
-        E_tot^NL = E_tot^DFT - E_x^PBE - E_c^PBE + (E_x + E_c^LDA + E_c^nl),
-    with E_x = E_x^PBE, or E_x^revPBE for exchange="revpbe" (the alternative the
-    paper mentions after eq. 3).  Plain host arithmetic."""
+    """Eq. 3 through vdwdf_total_energy_nl: the total energy with the nonlocal
+    correlation, from the DFT total energy of a PBE calculation, the semilocal
+    terms of that density (the dict of semilocal()) and E_c^nl, with E_x^PBE or,
+    for exchange="revpbe", E_x^revPBE in the bracket."""
     if exchange not in ("pbe", "revpbe"):
         raise ValueError("exchange must be 'pbe' or 'revpbe'")
-    ex = semi["Ex_pbe"] if exchange == "pbe" else semi["Ex_revpbe"]
-    return E_tot_dft - semi["Ex_pbe"] - semi["Ec_pbe"] + (ex + semi["Ec_lda"] + E_c_nl)
+    lib = _native.load()
+    s = _native.vdwdf_semilocal_result()
+    for k in ("Ex_lda", "Ec_lda", "Ex_pbe", "Ec_pbe", "Ex_revpbe"):
+        setattr(s, k, float(semi[k]))
+    out = ctypes.c_double()
+    st = lib.vdwdf_total_energy_nl(float(E_tot_dft), ctypes.byref(s), float(E_c_nl),
+                                   0 if exchange == "pbe" else 1, ctypes.byref(out))
+    _native.check(st, "vdwdf_total_energy_nl")
+    return out.value
 
 
 def potential(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", tuning=None,

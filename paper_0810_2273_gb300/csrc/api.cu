@@ -25,6 +25,7 @@
 struct vdwdf_table {
     int nD, nd;
     double Dmax;
+    unsigned long long gen = 0;  // unique per table of this process (graph-cache keys)
     std::vector<double> nodes;   // nD * nd, D outer
     std::vector<double> coef64;  // (nD + 2) * (nd + 2), / 36
     std::vector<float> coef32;
@@ -37,6 +38,7 @@ namespace vdwdf {
 namespace {
 
 std::atomic<long long> g_launches{0};
+std::atomic<unsigned long long> g_table_gen{0};  // generation ids of tables
 
 // Fault injection for tests, on the host only (no device fault is ever caused):
 //   VDWDF_FAIL_ALLOC=1  every scratch allocation of a call fails (VDWDF_EALLOC);
@@ -68,6 +70,7 @@ constexpr int kMaxImages = 64;
 // Device layout of the coefficients: (nD + 2) x (nd + 2) bicubic coefficients / 36,
 // then nd + 2 coefficients / 6 of the beyond-table normalisation rho(delta).
 int finish_table(vdwdf_table *t) {
+    t->gen = ++g_table_gen;
     const int S = t->nd + 2;
     const size_t main = static_cast<size_t>(t->nD + 2) * S;
     try {
@@ -484,10 +487,15 @@ void fill_shared(const vdwdf_table *t, const double *d64, const float *d32, cons
     sh.cD = 0.5 / hD;
     sh.cd = static_cast<double>(t->nd);
     sh.C_asym = 12.0 * std::pow(4.0 * kPi / 9.0, 3);
+    // rho(0): the last node row at delta = 0 over eq. (17) at d1 = d2 = Dmax
+    const double Dm = t->Dmax, Dm2 = Dm * Dm;
+    const double p17 = -sh.C_asym / (2.0 * Dm2 * Dm2 * Dm2);
+    sh.om_rho0 = 1.0 - t->nodes[static_cast<size_t>(t->nD - 1) * t->nd] / p17;
     sh.ks0 = ln.ks0;
     sh.ksn = ln.ksn;
     sh.jtiles_per_item = ln.jt;
     sh.item_limit = 0xFFFFFFFFu;
+    sh.item_stride = 1u;
     sh.max_iters = max_iters_override(max_iters);
     sh.queue = queue;
     sh.item_E = nullptr;
@@ -496,9 +504,17 @@ void fill_shared(const vdwdf_table *t, const double *d64, const float *d32, cons
 
 // A caller's launch shape: VDWDF_EINVAL outside the documented values,
 // VDWDF_EUNSUPPORTED for a thread count the skewed kernel is not built for.
-int check_tuning(const vdwdf_tuning *tu, bool skew) {
+// The autotuner's candidate launch shapes (threads, items per warp slot, shared
+// band rows, band start); the fourth is the energy-mode default.
+constexpr int kTuneCount = 8;
+constexpr vdwdf_tuning kTuneCandidates[kTuneCount] = {
+    {256, 256, 0, -1}, {384, 256, 0, -1}, {448, 256, 0, -1}, {512, 256, 0, -1},
+    {1024, 256, 0, -1}, {512, 64, 0, -1}, {512, 1024, 0, -1}, {512, 256, -1, 0}};
+
+int check_tuning(const vdwdf_tuning *tu, bool skew, bool allow_auto = false) {
     if (!tu) return VDWDF_OK;
     const int t = tu->threads;
+    if (allow_auto && t == VDWDF_TUNE_AUTO) return VDWDF_OK;  // the other fields are ignored
     if (t != 0 && t != 256 && t != 384 && t != 448 && t != 512 && t != 1024) return VDWDF_EINVAL;
     if (tu->items_per_sm < 0 || tu->smem_rows < -1 || tu->smem_row0 < -1) return VDWDF_EINVAL;
     if (skew && (t == 256 || t == 1024)) return VDWDF_EUNSUPPORTED;
@@ -706,6 +722,8 @@ int run_single(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
 // recorded into a CUDA graph and replayed for the same inputs
 // ---------------------------------------------------------------------------
 struct BatchPlan {
+    unsigned long long table_gen = 0;  // the table the graph reads (its device copies)
+    unsigned long long last_use = 0;   // for least-recently-used eviction
     std::vector<Geom> geo;
     std::vector<Work> work;
     std::vector<unsigned char *> bufs;
@@ -717,6 +735,7 @@ struct BatchPlan {
     int launches_per_replay = 0;
     int row0 = 0;                    // band start of the first launch (-1: chosen on the device)
     int threads = 0;                 // the pair kernel's threads per CTA
+    vdwdf_tuning tuned = {0, 0, 0, 0};  // VDWDF_TUNE_AUTO: the shape the autotuner chose
     ~BatchPlan() {
         if (exec) cudaGraphExecDestroy(exec);
         for (auto *b : bufs) cudaFree(b);
@@ -725,8 +744,23 @@ struct BatchPlan {
     }
 };
 
+// Recorded batch graphs, keyed by everything the recording baked in.  At most
+// kMaxPlans are kept (least recently used goes first); the plans of a table are
+// dropped when it is freed.  A plan is only ever destroyed under g_batch_mu, which
+// a batched call holds until its replay has finished on its stream.
 std::mutex g_batch_mu;
 std::map<std::vector<uintptr_t>, BatchPlan *> g_batches;
+constexpr size_t kMaxPlans = 8;
+unsigned long long g_batch_clock = 0;
+
+void destroy_plan(BatchPlan *bp) {
+    int cur = 0;
+    const bool have = cudaGetDevice(&cur) == cudaSuccess;
+    if (!have || cur != bp->device) cudaSetDevice(bp->device);
+    const int dev = bp->device;
+    delete bp;
+    if (have && cur != dev) cudaSetDevice(cur);
+}
 
 int record_batch(BatchPlan &bp, int ninst, const double *const *n_dev, double n_cut,
                  const vdwdf_table *table, int precision, const vdwdf_tuning *tu, double *d64,
@@ -871,6 +905,18 @@ const char *vdwdf_strerror(int s) {
 
 int vdwdf_version(void) { return VDWDF_VERSION; }
 
+int vdwdf_total_energy_nl(double E_tot_dft, const vdwdf_semilocal_result *semi, double E_c_nl, int exchange,
+                          double *E_out) {
+    if (!semi || !E_out || (exchange != VDWDF_X_PBE && exchange != VDWDF_X_REVPBE)) return VDWDF_EINVAL;
+    const double ex = exchange == VDWDF_X_PBE ? semi->Ex_pbe : semi->Ex_revpbe;
+    // eq. (3): the PBE exchange-correlation is taken out and replaced by the
+    // chosen exchange, LDA correlation and the nonlocal correlation
+    const double E = E_tot_dft - semi->Ex_pbe - semi->Ec_pbe + (ex + semi->Ec_lda + E_c_nl);
+    if (!std::isfinite(E)) return VDWDF_EINVAL;
+    *E_out = E;
+    return VDWDF_OK;
+}
+
 int64_t vdwdf_launch_count(void) { return g_launches.load(); }
 
 int vdwdf_table_build(int nD, double Dmax, int ndelta, int quad_level, double *phi_nodes_out,
@@ -945,6 +991,18 @@ int vdwdf_table_info(const vdwdf_table *t, int *nD, double *Dmax, int *ndelta) {
 
 void vdwdf_table_free(vdwdf_table *t) {
     if (!t) return;
+    {
+        // recorded batch graphs read this table's device copies: drop them first
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        for (auto it = g_batches.begin(); it != g_batches.end();) {
+            if (it->second->table_gen == t->gen) {
+                destroy_plan(it->second);
+                it = g_batches.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
     int cur = 0;
     const bool have = cudaGetDevice(&cur) == cudaSuccess;
     for (auto &kv : t->dev) {
@@ -1213,6 +1271,82 @@ int diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_d
     return VDWDF_OK;
 }
 
+// The autotuner: the energy pass of each candidate launch shape on a strided
+// sample of the work items (every stride-th item, about 16 items per warp slot,
+// spread over the whole i <-> j triangle), timed twice with CUDA events on the
+// stream; the second timing counts.  The candidate with the most pair
+// evaluations per millisecond wins.
+int autotune_one(const Geom &G, const double *n_dev, double n_cut, const vdwdf_table *table, int precision,
+                 vdwdf_tuning *best, cudaStream_t st) {
+    double *d64 = nullptr;
+    float *d32 = nullptr;
+    int rc = table_on_device(table, &d64, &d32);
+    if (rc) return rc;
+    int *order = nullptr, nb = 0;
+    rc = brick_order(G.dims, &order, &nb);
+    if (rc) return rc;
+    const bool fp64 = precision == VDWDF_FP64;
+    const size_t bytes = layout(G, nb, false, fp64, nullptr, nullptr);
+    unsigned char *base = nullptr;
+    if (scratch_malloc_async(reinterpret_cast<void **>(&base), bytes, st) != cudaSuccess) return VDWDF_EALLOC;
+    Work w;
+    layout(G, nb, false, fp64, &w, base);
+    rc = prepare(G, n_dev, nullptr, n_cut, false, w, st);
+    Stats hs;
+    std::memset(&hs, 0, sizeof(hs));
+    if (rc == VDWDF_OK && cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = VDWDF_ECUDA;
+    if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
+    double best_rate = -1.0;
+    vdwdf_tuning choice = kTuneCandidates[3];
+    Timer tm;
+    for (int ci = 0; ci < kTuneCount && rc == VDWDF_OK && hs.n_active > 0; ++ci) {
+        const vdwdf_tuning &cd = kTuneCandidates[ci];
+        if (fp64 && cd.smem_rows != 0) continue;
+        if (check_tuning(&cd, G.skew) != VDWDF_OK) continue;  // no such kernel for this cell
+        Launch ln = choose_launch(precision, false, &cd, table, hs.n_active, G.skew);
+        const long long total = pair_items(hs.n_active, ln.jt);
+        const long long want = 16LL * ln.nctas * (ln.threads / 32);
+        const long long stride = std::max<long long>(1, total / std::max<long long>(1, want));
+        for (int rep = 0; rep < 2 && rc == VDWDF_OK; ++rep) {
+            if (cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st) != cudaSuccess) rc = VDWDF_ECUDA;
+            Stats zero;
+            std::memset(&zero, 0, sizeof(zero));
+            zero.n_active = hs.n_active;
+            if (rc == VDWDF_OK &&
+                cudaMemcpyAsync(w.stats, &zero, sizeof(Stats), cudaMemcpyHostToDevice, st) != cudaSuccess)
+                rc = VDWDF_ECUDA;
+            PairLaunch pl;
+            std::memset(&pl, 0, sizeof(pl));
+            fill_shared(table, d64, d32, ln, w.queue, 0xFFFFFFF0u, pl.sh);
+            pl.sh.item_limit = static_cast<unsigned int>(std::min<long long>(want, 0xFFFFFFF0LL));
+            pl.sh.item_stride = static_cast<unsigned int>(std::min<long long>(stride, 0xFFFFFFF0LL));
+            pl.ninst = 1;
+            fill_params(G, w, pl.inst[0]);
+            if (rc == VDWDF_OK && ln.ks0 < 0) rc = launch_band_choose(pl, w.hist, st);
+            tm.mark(0, st);
+            if (rc == VDWDF_OK) rc = launch_pair(precision, false, G.skew, ln.threads, pl, ln.nctas, st);
+            tm.mark(1, st);
+            Stats out;
+            if (rc == VDWDF_OK &&
+                cudaMemcpyAsync(&out, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                rc = VDWDF_ECUDA;
+            if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
+            const double ms = tm.ms(0, 1);
+            if (rc == VDWDF_OK && rep == 1 && ms > 0.0) {
+                const double rate = static_cast<double>(out.evals) / ms;
+                if (rate > best_rate) {
+                    best_rate = rate;
+                    choice = cd;
+                }
+            }
+        }
+    }
+    cudaFreeAsync(base, st);
+    if (rc == VDWDF_OK) *best = choice;
+    return rc;
+}
+
 }  // namespace
 }  // namespace vdwdf
 
@@ -1258,9 +1392,10 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
         rc = check_cut(n_cut, r_cut, geo[k]);
         if (rc) return rc;
         if (!n_dev[k]) return VDWDF_EINVAL;
-        rc = check_tuning(tuning, geo[k].skew);
+        rc = check_tuning(tuning, geo[k].skew, true);
         if (rc) return rc;
     }
+    const bool tune_auto = tuning && tuning->threads == VDWDF_TUNE_AUTO;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     double *d64 = nullptr;
     float *d32 = nullptr;
@@ -1268,11 +1403,15 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
     if (rc) return rc;
     int dev = 0;
     VDWDF_CUDA_TRY(cudaGetDevice(&dev));
-    // signature of the recorded graph: inputs, shapes, cutoffs, table, precision, tuning
+    // signature of the recorded graph: everything the recording bakes in -- inputs,
+    // shapes, the whole cell, periodicity, gradient kind, cutoffs, the table (its
+    // generation and device copies), precision and tuning
     std::vector<uintptr_t> key;
     key.push_back(static_cast<uintptr_t>(dev));
     key.push_back(static_cast<uintptr_t>(ninst));
-    key.push_back(reinterpret_cast<uintptr_t>(table));
+    key.push_back(static_cast<uintptr_t>(table->gen));
+    key.push_back(reinterpret_cast<uintptr_t>(d64));
+    key.push_back(reinterpret_cast<uintptr_t>(d32));
     key.push_back(static_cast<uintptr_t>(precision));
     uint64_t bits;
     std::memcpy(&bits, &n_cut, 8);
@@ -1287,23 +1426,49 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
     }
     for (int k = 0; k < ninst; ++k) {
         key.push_back(reinterpret_cast<uintptr_t>(n_dev[k]));
+        key.push_back(static_cast<uintptr_t>(static_cast<uint32_t>(grids[k].gradient)));
         for (int a = 0; a < 3; ++a) {
             key.push_back(static_cast<uintptr_t>(grids[k].n[a]));
             key.push_back(static_cast<uintptr_t>(grids[k].periodic[a]));
-            std::memcpy(&bits, &grids[k].cell[a][a], 8);
-            key.push_back(static_cast<uintptr_t>(bits));
+            for (int b = 0; b < 3; ++b) {
+                std::memcpy(&bits, &grids[k].cell[a][b], 8);
+                key.push_back(static_cast<uintptr_t>(bits));
+            }
         }
     }
     const long long launches0 = g_launches.load();
     std::lock_guard<std::mutex> lk(g_batch_mu);
     BatchPlan *bp = nullptr;
+    vdwdf_tuning tuned = {0, 0, 0, 0};
+    const vdwdf_tuning *use = tune_auto ? nullptr : tuning;
     auto it = g_batches.find(key);
     if (it != g_batches.end()) {
         bp = it->second;
     } else {
+        // make room: the least recently used plan goes (no replay of it is in
+        // flight: every batched call synchronises its stream before releasing the lock)
+        while (g_batches.size() >= kMaxPlans) {
+            auto old = g_batches.begin();
+            for (auto jt = g_batches.begin(); jt != g_batches.end(); ++jt)
+                if (jt->second->last_use < old->second->last_use) old = jt;
+            destroy_plan(old->second);
+            g_batches.erase(old);
+        }
+        // VDWDF_TUNE_AUTO: the autotuner picks the launch shape on the batch's
+        // largest instance before the graph is recorded (once per plan)
+        if (tune_auto) {
+            int kbig = 0;
+            for (int k = 1; k < ninst; ++k)
+                if (geo[k].N > geo[kbig].N) kbig = k;
+            rc = autotune_one(geo[kbig], n_dev[kbig], n_cut, table, precision, &tuned, st);
+            if (rc) return rc;
+            use = &tuned;
+        }
         bp = new (std::nothrow) BatchPlan;
         if (!bp) return VDWDF_EALLOC;
         bp->device = dev;
+        bp->table_gen = table->gen;
+        bp->tuned = tuned;
         bp->geo = geo;
         bp->work.resize(ninst);
         const int ngroups = (ninst + kMaxInst - 1) / kMaxInst;
@@ -1335,7 +1500,7 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
                 gsum += geo[k].N;
                 gskew = gskew || geo[k].skew;
             }
-            const Launch ln = choose_launch(precision, false, tuning, table, std::max<long long>(1, gsum / (k1 - k0)), gskew,
+            const Launch ln = choose_launch(precision, false, use, table, std::max<long long>(1, gsum / (k1 - k0)), gskew,
                                             k1 - k0);
             long long items = 0;
             for (int k = k0; k < k1; ++k) items += pair_items(geo[k].N, ln.jt);
@@ -1357,7 +1522,7 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            rc = record_batch(*bp, ninst, n_dev, n_cut, table, precision, tuning, d64, d32, cs);
+            rc = record_batch(*bp, ninst, n_dev, n_cut, table, precision, use, d64, d32, cs);
             e = cudaStreamEndCapture(cs, &graph);
         }
         if (e == cudaSuccess && rc == VDWDF_OK) e = cudaGraphInstantiate(&bp->exec, graph, 0);
@@ -1372,6 +1537,7 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
         }
         g_batches[key] = bp;
     }
+    bp->last_use = ++g_batch_clock;
     Timer tm;
     tm.mark(0, st);
     VDWDF_CUDA_TRY(cudaGraphLaunch(bp->exec, st));
@@ -1417,72 +1583,7 @@ int vdwdf_autotune(const vdwdf_grid *grid, const double *n_dev, double n_cut, do
     if (!n_dev) return VDWDF_EINVAL;
     if (!table) return VDWDF_ENOTABLE;
     if (precision != VDWDF_FP32 && precision != VDWDF_FP64) return VDWDF_EINVAL;
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    double *d64 = nullptr;
-    float *d32 = nullptr;
-    rc = table_on_device(table, &d64, &d32);
-    if (rc) return rc;
-    int *order = nullptr, nb = 0;
-    rc = brick_order(G.dims, &order, &nb);
-    if (rc) return rc;
-    const bool fp64 = precision == VDWDF_FP64;
-    const size_t bytes = layout(G, nb, false, fp64, nullptr, nullptr);
-    unsigned char *base = nullptr;
-    if (scratch_malloc_async(reinterpret_cast<void **>(&base), bytes, st) != cudaSuccess) return VDWDF_EALLOC;
-    Work w;
-    layout(G, nb, false, fp64, &w, base);
-    rc = prepare(G, n_dev, nullptr, n_cut, false, w, st);
-    Stats hs;
-    std::memset(&hs, 0, sizeof(hs));
-    if (rc == VDWDF_OK && cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        rc = VDWDF_ECUDA;
-    if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
-    constexpr int kCand = 8;
-    vdwdf_tuning cand[kCand] = {{256, 256, 0, -1}, {384, 256, 0, -1}, {448, 256, 0, -1}, {512, 256, 0, -1},
-                                {1024, 256, 0, -1}, {512, 64, 0, -1}, {512, 1024, 0, -1}, {512, 256, -1, 0}};
-    double best_rate = -1.0;
-    vdwdf_tuning choice = {512, 256, 0, -1};
-    Timer tm;
-    for (int ci = 0; ci < kCand && rc == VDWDF_OK && hs.n_active > 0; ++ci) {
-        if (fp64 && cand[ci].smem_rows != 0) continue;
-        if (check_tuning(&cand[ci], G.skew) != VDWDF_OK) continue;  // no such kernel for this cell
-        Launch ln = choose_launch(precision, false, &cand[ci], table, hs.n_active, G.skew);
-        for (int rep = 0; rep < 2 && rc == VDWDF_OK; ++rep) {
-            if (cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st) != cudaSuccess) rc = VDWDF_ECUDA;
-            Stats zero;
-            std::memset(&zero, 0, sizeof(zero));
-            zero.n_active = hs.n_active;
-            if (rc == VDWDF_OK &&
-                cudaMemcpyAsync(w.stats, &zero, sizeof(Stats), cudaMemcpyHostToDevice, st) != cudaSuccess)
-                rc = VDWDF_ECUDA;
-            PairLaunch pl;
-            std::memset(&pl, 0, sizeof(pl));
-            fill_shared(table, d64, d32, ln, w.queue, 0xFFFFFFF0u, pl.sh);
-            pl.sh.item_limit = static_cast<unsigned int>(4 * ln.nctas);
-            pl.ninst = 1;
-            fill_params(G, w, pl.inst[0]);
-            if (rc == VDWDF_OK && ln.ks0 < 0) rc = launch_band_choose(pl, w.hist, st);
-            tm.mark(0, st);
-            if (rc == VDWDF_OK) rc = launch_pair(precision, false, G.skew, ln.threads, pl, ln.nctas, st);
-            tm.mark(1, st);
-            Stats out;
-            if (rc == VDWDF_OK &&
-                cudaMemcpyAsync(&out, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-                rc = VDWDF_ECUDA;
-            if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
-            const double ms = tm.ms(0, 1);
-            if (rc == VDWDF_OK && rep == 1 && ms > 0.0) {
-                const double rate = static_cast<double>(out.evals) / ms;
-                if (rate > best_rate) {
-                    best_rate = rate;
-                    choice = cand[ci];
-                }
-            }
-        }
-    }
-    cudaFreeAsync(base, st);
-    if (rc == VDWDF_OK) *best = choice;
-    return rc;
+    return autotune_one(G, n_dev, n_cut, table, precision, best, static_cast<cudaStream_t>(cuda_stream));
 }
 
 }  // extern "C"
@@ -1590,76 +1691,88 @@ int vdwdf_energy_noalloc(const vdwdf_grid *grid, const double *n_dev, const doub
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const long long launches0 = g_launches.load();
-    double *d64 = nullptr;
-    float *d32 = nullptr;
-    rc = table_resident(table, &d64, &d32);
-    if (rc) return rc;
-    unsigned char *base = nullptr;
-    rc = noalloc_base(&base);
-    if (rc) return rc;
-    Work w;
-    layout(G, nb, false, fp64, &w, base);
-    int *order_dev = reinterpret_cast<int *>(base + o_order);
-    double *item_E = reinterpret_cast<double *>(base + o_items);
-
-    // as vdwdf_energy: gradient, q0, trimming and tiles, then the pair sum with
-    // one partial per work item summed in a fixed order
-    rc = noalloc_order(G.dims, order_dev, st);
-    if (rc) return rc;
-    rc = reset_stats(w.stats, st);  // counters start at zero (q0 minimum above all floats)
-    if (rc) return rc;
-    const double *g_use = nullptr;
-    rc = q0_gradient(G, n_dev, grad_dev, w.gsp, w.coef, &g_use, st);
-    if (rc) return rc;
-    rc = launch_grad_q0(G.dims, G.am, n_dev, g_use, w.q0, w.qn, w.qg, st);
-    if (rc) return rc;
-    rc = launch_compact(G.dims, n_dev, n_cut, w.q0, order_dev, nb, w.cnt, w.off, nullptr, w.p32, w.n32,
-                        w.p64, w.n64, w.blo, w.bhi, w.stats, st);
-    if (rc) return rc;
-    if (G.skew) {
-        rc = launch_tiles_cart(w.p32, w.stats, G.vrow, w.clo, w.chi, G.N, st);
+    // the call proper; every return of it, error or not, is followed by the stream
+    // synchronisation below, so that nothing of this call is still queued on the
+    // shared array when the lock is released
+    auto run = [&]() -> int {
+        double *d64 = nullptr;
+        float *d32 = nullptr;
+        rc = table_resident(table, &d64, &d32);
         if (rc) return rc;
-    }
-    Stats hs;
-    std::memset(&hs, 0, sizeof(hs));
-    VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
-    VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
-    int row0 = 0, threads = 0;
-    if (hs.n_active > 0) {
-        Launch ln = choose_launch(precision, false, nullptr, table, hs.n_active, G.skew);
-        row0 = ln.ks0;
-        threads = ln.threads;
-        VDWDF_CUDA_TRY(cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st));  // work-queue head
-        PairLaunch pl;
-        std::memset(&pl, 0, sizeof(pl));
-        const long long items = pair_items(hs.n_active, ln.jt);
-        if (items > 0xFFFFFFF0LL) return VDWDF_EINVAL;
-        fill_shared(table, d64, d32, ln, w.queue, static_cast<unsigned int>(items + 2), pl.sh);
-        // every item below item_cap writes its partial; any beyond it are added atomically
-        pl.sh.item_E = item_E;
-        pl.sh.item_cap = static_cast<unsigned int>(std::min<long long>(items, item_space));
-        pl.ninst = 1;
-        fill_params(G, w, pl.inst[0]);
-        if (ln.ks0 < 0) {
-            rc = launch_band_choose(pl, w.hist, st);
+        unsigned char *base = nullptr;
+        rc = noalloc_base(&base);
+        if (rc) return rc;
+        Work w;
+        layout(G, nb, false, fp64, &w, base);
+        int *order_dev = reinterpret_cast<int *>(base + o_order);
+        double *item_E = reinterpret_cast<double *>(base + o_items);
+
+        // as vdwdf_energy: gradient, q0, trimming and tiles, then the pair sum with
+        // one partial per work item summed in a fixed order
+        rc = noalloc_order(G.dims, order_dev, st);
+        if (rc) return rc;
+        rc = reset_stats(w.stats, st);  // counters start at zero (q0 minimum above all floats)
+        if (rc) return rc;
+        const double *g_use = nullptr;
+        rc = q0_gradient(G, n_dev, grad_dev, w.gsp, w.coef, &g_use, st);
+        if (rc) return rc;
+        rc = launch_grad_q0(G.dims, G.am, n_dev, g_use, w.q0, w.qn, w.qg, st);
+        if (rc) return rc;
+        rc = launch_compact(G.dims, n_dev, n_cut, w.q0, order_dev, nb, w.cnt, w.off, nullptr, w.p32, w.n32,
+                            w.p64, w.n64, w.blo, w.bhi, w.stats, st);
+        if (rc) return rc;
+        if (G.skew) {
+            rc = launch_tiles_cart(w.p32, w.stats, G.vrow, w.clo, w.chi, G.N, st);
             if (rc) return rc;
         }
-        rc = launch_pair(precision, false, G.skew, ln.threads, pl, ln.nctas, st);
-        if (rc) return rc;
-        rc = launch_reduce_items(pl, st);
-        if (rc) return rc;
+        Stats hs;
+        std::memset(&hs, 0, sizeof(hs));
+        VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+        VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+        int row0 = 0, threads = 0;
+        if (hs.n_active > 0) {
+            Launch ln = choose_launch(precision, false, nullptr, table, hs.n_active, G.skew);
+            row0 = ln.ks0;
+            threads = ln.threads;
+            VDWDF_CUDA_TRY(cudaMemsetAsync(w.queue, 0, sizeof(unsigned int), st));  // work-queue head
+            PairLaunch pl;
+            std::memset(&pl, 0, sizeof(pl));
+            const long long items = pair_items(hs.n_active, ln.jt);
+            if (items > 0xFFFFFFF0LL) return VDWDF_EINVAL;
+            fill_shared(table, d64, d32, ln, w.queue, static_cast<unsigned int>(items + 2), pl.sh);
+            // every item below item_cap writes its partial; any beyond it are added atomically
+            pl.sh.item_E = item_E;
+            pl.sh.item_cap = static_cast<unsigned int>(std::min<long long>(items, item_space));
+            pl.ninst = 1;
+            fill_params(G, w, pl.inst[0]);
+            if (ln.ks0 < 0) {
+                rc = launch_band_choose(pl, w.hist, st);
+                if (rc) return rc;
+            }
+            rc = launch_pair(precision, false, G.skew, ln.threads, pl, ln.nctas, st);
+            if (rc) return rc;
+            rc = launch_reduce_items(pl, st);
+            if (rc) return rc;
+        }
+        VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+        VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hs.guard_trips) return VDWDF_ETIMEOUT;
+        if (out) {
+            std::memset(out, 0, sizeof(*out));
+            fill_result(hs, G, table, out);
+            out->launches = static_cast<int32_t>(g_launches.load() - launches0);
+            out->smem_row0 = precision == VDWDF_FP32 ? (row0 >= 0 ? row0 : hs.band_row0) : -1;
+            out->pair_threads = threads;
+        }
+        return VDWDF_OK;
+    };
+    const int status = run();
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        note_cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+        return status != VDWDF_OK ? status : VDWDF_ECUDA;
     }
-    VDWDF_CUDA_TRY(cudaMemcpyAsync(&hs, w.stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
-    VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
-    if (hs.guard_trips) return VDWDF_ETIMEOUT;
-    if (out) {
-        std::memset(out, 0, sizeof(*out));
-        fill_result(hs, G, table, out);
-        out->launches = static_cast<int32_t>(g_launches.load() - launches0);
-        out->smem_row0 = precision == VDWDF_FP32 ? (row0 >= 0 ? row0 : hs.band_row0) : -1;
-        out->pair_threads = threads;
-    }
-    return VDWDF_OK;
+    return status;
 }
 
 }  // extern "C"

@@ -85,15 +85,17 @@ struct PairParams {
 // Inputs shared by all instances of a launch.
 struct PairShared {
     const double *tab64;  // (nD + 2) x (nd + 2) B-spline coefficients / 36, D outer,
-    const float *tab32;   // then nd + 2 coefficients / 6 of rho(delta) (beyond-table scale)
+    const float *tab32;   // then nd + 2 coefficients / 6 of rho(delta) (beyond-table factor)
     int S;                // row stride (nd + 2)
     int nD, nd;
     double cD, cd;        // tD = r (q_i + q_j) cD,  td = |q_i - q_j|/(q_i + q_j) cd
     double C_asym;
+    double om_rho0;       // 1 - rho(0), rho(0) = phi(Dmax, 0) / phi17(Dmax, 0)
     int ks0, ksn;         // FP32: table rows [ks0, ks0 + ksn) resident in shared memory;
                           // ks0 < 0: ks0 is inst[0].stats->band_row0 (set by launch_band_choose)
     int jtiles_per_item;  // j tiles per work item
-    unsigned int item_limit;  // process only the first item_limit items (autotuning)
+    unsigned int item_limit;  // process at most item_limit items (autotuning) ...
+    unsigned int item_stride; // ... taking every item_stride-th one (1: all in order)
     unsigned int max_iters;   // cap on the work loop of one CTA
     unsigned int *queue;      // work-queue head (zeroed before launch)
     double *item_E;           // energy mode: one partial sum per work item (then reduced in

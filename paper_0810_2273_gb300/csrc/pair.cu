@@ -4,16 +4,21 @@
 // For active points i, j and image vectors L (periodic axes),
 //   r = |r_i - r_j + L|,  D = r (q_i + q_j)/2,  delta = |q_i - q_j|/(q_i + q_j),
 //   phi = bicubic B-spline of the node table at (D, delta)         if D <= Dmax,
-//   phi = rho(delta) phi17,  phi17 = -C / (d1^2 d2^2 (d1^2 + d2^2))   otherwise,
+//   phi = g phi17,  phi17 = -C / (d1^2 d2^2 (d1^2 + d2^2))            otherwise,
 // d1 = q_i r, d2 = q_j r (section 2: the kernel "can be redefined to depend on two
-// quantities D and delta"; Dion eq. 17 for large D, scaled by the cubic spline
-// rho of phi(Dmax, delta) / phi17(Dmax, delta) so that phi is continuous at Dmax).
+// quantities D and delta"; Dion eq. 17 for large D).  The factor
+//   g = rho(delta*) + (1 - rho(0)) (1 - (Dmax/D)^2),  delta* = max(0, 1 - min(d1, d2)/Dmax),
+// with rho the cubic spline of phi(Dmax, delta) / phi17(Dmax, delta), carries the
+// table's departure from eq. 17 at Dmax to larger D along the smaller argument
+// (on which that departure depends once the larger one is big), so phi is
+// continuous at Dmax and tends to eq. 17 as both arguments grow.
 // Energy mode sums each unordered pair once with weight 2 (phi is symmetric in
 // i, j); potential mode gives, per point,
 //   A_i = sum_{j,L} n_j phi,   U_i = n_i sum_{j,L} n_j r dphi/dd1,
 //   r dphi/dd1 = r/2 phi_D + (1 - ds)/(q_i + q_j) phi_ds,  ds = (q_i - q_j)/(q_i + q_j),
-// and beyond the table rho r dphi17/dd1 + phi17 (1 - ds)/(q_i + q_j) rho_ds with
-// r dphi17/dd1 = -2 phi17 (1/q_i + q_i/(q_i^2 + q_j^2)).
+// and beyond the table g r dphi17/dd1 + phi17 r dg/dd1 with
+// r dphi17/dd1 = -2 phi17 (1/q_i + q_i/(q_i^2 + q_j^2)) and
+// r dg/dd1 = (1 - rho(0)) (Dmax/D)^2 r/D - [d1 < d2] rho'(delta*) r/Dmax.
 //
 // Work decomposition: persistent CTAs keep a band of B-spline rows resident in
 // shared memory (FP32 path, staged once; which rows is chosen on the device from
@@ -171,7 +176,8 @@ __device__ __forceinline__ void combine(const R c[4][4], const R wD[4], const R 
 template <typename R>
 struct Consts {
     R cD, cd, tDmax, tDclamp, tdmax, tdclamp, C;
-    int kmax, lmax;  // last cell index along D and delta
+    R iDmax, om_rho0;  // 1/Dmax; 1 - rho(0)
+    int kmax, lmax;    // last cell index along D and delta
 };
 
 template <typename R>
@@ -333,16 +339,42 @@ __device__ __forceinline__ void dist_part(R r2, R qi, R qj, R inv_qi, R qi2, con
         const R qj2 = qj * qj;
         const R s2 = qi2 + qj2;
         const R p17 = -K.C * recip(r4 * r2 * qi2 * qj2 * s2);
-        const R *rc = tb.rho + d.l;
+        // rho at delta* = 1 - min(d1, d2)/Dmax, in delta cells; at or below 0 the
+        // spline's value at delta = 0 with zero slope (its end condition), past the
+        // last node its linear continuation.  No index leaves the rho block.
+        const bool i_small = qi < qj;
+        const R ts0 = (R(1) - r * fmin(qi, qj) * K.iDmax) * K.cd;
+        const bool up = ts0 > R(0);
+        const bool past = ts0 > K.tdmax;
+        const R ts = fmin(fmax(ts0, R(0)), K.tdclamp);
+        R u;
+        int l = floor_split(ts, u);
+        if (sizeof(R) == 8 && l > K.lmax) {
+            l = K.lmax;
+            u = ts - R(l);
+        }
+        R w[4], dw[4];
+        bw<R>(u, w);
+        const R *rc = tb.rho + l;
         const R c0 = __ldg(rc), c1 = __ldg(rc + 1), c2 = __ldg(rc + 2), c3 = __ldg(rc + 3);
-        const R rho = d.wd[0] * c0 + d.wd[1] * c1 + d.wd[2] * c2 + d.wd[3] * c3;
-        phi = rho * p17;
+        R rho = w[0] * c0 + w[1] * c1 + w[2] * c2 + w[3] * c3;
+        R drho = R(0);  // d rho / d delta*, in cells
+        if (POT || past) {
+            bdw<R>(u, dw);
+            drho = up ? dw[1] * (c1 - c0) + dw[2] * (c2 - c0) + dw[3] * (c3 - c0) : R(0);
+            if (past) rho += (ts0 - ts) * drho;
+        }
+        const R Dr = K.tDmax * recip(tD);  // Dmax / D
+        const R Dr2 = Dr * Dr;
+        const R g = rho + K.om_rho0 * (R(1) - Dr2);
+        phi = g * p17;
         if (POT) {
-            const R drho = d.dwd[1] * (c1 - c0) + d.dwd[2] * (c2 - c0) + d.dwd[3] * (c3 - c0);
             const R is2 = recip(s2);
-            const R b = p17 * drho;
-            rd = rho * (R(-2) * p17 * (inv_qi + qi * is2)) + b * d.b1;
-            rd2 = rho * (R(-2) * p17 * (recip(qj) + qj * is2)) + b * d.b2;
+            // (1 - rho(0)) (Dmax/D)^2 r/D with r/D = 2 cD r / tD, and rho'(delta*) r/Dmax
+            const R ramp = K.om_rho0 * Dr2 * R(2) * K.cD * r * recip(tD);
+            const R sl = drho * K.cd * r * K.iDmax;
+            rd = g * (R(-2) * p17 * (inv_qi + qi * is2)) + p17 * (i_small ? ramp - sl : ramp);
+            rd2 = g * (R(-2) * p17 * (recip(qj) + qj * is2)) + p17 * (i_small ? ramp : ramp - sl);
         }
     }
 }
@@ -374,6 +406,8 @@ __device__ void make_consts(const PairShared &sh, Consts<R> &K) {
     }
     K.kmax = sh.nD - 2;
     K.lmax = sh.nd - 2;
+    K.iDmax = static_cast<R>(2.0 * sh.cD / (sh.nD - 1));  // cD = 1/(2 hD), Dmax = (nD - 1) hD
+    K.om_rho0 = static_cast<R>(sh.om_rho0);
 }
 
 template <typename R>
@@ -657,7 +691,9 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
     const float band_lo = static_cast<float>(tb.k0);
     const float band_hi = static_cast<float>(min(tb.k0 + tb.kn - 3, sh.nD - 1));
     __syncthreads();  // the only block barrier: table band and item counts ready
-    const unsigned int n_items = min(s_prefix[pl.ninst], sh.item_limit);
+    // autotuning samples every item_stride-th item (item * stride < the total)
+    const unsigned int stride = max(1u, sh.item_stride);
+    const unsigned int n_items = min((s_prefix[pl.ninst] + stride - 1u) / stride, sh.item_limit);
 
 
     for (unsigned int iter = 0;; ++iter) {
@@ -669,6 +705,7 @@ __global__ void __launch_bounds__(NT, 1) k_pair(const __grid_constant__ PairLaun
         if (lane == 0) item = atomicAdd(sh.queue, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
+        item *= stride;
         int k = 0;
         while (k + 1 < pl.ninst && item >= s_prefix[k + 1]) ++k;
         const PairParams &pp = pl.inst[k];

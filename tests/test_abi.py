@@ -179,7 +179,7 @@ def test_table_roundtrip_from_nodes(tmp_path):
 
 
 def test_total_energy_assembly():
-    """Eq. 3 with PBE exchange leaves E_tot^DFT - E_c^PBE + E_c^LDA + E_c^nl (the
+    """Eq. 3 (host arithmetic behind the C ABI) with PBE exchange leaves E_tot^DFT - E_c^PBE + E_c^LDA + E_c^nl (the
     correction printed as the "needed number" in the paper's sample output); with
     revPBE exchange it adds E_x^revPBE - E_x^PBE on top."""
     import paper_0810_2273_gb300 as V
@@ -190,6 +190,16 @@ def test_total_energy_assembly():
     assert Er == pytest.approx(E + (-1.12) - (-1.10), abs=1e-15)
     with pytest.raises(ValueError):
         V.total_energy_nl(-50.0, semi, 0.05, exchange="lda")
+    # the C entry point refuses a NULL pointer, another exchange and a non-finite sum
+    import ctypes
+    from paper_0810_2273_gb300 import _native
+    lib = _native.load()
+    s = _native.vdwdf_semilocal_result()
+    out = ctypes.c_double(7.0)
+    assert lib.vdwdf_total_energy_nl(-50.0, None, 0.05, 0, ctypes.byref(out)) == -1
+    assert lib.vdwdf_total_energy_nl(-50.0, ctypes.byref(s), 0.05, 2, ctypes.byref(out)) == -1
+    assert lib.vdwdf_total_energy_nl(float("nan"), ctypes.byref(s), 0.05, 0, ctypes.byref(out)) == -1
+    assert out.value == 7.0
 
 
 def test_python_grid_and_tuning_marshalling():

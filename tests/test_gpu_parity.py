@@ -42,7 +42,8 @@ def _relerr(a, b):
 
 
 def test_kernel_eval_matches_oracle(V, dev, gtable, oracle_spline):
-    """Interpolation + asymptote branch in isolation, incl. the last cells and clamping."""
+    """Interpolation + the branch past the table in isolation, incl. the last cells,
+    clamping, and each case of delta* past the table."""
     rng = np.random.default_rng(3)
     n = 20000
     r = rng.uniform(0.0, 25.0, n)
@@ -55,6 +56,11 @@ def test_kernel_eval_matches_oracle(V, dev, gtable, oracle_spline):
     qi[4:8] = [8.0, 9.0, 7.5, 8.0]
     qj[4:8] = [0.01, 0.02, 0.015, 0.0101]
     r[4:8] = [0.5, 0.3, 0.2, 1.0]
+    # past the table: delta* > 0 with either argument the smaller, delta* past the
+    # last delta node, and D of several hundred (delta* clamped at 0)
+    r[8:14] = [10.0, 10.0, 5.0, 5.0, 400.0, 800.0]
+    qi[8:14] = [0.3, 6.0, 0.02, 12.1, 1.9, 0.05]
+    qj[8:14] = [6.0, 0.3, 12.1, 0.02, 0.1, 2.5]
     p_o, rd_o, _ = oracle_spline.kernel(r, qi, qj)
     p64, rd64 = V.kernel_eval(gtable, _t(r, dev), _t(qi, dev), _t(qj, dev), "fp64")
     p32, rd32 = V.kernel_eval(gtable, _t(r, dev), _t(qi, dev), _t(qj, dev), "fp32")

@@ -194,3 +194,39 @@ def test_slab_full_sampled(V, dev, gtable, oracle_mod, oracle_spline):
     e32, _ = V.energy(nc, *_args(wc, gtable), precision="fp32")
     e64, r64 = V.energy(nc, *_args(wc, gtable), precision="fp64")
     assert abs(e32 - e64) < 1e-6 * abs(e64)
+
+
+# the autotuner's candidate shapes (threads, items per warp slot, band rows, band start)
+TUNE_CANDIDATES = [(256, 256, 0, -1), (384, 256, 0, -1), (448, 256, 0, -1), (512, 256, 0, -1),
+                   (1024, 256, 0, -1), (512, 64, 0, -1), (512, 1024, 0, -1), (512, 256, -1, 0)]
+
+
+def test_autotuned_binding_curve(V, dev, gtable):
+    """The autotuner on the largest binding-curve cell returns one of its candidate
+    shapes; the batched graph with that shape, and with the autotuner run by the
+    batched call itself (VDWDF_TUNE_AUTO), gives the default shape's energies to FP32
+    rounding, and binding energies within 0.01 meV of FP64 single calls."""
+    from paper_0810_2273_gb300 import inputs
+    ws = inputs.binding_curve()
+    ns = [_t(w["density"], dev) for w in ws]
+    L = [w["lengths"] for w in ws]
+    per = [w["periodic"] for w in ws]
+    big = int(np.argmax([w["density"].size for w in ws]))
+    tu = V.autotune(ns[big], L[big], per[big], 1e-6, 0.0, gtable, "fp32")
+    shape = (tu["threads"], tu["items_per_sm"], tu["smem_rows"], tu["smem_row0"])
+    assert shape in TUNE_CANDIDATES, shape
+    E_def, _ = V.energy_batched(ns, L, per, 1e-6, 0.0, gtable, "fp32")
+    E_tu, r_tu = V.energy_batched(ns, L, per, 1e-6, 0.0, gtable, "fp32", tuning=tu)
+    E_auto, r_auto = V.energy_batched(ns, L, per, 1e-6, 0.0, gtable, "fp32", tuning={"threads": -1})
+    E_auto2, _ = V.energy_batched(ns, L, per, 1e-6, 0.0, gtable, "fp32", tuning={"threads": -1})  # replay
+    assert r_tu["pair_threads"] == tu["threads"]
+    assert r_auto["pair_threads"] in {c[0] for c in TUNE_CANDIDATES}
+    assert np.array_equal(E_auto, E_auto2)
+    for E in (E_tu, E_auto):
+        assert np.max(np.abs(E - E_def) / np.abs(E_def)) < 1e-6
+    E64 = np.array([V.energy(t, w["lengths"], w["periodic"], 1e-6, 0.0, gtable, "fp64")[0]
+                    for t, w in zip(ns, ws)])
+    for E in (E_tu, E_auto):
+        bind = E[:16] - 2 * E[-1]
+        bind64 = E64[:16] - 2 * E64[-1]
+        assert np.max(np.abs(bind - bind64)) * HARTREE_MEV < 0.01
