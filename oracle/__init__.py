@@ -86,6 +86,8 @@ def load_library(path):
     L.orc_fx_many.argtypes = [_i, _p, _d, _p]
     L.orc_pbe_H_many.restype = _i
     L.orc_pbe_H_many.argtypes = [_i, _p, _p, _p]
+    L.orc_far_tail.restype = _i
+    L.orc_far_tail.argtypes = [_i, _p, _p, _p, _p, _p, _i, _i, _i, _p, _i, _i, _i, _d, _p]
     L.orc_semilocal.restype = _i
     L.orc_semilocal.argtypes = [_i, _p, _p, _p, _p]
     return L
@@ -562,6 +564,13 @@ class Problem:
             out[t] = self.dV * val
         return out
 
+    def far_tail(self):
+        """The far field past the cutoff from eq. (17) and the lattice continuum
+        (see orc_far_tail): T such that E(r_cut -> inf) reads E(r_cut) + T."""
+        cell = np.diag(self.lengths) if self.cell is None else self.cell
+        return far_tail_points(self.i0, self.i1, self.i2, self.na, self.qa, self.dims, cell,
+                               self.periodic, self.rc)
+
     def voxel(self):
         """Rows v_a = M_a / N_a spanning one voxel."""
         cell = np.diag(self.lengths) if self.cell is None else self.cell
@@ -585,6 +594,19 @@ class Problem:
         if rc != 0:
             raise RuntimeError("orc_pair_brute failed (%d)" % rc)
         return 0.5 * self.dV ** 2 * out.value
+
+
+def far_tail_points(i0, i1, i2, n, q, dims, cell, periodic, rc):
+    """orc_far_tail on given points (grid indices), densities and q0 values."""
+    i0, i1, i2 = _i32(i0), _i32(i1), _i32(i2)
+    n, q = _f64(n), _f64(q)
+    cell = _f64(cell).reshape(3, 3)
+    out = ctypes.c_double(0.0)
+    rc_ = lib().orc_far_tail(len(n), _ptr(i0), _ptr(i1), _ptr(i2), _ptr(n), _ptr(q), *map(int, dims),
+                             _ptr(cell), *[int(bool(p)) for p in periodic], float(rc), ctypes.byref(out))
+    if rc_ != 0:
+        raise ValueError("far tail needs two or three periodic axes and rc > 0")
+    return out.value
 
 
 _TABLE_CACHE = {}

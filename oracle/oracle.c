@@ -46,6 +46,12 @@
  *   orc_gradient_T_cell             invariance of E, exact Fourier symbol of
  *                                   the skewed gradient, adjoint identity,
  *                                   brute-force pair counts
+ *   orc_far_tail                    pinned: the radial integrals of the
+ *                                   lattice continuum by adaptive quadrature
+ *                                   (two and three periodic axes, skewed
+ *                                   cells), the exact lattice sum of eq. (17)
+ *                                   beyond r_cut, convergence of E + T with
+ *                                   r_cut against direct sums
  *   orc_phi0_many                   pinned: small-voxel logarithmic law,
  *                                   scale duality phi0(s q; v) = phi0(q; s v),
  *                                   Monte Carlo voxel average, quadrature
@@ -1129,5 +1135,85 @@ int orc_phi0_many(int nD, double hD, int nd, double hd, const double *f,
     }
     free(x);
     free(w);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Far field past the cutoff from the asymptote alone.  Section 7 names      */
+/* image sums sped up by the kernel's asymptotic form as future work;       */
+/* sections 3 and 6.2 repeat the cell until the energy converges.           */
+/* Reading: every pair beyond r_cut takes eq. (17),                          */
+/*   phi17 = -C / (q_i^2 q_j^2 (q_i^2 + q_j^2) r^6),                          */
+/* and the lattice images beyond r_cut are replaced by the lattice's        */
+/* continuum (images per unit area or volume):                              */
+/*   two periodic axes a, b (area A = |a x b|, unit normal e):              */
+/*     sum_{L : |d + L| > rc} g(|d + L|)                                    */
+/*       -> (1/A) int_{rho^2 + z^2 > rc^2} g(sqrt(rho^2 + z^2)) d^2 rho      */
+/*        = (2 pi / A) int_{R}^inf g(r) r dr,  z = d . e,  R = max(rc, |z|), */
+/*     which for g = r^-6 is (2 pi / A) / (4 R^4);                           */
+/*   three periodic axes (volume V): (4 pi / V) int_rc^inf g(r) r^2 dr       */
+/*     = (4 pi / V) / (3 rc^3).                                             */
+/* So the tail is                                                           */
+/*   T = 1/2 dV^2 sum_i sum_j n_i n_j (-C / (q_i^2 q_j^2 (q_i^2 + q_j^2))) K_ij */
+/* over all ordered pairs of active points, i = j included (the self term's */
+/* own images), and E(r_cut -> inf) is read as E(r_cut) + T.  Cells with    */
+/* fewer than two periodic axes have no lattice continuum: returns -1.      */
+/* Points i at fractional index (i0/n0, i1/n1, i2/n2) of the cell (rows of  */
+/* `cell` are the lattice vectors).                                          */
+/* ---------------------------------------------------------------------- */
+int orc_far_tail(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2,
+                 const double *n, const double *q, int n0, int n1, int n2, const double *cell,
+                 int per0, int per1, int per2, double rc, double *out)
+{
+    int per[3] = {per0, per1, per2};
+    int np = (per0 != 0) + (per1 != 0) + (per2 != 0);
+    if (np < 2 || !(rc > 0.0)) return -1;
+    const double C = 12.0 * pow(4.0 * M_PI / 9.0, 3);
+    const double *M0 = cell, *M1 = cell + 3, *M2 = cell + 6;
+    /* volume and, for two periodic axes, the area and unit normal of the plane */
+    double x01[3] = {M0[1] * M1[2] - M0[2] * M1[1], M0[2] * M1[0] - M0[0] * M1[2], M0[0] * M1[1] - M0[1] * M1[0]};
+    double V = fabs(x01[0] * M2[0] + x01[1] * M2[1] + x01[2] * M2[2]);
+    if (!(V > 0.0)) return -1;
+    double e[3] = {0.0, 0.0, 0.0}, A = 0.0;
+    if (np == 2) {
+        /* the two periodic lattice vectors, in axis order */
+        const double *P[3] = {M0, M1, M2};
+        const double *a = NULL, *b = NULL;
+        for (int k = 0; k < 3; ++k)
+            if (per[k]) { if (!a) a = P[k]; else b = P[k]; }
+        double x[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+        A = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (int c = 0; c < 3; ++c) e[c] = x[c] / A;
+    }
+    int N[3] = {n0, n1, n2};
+    double dV = V / ((double)n0 * n1 * n2);
+    double sum = 0.0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : sum)
+    for (int i = 0; i < Na; ++i) {
+        double ri[3];
+        for (int c = 0; c < 3; ++c)
+            ri[c] = i0[i] / (double)N[0] * M0[c] + i1[i] / (double)N[1] * M1[c] + i2[i] / (double)N[2] * M2[c];
+        double ui = q[i] * q[i];
+        double acc = 0.0;
+        for (int j = 0; j < Na; ++j) {
+            double uj = q[j] * q[j];
+            double K;
+            if (np == 3) {
+                K = (4.0 * M_PI / V) / (3.0 * rc * rc * rc);
+            } else {
+                double z = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    double rjc = i0[j] / (double)N[0] * M0[c] + i1[j] / (double)N[1] * M1[c] +
+                                 i2[j] / (double)N[2] * M2[c];
+                    z += (ri[c] - rjc) * e[c];
+                }
+                double R = fabs(z) > rc ? fabs(z) : rc;
+                K = (2.0 * M_PI / A) / (4.0 * R * R * R * R);
+            }
+            acc += n[j] * (-C / (ui * uj * (ui + uj))) * K;
+        }
+        sum += n[i] * acc;
+    }
+    *out = 0.5 * dV * dV * sum;
     return 0;
 }

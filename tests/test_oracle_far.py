@@ -1,0 +1,121 @@
+"""Pins of the oracle's far field past the cutoff (orc_far_tail): eq. (17) for
+every pair beyond r_cut, with the lattice images beyond r_cut replaced by the
+lattice continuum (section 7's asymptote-accelerated image sums; sections 3
+and 6.2 repeat the cell until the energy converges)."""
+import numpy as np
+import pytest
+
+C_ASYM = 12.0 * (4.0 * np.pi / 9.0) ** 3
+
+
+def _pref(n, q, dV):
+    """1/2 dV^2 n_i n_j (-C / (q_i^2 q_j^2 (q_i^2 + q_j^2))) for all ordered pairs."""
+    u = q ** 2
+    return 0.5 * dV ** 2 * np.outer(n, n) * (-C_ASYM / (np.outer(u, u) * (u[:, None] + u[None, :])))
+
+
+def _positions(idx, dims, cell):
+    return (np.asarray(idx, dtype=float) / np.asarray(dims, dtype=float)) @ cell
+
+
+@pytest.mark.parametrize("skew", [False, True])
+def test_two_axis_continuum_is_the_radial_integral(oracle_mod, skew):
+    """Two periodic axes: each pair's factor is (1/A) times the integral of r^-6 over
+    the plane of images outside the cutoff sphere, done here by scipy's adaptive
+    quadrature (in the radius rho within the plane), for pairs whose normal
+    separation |z| is below and above r_cut; the normal comes from the cell."""
+    quad = pytest.importorskip("scipy.integrate").quad
+    dims = (10, 12, 40)
+    cell = np.array([[10.0, 0, 0], [0.0, 12.0, 0], [0, 0, 40.0]])
+    if skew:
+        cell = np.array([[10.0, 0, 0], [5.0, 11.0, 0], [1.5, -2.0, 40.0]])
+    idx = np.array([[0, 0, 0], [3, 4, 5], [7, 1, 31], [2, 9, 18]])
+    n = np.array([0.7, 1.3, 0.4, 0.9])
+    q = np.array([0.5, 1.1, 0.35, 2.0])
+    rc = 9.0
+    e = np.cross(cell[0], cell[1])
+    A = np.linalg.norm(e)
+    e /= A
+    pos = _positions(idx, dims, cell)
+    K = np.zeros((4, 4))
+    for i in range(4):
+        for j in range(4):
+            z = abs(np.dot(pos[i] - pos[j], e))
+            lo = np.sqrt(rc * rc - z * z) if z < rc else 0.0
+            val, _ = quad(lambda rho: 2 * np.pi * rho * (rho * rho + z * z) ** -3, lo, np.inf,
+                          epsabs=0, epsrel=1e-13, limit=200)
+            K[i, j] = val / A
+    dV = abs(np.linalg.det(cell)) / np.prod(dims)
+    ref = float(np.sum(_pref(n, q, dV) * K))
+    got = oracle_mod.far_tail_points(idx[:, 0], idx[:, 1], idx[:, 2], n, q, dims, cell, (1, 1, 0), rc)
+    assert abs(got - ref) < 1e-11 * abs(ref), (got, ref)
+
+
+def test_three_axis_continuum_is_the_radial_integral(oracle_mod):
+    quad = pytest.importorskip("scipy.integrate").quad
+    dims = (8, 8, 8)
+    cell = np.array([[9.0, 0, 0], [1.0, 9.5, 0], [0.5, 0.7, 10.0]])
+    idx = np.array([[0, 0, 0], [3, 4, 5], [7, 1, 2]])
+    n = np.array([0.7, 1.3, 0.4])
+    q = np.array([0.5, 1.1, 0.35])
+    rc = 12.0
+    V = abs(np.linalg.det(cell))
+    val, _ = quad(lambda r: 4 * np.pi * r * r * r ** -6, rc, np.inf, epsabs=0, epsrel=1e-13)
+    ref = float(np.sum(_pref(n, q, V / 512) * (val / V)))
+    got = oracle_mod.far_tail_points(idx[:, 0], idx[:, 1], idx[:, 2], n, q, dims, cell, (1, 1, 1), rc)
+    assert abs(got - ref) < 1e-11 * abs(ref), (got, ref)
+    with pytest.raises(ValueError):   # one periodic axis: no lattice continuum
+        oracle_mod.far_tail_points(idx[:, 0], idx[:, 1], idx[:, 2], n, q, dims, cell, (1, 0, 0), rc)
+
+
+def test_continuum_approaches_the_lattice_sum(oracle_mod):
+    """The continuum stands for the images beyond r_cut.  Against the lattice sum of
+    eq. (17) over those images (summed directly out to 8 r_cut, the continuum past
+    that), for 48 points spread over a skewed cell: within 3 % at r_cut = 10, 20
+    and within 1 % at 40, 80.  (For one pair alone the images just past r_cut make
+    the error jump about with r_cut; over offsets spread across the cell the lattice
+    sum averages to the continuum.)"""
+    dims = (10, 12, 40)
+    cell = np.array([[10.0, 0, 0], [4.0, 11.0, 0], [0, 0, 40.0]])
+    rng = np.random.default_rng(5)
+    K = 48
+    idx = np.stack([rng.integers(0, 10, K), rng.integers(0, 12, K), rng.integers(15, 25, K)], 1)
+    n = rng.uniform(0.3, 1.5, K)
+    q = rng.uniform(0.3, 1.5, K)
+    pos = _positions(idx, dims, cell)
+    A = np.linalg.norm(np.cross(cell[0], cell[1]))
+    dV = abs(np.linalg.det(cell)) / np.prod(dims)
+    P = _pref(n, q, dV)
+    for rc, tol in ((10.0, 0.03), (20.0, 0.03), (40.0, 0.01), (80.0, 0.01)):
+        Rb = 8 * rc
+        M = int(np.ceil(Rb / 9.0)) + 2
+        m0, m1 = np.meshgrid(np.arange(-M, M + 1), np.arange(-M, M + 1), indexing="ij")
+        L = m0.ravel()[:, None] * cell[0] + m1.ravel()[:, None] * cell[1]
+        lat = 0.0
+        for i in range(K):
+            d = pos[i] - pos
+            r = np.linalg.norm(d[:, None, :] + L[None, :, :], axis=2)
+            sel = (r > rc) & (r <= Rb)
+            S = np.sum(np.where(sel, r, np.inf) ** -6, axis=1) + (2 * np.pi / A) / (4 * np.maximum(Rb, np.abs(d[:, 2])) ** 4)
+            lat += float(np.dot(P[i], S))
+        got = oracle_mod.far_tail_points(idx[:, 0], idx[:, 1], idx[:, 2], n, q, dims, cell, (1, 1, 0), rc)
+        assert abs(got - lat) < tol * abs(lat), (rc, got, lat)
+
+
+def test_energy_plus_tail_converges(oracle_mod, oracle_spline):
+    """Coarse periodic monolayer: the oracle's direct sums E(r_cut) and E(r_cut) + T(r_cut)
+    at r_cut = 15, 25, 35 bohr.  The tail takes up what the direct sum still gains
+    past each cutoff: against r_cut = 35, E + T moves by under a tenth of what E moves
+    from 15 and under a hundredth from 25."""
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.xe_monolayer((8, 14, 20))
+    Es, Ts = [], []
+    for rc in (15.0, 25.0, 35.0):
+        P = oracle_mod.Problem(w["density"], w["lengths"], w["periodic"], w["n_cut"], rc, oracle_spline)
+        Es.append(P.energy()["E"])
+        Ts.append(P.far_tail())
+    Es, Ts = np.array(Es), np.array(Ts)
+    assert np.all(Ts < 0) and abs(Ts[0]) > abs(Ts[1]) > abs(Ts[2])
+    d_direct = abs(Es[0] - Es[2]), abs(Es[1] - Es[2])
+    d_tail = abs(Es[0] + Ts[0] - Es[2] - Ts[2]), abs(Es[1] + Ts[1] - Es[2] - Ts[2])
+    assert d_tail[0] < 0.1 * d_direct[0] and d_tail[1] < 0.01 * d_direct[1], (d_direct, d_tail)

@@ -14,6 +14,7 @@ import pytest
 from conftest import ROOT
 
 import test_oracle_cell as CELL
+import test_oracle_far as FAR
 import test_oracle_kernel as K
 import test_oracle_phi0 as PHI0
 import test_oracle_q0 as Q
@@ -104,6 +105,12 @@ MUTATIONS = [
      "if (d1 < d2 && dstar > 0.0) rdg -= drho * r / Dmax;",
      "if (d1 < d2 && dstar > 0.0) rdg += drho * r / Dmax;", 0,
      SPL.test_kernel_branches, ("oracle_mod", "oracle_spline")),
+    ("far tail: the normal separation |z| ignored (R = r_cut for every pair)",
+     "double R = fabs(z) > rc ? fabs(z) : rc;", "double R = rc;", 0,
+     FAR.test_two_axis_continuum_is_the_radial_integral, ("oracle_mod", False)),
+    ("far tail: 2 pi / A written pi / A",
+     "K = (2.0 * M_PI / A) / (4.0 * R * R * R * R);", "K = (M_PI / A) / (4.0 * R * R * R * R);", 0,
+     FAR.test_continuum_approaches_the_lattice_sum, ("oracle_mod",)),
     ("PBE correlation: A^2 t^4 written A t^4",
      "double den = 1.0 + A * t2 + A * A * t2 * t2;", "double den = 1.0 + A * t2 + A * t2 * t2;", 0,
      SEMI.test_pbe_gradient_correction_limits, ("oracle_mod",)),
