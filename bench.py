@@ -7,6 +7,13 @@ accumulation.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+Besides the headline step, the line carries one entry per standard workload
+under "workloads" (pairs/s, fraction of the FP32 lane peak, the FP64 path's
+rate and the FP32/FP64 ratio), timed after the headline steps: the Kr dimer
+(FP64 E), the open 24-atom molecule (FP32 E + v), the 18-cell binding curve
+(batched CUDA graph, default and autotuned launch shapes) and the metal slab
+with a flake (FP32 E + v).  --no-workloads skips them.
+
 --impl reference times the FP64 CPU oracle on the host cores on bounded samples of
 the same workload (each step: A_i, U_i of a random sample of active points).
 Multi-GPU (torchrun): every rank runs its own replica (weak scaling); rank 0
@@ -35,6 +42,9 @@ WORKLOAD = "xe_monolayer 48x84x120 periodic-xy r_cut=20 n_cut=1e-6 (E_nl + v_nl)
 # chain rule for both d1 and d2, accumulation on both sides); shared-memory loads
 # and MUFU operations are not in this count.
 OPS_PER_PAIR_EV = 62
+# The same count for the energy-only pass: 71 operations per unordered pair
+# (no derivative weights, no chain rule, one accumulation side), 35.5 per ordered pair.
+OPS_PER_PAIR_E = 35.5
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 
@@ -199,10 +209,17 @@ def run_gpu(args):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e = float(np.mean(e2e_ms))
 
-    # FP64 path on the same workload, energy + potential once (outside the timed steps)
-    t0 = time.perf_counter()
+    # FP64 path on the same workload, energy + potential once (outside the timed
+    # steps), after a warm-up call of the FP64 kernels on a small grid of the same cell
+    ws_small = inputs.xe_monolayer((12, 21, 30))
+    V.potential(torch.from_numpy(ws_small["density"]).to(dev), *a, precision="fp64")
+    torch.cuda.synchronize()
+    e64a, e64b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e64a.record()
     E64, _, r64 = V.potential(n, *a, precision="fp64")
-    fp64_s = time.perf_counter() - t0
+    e64b.record()
+    torch.cuda.synchronize()
+    fp64_s = 1e-3 * e64a.elapsed_time(e64b)
 
     # the semilocal terms of eq. 3 on the same density (outside the timed steps; the
     # call's own CUDA events, L2 flushed before each call)
@@ -223,7 +240,8 @@ def run_gpu(args):
     value = total_pairs / (ms * 1e-3)
     sm_mhz = clocks["sm_mhz"] if clocks else None
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    clk = 2070.0
+    clk, clk_basis = (sm_mhz, "median SM clock sampled during the timed steps") if sm_mhz else \
+        (2070.0, "maximum SM clock (no clock samples)")
     peak = sms * FP32_LANES_PER_SM * clk * 1e6 / 1e12
     pms = float(np.mean(pair_ms))
     achieved = OPS_PER_PAIR_EV * pairs / (pms * 1e-3) / 1e12
@@ -237,24 +255,26 @@ def run_gpu(args):
         except (OSError, ValueError):
             pass
     cpu = oracle_sample(w, T, seconds=args.cpu_seconds)
+    wl = None if args.no_workloads else run_workloads(V, inputs, T, dev, flush, sms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": list(n.shape), "n_active": results[-1][1]["n_active"],
-                   "pairs_per_step": pairs, "precision": "fp32 pairs, fp64 accumulation",
-                   "l2": "flushed (256 MB write) between timed steps",
-                   "parallelism": "replicas" if ws > 1 else "single"},
+        "config": config_keys(ws),
+        "workload_stats": {"n_active": results[-1][1]["n_active"], "pairs_per_step": pairs,
+                           "precision": "fp32 pairs, fp64 accumulation"},
         "E_hartree": results[-1][0],
         "fp64_path": {"value": pairs / fp64_s, "unit": UNIT, "E_hartree": E64,
                       "rel_err_fp32_vs_fp64": abs(results[-1][0] - E64) / abs(E64),
-                      "seconds": fp64_s},
+                      "seconds": fp64_s, "fp32_over_fp64": value / (pairs / fp64_s),
+                      "timing": "CUDA events around one call, after an FP64 warm-up call on a 12x21x30 grid"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T fp32-lane-ops/s",
                      "frac": achieved / peak, "traffic": prof_traffic,
                      "kernel": "k_pair<float, potential, %d>" % results[-1][1]["pair_threads"],
                      "ms_per_launch": pms,
                      "ops_per_pair": OPS_PER_PAIR_EV,
-                     "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (max SM clock)" % (sms, FP32_LANES_PER_SM, clk)},
+                     "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (%s)" % (sms, FP32_LANES_PER_SM, clk,
+                                                                                clk_basis)},
         "semilocal": {"ms_per_call": semi_t, "points": int(n.numel()),
                       "points_per_s": n.numel() / (semi_t * 1e-3),
                       "hbm_gbs": 8.0 * n.numel() / (semi_t * 1e-3) / 1e9,
@@ -267,10 +287,129 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "wall_s_timed": wall,
+        "workloads": wl,
     }
     print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_workloads(V, inputs, T, dev, flush, sms):
+    """Every standard workload in the launch configuration the library uses by
+    default: pair interactions/s from the pair kernel's CUDA-event time (the
+    call's ms_pairs; for the batched graph the replay's whole time), L2 flushed
+    before each timed call, the fraction of the FP32 lane peak at the SM clock
+    sampled during these runs, and the FP64 path on the same input."""
+    import torch
+
+    def to_dev(wk):
+        return torch.from_numpy(wk["density"]).to(dev)
+
+    def args_of(wk):
+        return (wk.get("cell", wk["lengths"]), wk["periodic"], wk["n_cut"], wk["r_cut"], T)
+
+    def timed(fn, reps, warm=True):
+        if warm:
+            fn()                            # warm-up (and, for batches, the graph recording)
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            out.append(fn())
+        ms = float(np.mean([r[1]["ms_pairs"] for r in out]))
+        return ms, out[-1][1]["pairs"], out[-1][0], out[-1][1]
+
+    def energy(n, a, prec):
+        return lambda: V.energy(n, *a, precision=prec)
+
+    def potential(n, a, prec):
+        def f():
+            E, _, r = V.potential(n, *a, precision=prec)
+            return E, r
+        return f
+
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    raw = {}
+    # kr_dimer: FP64 E (and FP32 E for the ratio)
+    w0 = inputs.kr_dimer()
+    n0, a0 = to_dev(w0), args_of(w0)
+    raw["kr_dimer"] = dict(workload="kr_dimer 24x18x18 open, E_nl", mode="energy",
+                           f32=timed(energy(n0, a0, "fp32"), 5), f64=timed(energy(n0, a0, "fp64"), 5))
+    # molecule24: FP32 E + v, FP64 E + v once
+    w2 = inputs.molecule24()
+    n2, a2 = to_dev(w2), args_of(w2)
+    raw["molecule24"] = dict(workload="molecule24 64^3 open, E_nl + v_nl", mode="potential",
+                             f32=timed(potential(n2, a2, "fp32"), 3), f64=timed(potential(n2, a2, "fp64"), 1, warm=False))
+    # binding curve: 18 cells in one recorded graph (FP32 E), default and autotuned shapes
+    ws3 = inputs.binding_curve()
+    ns3 = [to_dev(x) for x in ws3]
+    L3, P3 = [x["lengths"] for x in ws3], [x["periodic"] for x in ws3]
+
+    def batched(prec, tu):
+        def f():
+            E, r = V.energy_batched(ns3, L3, P3, 1e-6, 0.0, T, prec, tuning=tu)
+            return float(np.sum(E)), r
+        return f
+    big = int(np.argmax([x["density"].size for x in ws3]))
+    t_tune = time.perf_counter()
+    tuned = V.autotune(ns3[big], L3[big], P3[big], 1e-6, 0.0, T, "fp32")
+    t_tune = time.perf_counter() - t_tune
+    raw["binding_curve"] = dict(workload="binding_curve 18 open cells (32x24x24 .. 64x32x32) in one graph, E_nl",
+                                mode="energy", f32=timed(batched("fp32", None), 5),
+                                f32_auto=timed(batched("fp32", {"threads": -1}), 5),
+                                f64=timed(batched("fp64", None), 2))
+    # slab_adsorbate: FP32 E + v at full size; the FP64 ratio on its 64x56x100 regrid
+    w4 = inputs.slab_adsorbate()
+    n4, a4 = to_dev(w4), args_of(w4)
+    f32_full = timed(potential(n4, a4, "fp32"), 2)
+    del n4
+    w4c = inputs.slab_adsorbate((64, 56, 100))
+    n4c, a4c = to_dev(w4c), args_of(w4c)
+    raw["slab_adsorbate"] = dict(workload="slab_adsorbate 128x112x200 periodic-xy r_cut=20, E_nl + v_nl",
+                                 mode="potential", f32=f32_full, f32_regrid=timed(potential(n4c, a4c, "fp32"), 2),
+                                 f64_regrid=timed(potential(n4c, a4c, "fp64"), 1, warm=False))
+    clocks = sampler.stop()
+    clk = clocks["sm_mhz"] if clocks else 2070.0
+    peak = sms * FP32_LANES_PER_SM * clk * 1e6 / 1e12
+
+    def rate(t, ops):
+        ms, pairs, E, r = t
+        d = {"pairs_per_s": pairs / (ms * 1e-3), "ms_pairs": ms, "pairs": int(pairs), "E_hartree": E,
+             "pair_threads": r.get("pair_threads")}
+        if ops:
+            d["frac"] = ops * pairs / (ms * 1e-3) / 1e12 / peak
+        return d
+
+    out = {"clocks": clocks, "peak_T_lane_ops": peak,
+           "note": "frac: FP32 lane operations (62 per ordered pair for E + v, 35.5 for E) over "
+                   "%d SMs x %d lanes x the sampled SM clock" % (sms, FP32_LANES_PER_SM)}
+    for key, d in raw.items():
+        ops = OPS_PER_PAIR_EV if d["mode"] == "potential" else OPS_PER_PAIR_E
+        e = {"workload": d["workload"], "fp32": rate(d["f32"], ops)}
+        if "f64" in d:
+            e["fp64"] = rate(d["f64"], None)
+            e["fp32_over_fp64"] = e["fp32"]["pairs_per_s"] / e["fp64"]["pairs_per_s"]
+            e["rel_err_fp32_vs_fp64"] = abs(d["f32"][2] - d["f64"][2]) / abs(d["f64"][2])
+        if "f32_auto" in d:
+            e["fp32_autotuned"] = rate(d["f32_auto"], ops)
+            e["autotune"] = {"largest_cell_choice": tuned, "seconds": t_tune,
+                             "batched_auto_over_default": d["f32_auto"][0] and d["f32"][0] / d["f32_auto"][0]}
+        if "f64_regrid" in d:
+            e["fp32_64x56x100"] = rate(d["f32_regrid"], ops)
+            e["fp64_64x56x100"] = rate(d["f64_regrid"], None)
+            e["fp32_over_fp64"] = e["fp32_64x56x100"]["pairs_per_s"] / e["fp64_64x56x100"]["pairs_per_s"]
+            e["rel_err_fp32_vs_fp64"] = abs(d["f32_regrid"][2] - d["f64_regrid"][2]) / abs(d["f64_regrid"][2])
+            e["fp64_note"] = "the FP64 E + v pass at full size takes about 7 min; ratio on the 64x56x100 regrid"
+        out[key] = e
+    return out
+
+
+def config_keys(ws):
+    """The workload the line is quoted on, the same in both arms."""
+    return {"workload": WORKLOAD, "grid": [48, 84, 120],
+            "l2": "flushed (256 MB write) between timed GPU steps",
+            "parallelism": "replicas" if ws > 1 else "single"}
 
 
 def kernel_hash():
@@ -345,7 +484,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_time / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "data": "synthetic", "config": config_keys(ws),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -360,6 +499,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-points", type=int, default=48)
+    ap.add_argument("--no-workloads", action="store_true", help="skip the per-workload entries")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3

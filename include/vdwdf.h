@@ -315,6 +315,42 @@ int vdwdf_total_energy_nl(double E_tot_dft, const vdwdf_semilocal_result *semi, 
                           double *E_out);
 
 /* --------------------------------------------------------------------- */
+/* Far field past the cutoff (section 7: image sums sped up by the kernel's */
+/* asymptotic form, named there as future work)                           */
+/* --------------------------------------------------------------------- */
+
+typedef struct {
+    double T;            /* the far field past r_cut, Hartree: E(r_cut -> inf) reads E + T */
+    int64_t n_active;    /* grid points with n >= n_cut                          */
+    int32_t nodes;       /* nodes of the quadrature in ln s                       */
+    int32_t planes;      /* grid planes along the non-periodic axis (1: three periodic axes) */
+    float ms;            /* device time of the call                               */
+    int32_t launches;    /* kernels launched by the call                          */
+} vdwdf_tail_result;
+
+/* The pair sum's far field beyond r_cut, from eq. (17) alone (sections 3 and
+ * 6.2 repeat the cell until the energy converges; section 7 proposes the
+ * asymptote for the far images).  Reading: every pair beyond r_cut takes
+ *   phi17 = -C / (q_i^2 q_j^2 (q_i^2 + q_j^2) r^6),  C = 12 (4 pi / 9)^3,
+ * and the lattice images beyond r_cut are replaced by the lattice continuum:
+ *   T = 1/2 dV^2 sum_{i,j active} n_i n_j (-C / (q_i^2 q_j^2 (q_i^2 + q_j^2))) K_ij,
+ *   K_ij = (2 pi / A) / (4 max(r_cut, |z_ij|)^4)   two periodic axes (A the
+ *          area of the periodic plane, z_ij the separation normal to it),
+ *   K    = (4 pi / V) / (3 r_cut^3)                 three periodic axes.
+ * E(r_cut) + T estimates the fully converged periodic energy; the estimate
+ * is exact for the continuum of images and tends to the lattice sum of eq.
+ * (17) as r_cut grows.  The library evaluates T in FP64, with
+ * 1/(a + b) = int exp(-(a + b) s) ds by the trapezoidal rule in ln s
+ * (relative error below 1e-15), from per-plane sums over the grid.
+ * grid as in vdwdf_energy with exactly two or three periodic axes; grad_dev
+ * as in vdwdf_q0; r_cut > 0.  Synchronises the stream.
+ * Errors: VDWDF_EINVAL (bad argument, r_cut <= 0), VDWDF_EUNSUPPORTED (fewer
+ * than two periodic axes, or a q0 range needing more than 4096 nodes),
+ * VDWDF_ECUDA, VDWDF_EALLOC. */
+int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
+                   double r_cut, vdwdf_tail_result *out, void *cuda_stream);
+
+/* --------------------------------------------------------------------- */
 /* Voxel-averaged diagonal (the "phi0" step of the paper's Appendix A      */
 /* output; the paper does not describe its method)                        */
 /* --------------------------------------------------------------------- */

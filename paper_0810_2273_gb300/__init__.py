@@ -18,7 +18,7 @@ from ._native import (VDWDF_FP32, VDWDF_FP64, VdwdfError, vdwdf_diag_result, vdw
                       vdwdf_semilocal_result, vdwdf_tuning)
 
 __all__ = ["Table", "grid", "energy", "energy_noalloc", "potential", "energy_batched", "q0", "kernel_eval",
-           "semilocal", "total_energy_nl", "phi0_eval", "diag_voxel", "diag_voxel_potential",
+           "semilocal", "total_energy_nl", "far_tail", "phi0_eval", "diag_voxel", "diag_voxel_potential",
            "autotune", "launch_count", "NonlocalEnergy", "nonlocal_energy", "VdwdfError",
            "VDWDF_FP32", "VDWDF_FP64"]
 
@@ -209,6 +209,25 @@ def semilocal(n, lengths, periodic, grad=None, gradient="fd"):
                                  ctypes.c_void_p(grad.data_ptr()) if grad is not None else None,
                                  ctypes.byref(res), _stream(n))
     _native.check(st, "vdwdf_semilocal")
+    return res.as_dict()
+
+
+def far_tail(n, lengths, periodic, n_cut, r_cut, grad=None, gradient="fd"):
+    """The far field past r_cut from eq. (17) and the lattice continuum
+    (vdwdf_far_tail): E(r_cut -> inf) reads E(r_cut) + T.  Returns the result dict
+    (T in Hartree)."""
+    _check_tensor(n, "n")
+    if grad is not None:
+        _check_tensor(grad, "grad")
+    torch = _torch()
+    lib = _native.load()
+    g = grid(lengths, n.shape, periodic, gradient)
+    res = _native.vdwdf_tail_result()
+    with torch.cuda.device(n.device):
+        st = lib.vdwdf_far_tail(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()),
+                                ctypes.c_void_p(grad.data_ptr()) if grad is not None else None,
+                                float(n_cut), float(r_cut), ctypes.byref(res), _stream(n))
+    _native.check(st, "vdwdf_far_tail")
     return res.as_dict()
 
 

@@ -51,6 +51,14 @@ class vdwdf_diag_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class vdwdf_tail_result(ctypes.Structure):
+    _fields_ = [("T", _c_d), ("n_active", _c_i64), ("nodes", _c_i32), ("planes", _c_i32),
+                ("ms", ctypes.c_float), ("launches", _c_i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class vdwdf_tuning(ctypes.Structure):
     _fields_ = [("threads", _c_i32), ("items_per_sm", _c_i32), ("smem_rows", _c_i32),
                 ("smem_row0", _c_i32)]
@@ -86,6 +94,8 @@ PROTOTYPES = {
     "vdwdf_autotune": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_d, _c_d, _c_p, _c_i,
                               ctypes.POINTER(vdwdf_tuning), _c_p]),
     "vdwdf_total_energy_nl": (_c_i, [_c_d, ctypes.POINTER(vdwdf_semilocal_result), _c_d, _c_i, _c_p]),
+    "vdwdf_far_tail": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_d, _c_d, ctypes.POINTER(vdwdf_tail_result),
+                              _c_p]),
     "vdwdf_strerror": (ctypes.c_char_p, [_c_i]),
     "vdwdf_version": (_c_i, []),
     "vdwdf_launch_count": (_c_i64, []),

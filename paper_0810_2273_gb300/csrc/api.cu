@@ -476,6 +476,24 @@ int ctas_per_sm(int precision, bool pot, int threads, int ksn, int S) {
     return std::max(1, 1024 / threads);
 }
 
+// The pair loop's constants in precision R from the FP64 ones of sh.
+template <typename R>
+void fill_loop_consts(const PairShared &sh, LoopConsts<R> &k) {
+    k.cD = static_cast<R>(sh.cD);
+    k.cd = static_cast<R>(sh.cd);
+    k.C = static_cast<R>(sh.C_asym);
+    k.tDmax = static_cast<R>(sh.nD - 1);
+    k.tdmax = static_cast<R>(sh.nd - 1);
+    // FP32: the largest float below nD - 1 (nd - 1), so that the last cell is reached
+    // with t < 1; FP64 clamps to the node and moves the last cell's index down instead
+    k.tDclamp = sizeof(R) == 4 ? static_cast<R>(std::nextafter(static_cast<float>(sh.nD - 1), 0.0f)) : k.tDmax;
+    k.tdclamp = sizeof(R) == 4 ? static_cast<R>(std::nextafter(static_cast<float>(sh.nd - 1), 0.0f)) : k.tdmax;
+    k.iDmax = static_cast<R>(2.0 * sh.cD / (sh.nD - 1));  // cD = 1/(2 hD), Dmax = (nD - 1) hD
+    k.om_rho0 = static_cast<R>(sh.om_rho0);
+    k.kmax = sh.nD - 2;
+    k.lmax = sh.nd - 2;
+}
+
 void fill_shared(const vdwdf_table *t, const double *d64, const float *d32, const Launch &ln,
                  unsigned int *queue, unsigned int max_iters, PairShared &sh) {
     sh.tab64 = d64;
@@ -491,6 +509,8 @@ void fill_shared(const vdwdf_table *t, const double *d64, const float *d32, cons
     const double Dm = t->Dmax, Dm2 = Dm * Dm;
     const double p17 = -sh.C_asym / (2.0 * Dm2 * Dm2 * Dm2);
     sh.om_rho0 = 1.0 - t->nodes[static_cast<size_t>(t->nD - 1) * t->nd] / p17;
+    fill_loop_consts(sh, sh.k32);
+    fill_loop_consts(sh, sh.k64);
     sh.ks0 = ln.ks0;
     sh.ksn = ln.ksn;
     sh.jtiles_per_item = ln.jt;
@@ -1351,6 +1371,114 @@ int autotune_one(const Geom &G, const double *n_dev, double n_cut, const vdwdf_t
 }  // namespace vdwdf
 
 extern "C" {
+
+int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
+                   double r_cut, vdwdf_tail_result *out, void *cuda_stream) {
+    using namespace vdwdf;
+    Geom G;
+    int rc = check_grid(grid, G);
+    if (rc) return rc;
+    if (!n_dev || !out) return VDWDF_EINVAL;
+    if (!(n_cut > 0.0) || !std::isfinite(n_cut) || !(r_cut > 0.0) || !std::isfinite(r_cut)) return VDWDF_EINVAL;
+    const int nper = (G.per[0] != 0) + (G.per[1] != 0) + (G.per[2] != 0);
+    if (nper < 2) return VDWDF_EUNSUPPORTED;
+    // geometry: the cell's volume; with two periodic axes the area of their plane, its
+    // unit normal e and the spacing dz = |M_ax . e| / N_ax of the planes along the
+    // third axis ax
+    double M[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) M[a][c] = grid->cell[a][c];
+    auto cross = [](const double *x, const double *y, double *z) {
+        z[0] = x[1] * y[2] - x[2] * y[1];
+        z[1] = x[2] * y[0] - x[0] * y[2];
+        z[2] = x[0] * y[1] - x[1] * y[0];
+    };
+    double x01[3];
+    cross(M[0], M[1], x01);
+    const double V = std::fabs(x01[0] * M[2][0] + x01[1] * M[2][1] + x01[2] * M[2][2]);
+    int ax = 0, np = 1;
+    double dz = 0.0, c2 = 0.0, c3 = 0.0;
+    if (nper == 2) {
+        ax = G.per[0] == 0 ? 0 : (G.per[1] == 0 ? 1 : 2);
+        const int a = ax == 0 ? 1 : 0, b = ax == 2 ? 1 : 2;
+        double e[3];
+        cross(M[a], M[b], e);
+        const double A = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        dz = std::fabs(M[ax][0] * e[0] + M[ax][1] * e[1] + M[ax][2] * e[2]) / A / G.dims[ax];
+        np = G.dims[ax];
+        c2 = (2.0 * kPi / A) / 4.0;
+    } else {
+        c3 = (4.0 * kPi / V) / (3.0 * r_cut * r_cut * r_cut);
+    }
+    constexpr int kMaxNodes = 4096;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const long long launches0 = g_launches.load();
+    Carve cv;
+    const size_t o_q0 = cv.take<double>(G.N), o_mm = cv.take<unsigned long long>(3),
+                 o_F = cv.take<double>(static_cast<size_t>(kMaxNodes) * np), o_Tk = cv.take<double>(kMaxNodes),
+                 o_out = cv.take<double>(1);
+    const size_t o_gsp = G.spectral ? cv.take<double>(3 * G.N) : 0,
+                 o_coef = G.spectral ? cv.take<double>(G.dims[0] + G.dims[1] + G.dims[2]) : 0;
+    unsigned char *base = nullptr;
+    if (scratch_malloc_async(reinterpret_cast<void **>(&base), cv.off, st) != cudaSuccess) return VDWDF_EALLOC;
+    double *q0 = reinterpret_cast<double *>(base + o_q0);
+    unsigned long long *mm = reinterpret_cast<unsigned long long *>(base + o_mm);
+    double *F = reinterpret_cast<double *>(base + o_F), *Tk = reinterpret_cast<double *>(base + o_Tk);
+    double *Tout = reinterpret_cast<double *>(base + o_out);
+    double *gsp = G.spectral ? reinterpret_cast<double *>(base + o_gsp) : nullptr;
+    double *coef = G.spectral ? reinterpret_cast<double *>(base + o_coef) : nullptr;
+    Timer tm;
+    unsigned long long hmm[3] = {0, 0, 0};
+    double T = 0.0;
+    int nodes = 0;
+    auto body = [&]() -> int {
+        tm.mark(0, st);
+        const double *g_use = nullptr;
+        int r = q0_gradient(G, n_dev, grad_dev, gsp, coef, &g_use, st);
+        if (r) return r;
+        r = launch_grad_q0(G.dims, G.am, n_dev, g_use, q0, nullptr, nullptr, st);
+        if (r) return r;
+        VDWDF_CUDA_TRY(cudaMemsetAsync(mm, 0xFF, sizeof(unsigned long long), st));
+        VDWDF_CUDA_TRY(cudaMemsetAsync(mm + 1, 0, 2 * sizeof(unsigned long long), st));
+        r = launch_diag_range(G.N, n_dev, q0, n_cut, mm, st);
+        if (r) return r;
+        VDWDF_CUDA_TRY(cudaMemcpyAsync(hmm, mm, sizeof(hmm), cudaMemcpyDeviceToHost, st));
+        VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hmm[2] == 0) return VDWDF_OK;
+        double qmin, qmax;
+        std::memcpy(&qmin, &hmm[0], 8);
+        std::memcpy(&qmax, &hmm[1], 8);
+        if (!(qmin > 0.0) || !std::isfinite(qmax)) return VDWDF_EINVAL;
+        // nodes x_k = x0 + k hx of int_0^inf e^{-c s} ds = int e^{-c e^x} e^x dx over
+        // c = u_i + u_j in [2 umin, 2 umax]: the part below x0 is under 1e-17 of 1/c
+        // for every c, e^{-c e^x} has fallen below e^-45 past the last node, and the
+        // step's error is about exp(-pi^2 / hx) = 4e-22
+        const double umin = qmin * qmin, umax = qmax * qmax, hx = 0.2;
+        const double x0 = std::log(1e-17 / (2.0 * umax)), x1 = std::log(45.0 / (2.0 * umin));
+        nodes = static_cast<int>(std::ceil((x1 - x0) / hx)) + 1;
+        if (nodes > kMaxNodes) return VDWDF_EUNSUPPORTED;
+        const double Cas = 12.0 * std::pow(4.0 * kPi / 9.0, 3);
+        r = launch_far_tail(G.dims, ax, np, n_dev, q0, n_cut, x0, hx, nodes, dz, r_cut, c2, c3,
+                            -0.5 * G.dV * G.dV * Cas, F, Tk, Tout, st);
+        if (r) return r;
+        tm.mark(1, st);
+        VDWDF_CUDA_TRY(cudaMemcpyAsync(&T, Tout, sizeof(double), cudaMemcpyDeviceToHost, st));
+        VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+        return VDWDF_OK;
+    };
+    rc = body();
+    cudaFreeAsync(base, st);
+    if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
+    if (rc) return rc;
+    std::memset(out, 0, sizeof(*out));
+    out->T = T;
+    out->n_active = static_cast<int64_t>(hmm[2]);
+    out->nodes = nodes;
+    out->planes = np;
+    if (hmm[2]) out->ms = tm.ms(0, 1);
+    out->launches = static_cast<int32_t>(g_launches.load() - launches0);
+    return VDWDF_OK;
+}
 
 int vdwdf_diag_voxel(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
                      const vdwdf_table *table, int nphi0, vdwdf_diag_result *out, void *cuda_stream) {

@@ -82,6 +82,19 @@ struct PairParams {
     Stats *stats;
 };
 
+// The pair loop's constants, computed on the host in the loop's own precision,
+// so that the device reads them as they are (no conversion or division in the
+// kernel that the compiler could repeat inside the loop).
+template <typename R>
+struct LoopConsts {
+    R cD, cd;            // cells per unit of D (times 1/2: tD = r (q_i + q_j) cD) and of delta
+    R tDmax, tDclamp;    // nD - 1, and the largest R below it (FP32) or nD - 1 (FP64)
+    R tdmax, tdclamp;    // the same along delta
+    R C;                 // 12 (4 pi / 9)^3 of eq. (17)
+    R iDmax, om_rho0;    // 1 / Dmax; 1 - rho(0)
+    int kmax, lmax;      // last cell index along D and delta
+};
+
 // Inputs shared by all instances of a launch.
 struct PairShared {
     const double *tab64;  // (nD + 2) x (nd + 2) B-spline coefficients / 36, D outer,
@@ -91,6 +104,8 @@ struct PairShared {
     double cD, cd;        // tD = r (q_i + q_j) cD,  td = |q_i - q_j|/(q_i + q_j) cd
     double C_asym;
     double om_rho0;       // 1 - rho(0), rho(0) = phi(Dmax, 0) / phi17(Dmax, 0)
+    LoopConsts<float> k32;   // the same constants for the FP32 ...
+    LoopConsts<double> k64;  // ... and the FP64 pair loop
     int ks0, ksn;         // FP32: table rows [ks0, ks0 + ksn) resident in shared memory;
                           // ks0 < 0: ks0 is inst[0].stats->band_row0 (set by launch_band_choose)
     int jtiles_per_item;  // j tiles per work item
@@ -187,6 +202,14 @@ int launch_diag_sum(long long N, const double *n, const double *q0, double n_cut
                     int nq, double lnq0, double dlnq, double *part, double *sums, cudaStream_t st);
 int launch_diag_AU(long long N, const double *n, const double *q0, double n_cut, const double *tab, int nq,
                    double lnq0, double dlnq, double phi00, int *slot, double *A, double *U, cudaStream_t st);
+// The far field past the cutoff (tail.cu): planes of grid axis ax (np of them, or
+// np = 1 for the whole cell), nodes of the trapezoidal rule x_k = x0 + k hx in
+// ln s; F (nodes x np) and Tk (nodes) scratch; out = scale sum_k hx e^{x_k} Tk[k]
+// with Tk[k] = sum_{p,p'} K(p, p') F_k(p) F_k(p'),
+// K = c2 / max(rc, |p - p'| dz)^4 (np > 1) or c3 (np = 1).
+int launch_far_tail(const int dims[3], int ax, int np, const double *n, const double *q0, double n_cut,
+                    double x0, double hx, int nodes, double dz, double rc, double c2, double c3, double scale,
+                    double *F, double *Tk, double *out, cudaStream_t st);
 int launch_kernel_eval(int precision, const PairShared &sh, int64_t npts, const double *r,
                        const double *qi, const double *qj, double *phi, double *rdphi,
                        cudaStream_t st);

@@ -166,6 +166,30 @@ def test_table_build_matches_oracle_quadrature(oracle_mod):
     assert T.info() == (13, 30.0, 8)
 
 
+def test_standard_table_at_random_nodes(oracle_mod):
+    """The standard 400 x 200 build (0 <= D <= 30, quadrature level 1) against the
+    oracle's reference quadrature at 240 random nodes of rows 1..399 (the spot-point
+    pin of the node table, within 1e-9 of max|phi|), and its row 0 rule."""
+    import os
+    from paper_0810_2273_gb300 import Table
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), ".cache",
+                        "vdwdf_table_400x200_D30_q1.npz")
+    T = Table.load(path) if os.path.exists(path) else Table.build(400, 30.0, 200, 1)
+    nodes = T.nodes
+    assert nodes.shape == (400, 200)
+    rng = np.random.default_rng(2024)
+    k = rng.integers(1, 400, 240)
+    l = rng.integers(0, 200, 240)
+    D = 30.0 * k / 399
+    dl = l / 200.0
+    ref = oracle_mod.phi(D * (1 + dl), D * (1 - dl), oracle_mod.QUAD_REFERENCE)
+    scale = np.max(np.abs(nodes))
+    # the two quadratures differ by up to 2e-10 absolute, at D < 1 where the
+    # integrand's switch h(a/d) sits at small a; the bound is 1e-9 max|phi|
+    assert np.max(np.abs(nodes[k, l] - ref)) < 1e-9 * scale, np.max(np.abs(nodes[k, l] - ref))
+    assert np.allclose(nodes[0], (4 * nodes[1] - nodes[2]) / 3, rtol=1e-15, atol=0)
+
+
 def test_table_roundtrip_from_nodes(tmp_path):
     from paper_0810_2273_gb300 import Table
     rng = np.random.default_rng(0)

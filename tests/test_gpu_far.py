@@ -1,0 +1,96 @@
+"""vdwdf_far_tail (the far field past r_cut from eq. 17 and the lattice continuum)
+through the C ABI against the oracle's plain O(N^2) sum: FP64 throughout on the
+GPU, so the bar is 1e-11 relative (the GPU's quadrature in ln s errs by less
+than 1e-15).  Also its refusals and E + T through the GPU converging with r_cut."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0810_2273_gb300 as V
+    return V
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    return torch.device("cuda:0")
+
+
+def _t(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+
+
+def _cases():
+    from paper_0810_2273_gb300 import inputs
+    mono = inputs.xe_monolayer((12, 21, 30))
+    hexa = inputs.xe_monolayer_hex((16, 16, 40))
+    slab = inputs.slab_adsorbate((32, 28, 50))
+    bulk = inputs.xe_monolayer((12, 21, 30))
+    bulk["name"] = "three periodic axes"
+    bulk["periodic"] = (True, True, True)
+    spec = inputs.xe_monolayer((12, 21, 30))
+    spec["name"] = "FFT gradient"
+    spec["gradient"] = "spectral"
+    # periodic y, z and open x: the planes run along the first axis
+    side = inputs.xe_monolayer((12, 21, 30))
+    side["name"] = "periodic along the second and third axes"
+    side["periodic"] = (False, True, True)
+    return [mono, hexa, slab, bulk, spec, side]
+
+
+@pytest.mark.parametrize("k", range(6))
+def test_far_tail_matches_oracle(V, dev, oracle_mod, oracle_spline, k):
+    w = _cases()[k]
+    geom = w.get("cell", w["lengths"])
+    kind = w.get("gradient", "fd")
+    for rc in (12.0, 20.0):
+        r = V.far_tail(_t(w["density"], dev), geom, w["periodic"], w["n_cut"], rc, gradient=kind)
+        P = oracle_mod.Problem(w["density"], w["lengths"], w["periodic"], w["n_cut"], rc, oracle_spline,
+                               cell=w.get("cell"), gradient=kind)
+        To = P.far_tail()
+        assert r["n_active"] == P.n_active
+        assert abs(r["T"] - To) <= 1e-11 * abs(To), (w["name"], rc, r["T"], To)
+        assert r["T"] < 0 and r["nodes"] > 0 and r["launches"] >= 5
+        nper = sum(bool(p) for p in w["periodic"])
+        assert r["planes"] == (1 if nper == 3 else w["density"].shape[list(map(bool, w["periodic"])).index(False)])
+
+
+def test_far_tail_refusals_and_empty(V, dev):
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.xe_monolayer((12, 21, 30))
+    n = _t(w["density"], dev)
+    with pytest.raises(V.VdwdfError) as e:
+        V.far_tail(n, w["lengths"], (True, False, False), w["n_cut"], 20.0)
+    assert e.value.status == -2  # one periodic axis: no lattice continuum
+    with pytest.raises(V.VdwdfError) as e:
+        V.far_tail(n, w["lengths"], w["periodic"], w["n_cut"], 0.0)
+    assert e.value.status == -1
+    r = V.far_tail(n, w["lengths"], w["periodic"], 1e9, 20.0)   # no active point
+    assert r["T"] == 0.0 and r["n_active"] == 0
+
+
+def test_energy_plus_tail_converges_on_gpu(V, dev, oracle_table):
+    """The coarse monolayer through the GPU: FP64 E(r_cut) and T(r_cut) at 15, 25 and
+    35 bohr; E + T moves by under a tenth of what E moves from 15, under a hundredth
+    from 25 (as the oracle's own sums do)."""
+    from paper_0810_2273_gb300 import inputs
+    T = V.Table.from_nodes(oracle_table, 30.0)
+    w = inputs.xe_monolayer((8, 14, 20))
+    n = _t(w["density"], dev)
+    Es, Ts = [], []
+    for rc in (15.0, 25.0, 35.0):
+        Es.append(V.energy(n, w["lengths"], w["periodic"], w["n_cut"], rc, T, "fp64")[0])
+        Ts.append(V.far_tail(n, w["lengths"], w["periodic"], w["n_cut"], rc)["T"])
+    Es, Ts = np.array(Es), np.array(Ts)
+    d_direct = abs(Es[0] - Es[2]), abs(Es[1] - Es[2])
+    d_tail = abs(Es[0] + Ts[0] - Es[2] - Ts[2]), abs(Es[1] + Ts[1] - Es[2] - Ts[2])
+    assert d_tail[0] < 0.1 * d_direct[0] and d_tail[1] < 0.01 * d_direct[1], (d_direct, d_tail)

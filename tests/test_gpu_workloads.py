@@ -58,6 +58,49 @@ def _sample_points(w, rng, n_act, n_inact, n_min=None):
     return np.array(pts, dtype=np.int64)
 
 
+def _inactive_near_active(w, rng, k):
+    """Inactive grid points (n < n_cut) with an active point within the gradient
+    stencil (+-2 along an axis): their v is the divergence term alone, not 0."""
+    n = w["density"]
+    act = n >= w["n_cut"]
+    near = np.zeros_like(act)
+    for ax in range(3):
+        for o in (-2, -1, 1, 2):
+            near |= np.roll(act, o, axis=ax)
+    cand = np.nonzero((~act & near).ravel())[0]
+    return rng.choice(cand, min(k, len(cand)), replace=False)
+
+
+def _stencil_slots(P, m):
+    """Active slots whose n or q0 moves with n_m: m and its stencil neighbours."""
+    d = P.dims
+    c = np.unravel_index(m, d)
+    out = set()
+    for ax in range(3):
+        for o in (-2, -1, 0, 1, 2):
+            cc = list(c)
+            cc[ax] = (cc[ax] + o) % d[ax]
+            s = int(P.slot[np.ravel_multi_index(cc, d)])
+            if s >= 0:
+                out.add(s)
+    return np.array(sorted(out), dtype=np.int64)
+
+
+def _local_energy(P, S):
+    """The part of the oracle's E that depends on the points S of an open cell:
+    E = dV^2 [sum_{i in S} n_i A_i - 1/2 sum_{i, j in S} n_i n_j phi_ij] + (terms
+    free of the points of S).  Two densities that differ only in n and q0 on S
+    differ in E by the difference of this."""
+    A, _, _, _ = P.AU(S)
+    t1 = float(np.dot(P.na[S], A))
+    pos = np.stack([P.i0[S], P.i1[S], P.i2[S]], 1) * np.array(P.h)
+    r = np.linalg.norm(pos[:, None, :] - pos[None, :, :], axis=-1)
+    k = len(S)
+    phi, _, _ = P.spline.kernel(r.ravel(), np.repeat(P.qa[S], k), np.tile(P.qa[S], k))
+    t2 = float(P.na[S] @ phi.reshape(k, k) @ P.na[S])
+    return P.dV ** 2 * (t1 - 0.5 * t2)
+
+
 def test_monolayer_full(V, dev, gtable, oracle_mod, oracle_spline):
     """48x84x120 periodic monolayer (the bench workload): FP32 E + v against the FP64
     GPU energy, identical pair counts, and v at sampled points against the oracle."""
@@ -108,7 +151,7 @@ def test_molecule_full_potential_and_fd(V, dev, gtable, oracle_mod, oracle_splin
     assert np.max(np.abs(v64[pts] - vo)) < 1e-10 * vmax
     assert np.max(np.abs(v32[pts] - vo)) < 1e-5 * vmax
     dV = np.prod(w["lengths"]) / flat.size
-    for m in _sample_points(w, rng, 4, 0, n_min=1e-3):
+    for m in _sample_points(w, rng, 2, 0, n_min=1e-3):
         h = 1e-4 * flat[m]
         Es = []
         for s in (1, -1):
@@ -117,6 +160,40 @@ def test_molecule_full_potential_and_fd(V, dev, gtable, oracle_mod, oracle_splin
             Es.append(V.energy(_t(nn.reshape(w["density"].shape), dev), *_args(w, gtable), precision="fp64")[0])
         fd = (Es[0] - Es[1]) / (2 * h) / dV
         assert abs(fd - v64[m]) < _fd_tol(E64, h, dV, vmax), (m, fd, v64[m])
+
+
+def test_molecule_full_fd_64_points(V, dev, gtable, oracle_mod, oracle_spline):
+    """64^3 open molecule: v (FP64 and FP32) at 64 random grid points with n >= 1e-3
+    against central differences (h = 1e-4 n) of the oracle's FP64 energy.  Moving n_m
+    moves n and q0 only at m and its gradient-stencil neighbours S, so the difference
+    of E is the difference of its S-dependent part (_local_energy), exact up to
+    rounding and summed over every active point of the full grid."""
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.molecule24()
+    n = _t(w["density"], dev)
+    _, v64, _ = V.potential(n, *_args(w, gtable), precision="fp64")
+    _, v32, _ = V.potential(n, *_args(w, gtable), precision="fp32")
+    v64 = v64.cpu().numpy().ravel()
+    v32 = v32.cpu().numpy().ravel()
+    vmax = np.max(np.abs(v64))
+    flat = w["density"].ravel()
+    P0 = oracle_mod.Problem(w["density"], *_args(w, oracle_spline))
+    rng = np.random.default_rng(23)
+    pts = rng.choice(np.nonzero(flat >= 1e-3)[0], 64, replace=False)
+    for m in pts:
+        S = _stencil_slots(P0, m)
+        h = 1e-4 * flat[m]
+        Es = []
+        for s in (1, -1):
+            nn = flat.copy()
+            nn[m] += s * h
+            P = oracle_mod.Problem(nn.reshape(w["density"].shape), *_args(w, oracle_spline))
+            assert np.array_equal(P.active, P0.active)   # the mask is frozen
+            Es.append(_local_energy(P, S))
+        fd = (Es[0] - Es[1]) / (2 * h) / P0.dV
+        # truncation O((h/n)^2) ~ 1e-8 of v_m, plus rounding of the local sums
+        assert abs(fd - v64[m]) < 1e-7 * vmax + 1e-6 * abs(v64[m]), (m, fd, v64[m])
+        assert abs(fd - v32[m]) < 1e-5 * vmax, (m, fd, v32[m])
 
 
 def test_molecule_coarse_fd(V, dev, gtable):
@@ -174,8 +251,10 @@ def test_binding_curve_batched(V, dev, gtable, oracle_mod, oracle_spline):
 
 
 def test_slab_full_sampled(V, dev, gtable, oracle_mod, oracle_spline):
-    """128x112x200 periodic slab + flake: FP32 E + v at full size with A, U, v at
-    sampled points against the oracle; FP32 vs FP64 E on a 64x56x100 regrid."""
+    """128x112x200 periodic slab + flake: FP32 E + v at full size with A, U at 12
+    sampled points and v at 20 (active, and inactive next to active) against the
+    oracle; FP32 vs FP64 E on a 64x56x100 regrid (the FP64 pass at full size takes
+    about 7 minutes)."""
     from paper_0810_2273_gb300 import inputs
     w = inputs.slab_adsorbate()
     n = _t(w["density"], dev)
@@ -189,6 +268,15 @@ def test_slab_full_sampled(V, dev, gtable, oracle_mod, oracle_spline):
     Ug = U32.cpu().numpy().ravel()[idx]
     assert np.max(np.abs(Ag - A)) < 1e-5 * np.max(np.abs(A))
     assert np.max(np.abs(Ug - U)) < 1e-5 * np.max(np.abs(U))
+    # v at 14 active and 6 inactive points next to active ones, against the oracle's
+    # potential from A, U of every active point in their stencil neighbourhoods
+    rng = np.random.default_rng(29)
+    pts = np.concatenate([_sample_points(w, rng, 14, 0), _inactive_near_active(w, rng, 6)])
+    vo = P.potential_at(pts)
+    v = v32.cpu().numpy().ravel()
+    vmax = np.max(np.abs(v))
+    assert np.max(np.abs(v[pts] - vo)) < 1e-5 * vmax, np.max(np.abs(v[pts] - vo)) / vmax
+    assert np.count_nonzero(vo) == len(pts)
     wc = inputs.slab_adsorbate((64, 56, 100))
     nc = _t(wc["density"], dev)
     e32, _ = V.energy(nc, *_args(wc, gtable), precision="fp32")
