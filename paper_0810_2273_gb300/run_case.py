@@ -1,7 +1,7 @@
 """Run one standard workload through the library and print per-call timings.
 
     python -m paper_0810_2273_gb300.run_case --workload xe_monolayer \
-        [--dims 24 42 60] [--mode potential|energy|semilocal|diag|gradient]
+        [--dims 24 42 60] [--mode potential|energy|semilocal|diag|gradient|tail]
         [--precision fp32|fp64] [--gradient fd|spectral] [--repeat 3]
 
 Workloads are the seeded densities of ``paper_0810_2273_gb300.inputs``
@@ -19,7 +19,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="xe_monolayer",
                     choices=["kr_dimer", "xe_monolayer", "xe_monolayer_hex", "molecule24", "slab_adsorbate"])
     ap.add_argument("--dims", type=int, nargs=3, default=None)
-    ap.add_argument("--mode", default="potential", choices=["potential", "energy", "semilocal", "diag", "gradient"])
+    ap.add_argument("--mode", default="potential",
+                    choices=["potential", "energy", "semilocal", "diag", "gradient", "tail"])
     ap.add_argument("--gradient", default="fd", choices=["fd", "spectral"], help="the library's density gradient")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--repeat", type=int, default=3)
@@ -55,6 +56,13 @@ def main(argv=None):
             print(json.dumps(dict(call=k, ms=e0.elapsed_time(e1), wall_ms=1e3 * (time.perf_counter() - t0),
                                   workload=a.workload, dims=list(n.shape), mode=a.mode, gradient=a.gradient,
                                   max_abs=float(g.abs().max()))), flush=True)
+            continue
+        if a.mode == "tail":
+            res = V.far_tail(n, cell, w["periodic"], w["n_cut"], w["r_cut"], gradient=a.gradient)
+            torch.cuda.synchronize()
+            res.update(call=k, wall_ms=1e3 * (time.perf_counter() - t0), workload=a.workload,
+                       dims=list(n.shape), mode=a.mode)
+            print(json.dumps(res), flush=True)
             continue
         if a.mode == "diag":
             res = V.diag_voxel(n, cell, w["periodic"], w["n_cut"], T, gradient=a.gradient)
