@@ -142,8 +142,9 @@ typedef struct {
 /* Optional launch shape of the pair kernel (NULL = defaults / tuned).  Values
  * outside those listed are VDWDF_EINVAL; 256 or 1024 threads on a skewed cell
  * are VDWDF_EUNSUPPORTED (both before any device work). */
-#define VDWDF_TUNE_AUTO (-1)  /* threads: vdwdf_energy_batched only -- the autotuner
-                                 picks the shape (the other fields are ignored) */
+#define VDWDF_TUNE_AUTO (-1)  /* threads: vdwdf_energy_batched only -- the fastest
+                                 candidate shape on the batch itself is used (the
+                                 other fields are ignored) */
 typedef struct {
     int32_t threads;      /* threads per CTA: 256, 384, 448, 512 or 1024 (0 = default:
                              FP32 E + v 448, or 384 on skewed cells; 512 otherwise);
@@ -255,9 +256,10 @@ int vdwdf_potential(const vdwdf_grid *grid, const double *n_dev, double n_cut, d
  * pointers, shapes, cells, periodicity, gradient kind, cutoffs, precision,
  * tuning and table (binding curves, section 6.1).  Up to 8 recorded graphs are
  * kept (the least recently used is dropped first, with its scratch); freeing a
- * table drops the graphs that read it.  tuning->threads = VDWDF_TUNE_AUTO runs
- * the autotuner (as vdwdf_autotune) on the largest instance when the graph is
- * recorded and uses the shape it picks; out->pair_threads reports it.  E_out:
+ * table drops the graphs that read it.  tuning->threads = VDWDF_TUNE_AUTO makes
+ * the call time every candidate shape of vdwdf_autotune on this batch (the
+ * whole pass, twice each, when the graph is first recorded) and record the
+ * fastest; out->pair_threads reports it.  E_out:
  * host array of ninst doubles.  Synchronises the stream.  Errors as
  * vdwdf_energy. */
 int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const *n_dev,

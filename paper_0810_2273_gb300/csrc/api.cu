@@ -1582,21 +1582,10 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
             destroy_plan(old->second);
             g_batches.erase(old);
         }
-        // VDWDF_TUNE_AUTO: the autotuner picks the launch shape on the batch's
-        // largest instance before the graph is recorded (once per plan)
-        if (tune_auto) {
-            int kbig = 0;
-            for (int k = 1; k < ninst; ++k)
-                if (geo[k].N > geo[kbig].N) kbig = k;
-            rc = autotune_one(geo[kbig], n_dev[kbig], n_cut, table, precision, &tuned, st);
-            if (rc) return rc;
-            use = &tuned;
-        }
         bp = new (std::nothrow) BatchPlan;
         if (!bp) return VDWDF_EALLOC;
         bp->device = dev;
         bp->table_gen = table->gen;
-        bp->tuned = tuned;
         bp->geo = geo;
         bp->work.resize(ninst);
         const int ngroups = (ninst + kMaxInst - 1) / kMaxInst;
@@ -1628,10 +1617,17 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
                 gsum += geo[k].N;
                 gskew = gskew || geo[k].skew;
             }
-            const Launch ln = choose_launch(precision, false, use, table, std::max<long long>(1, gsum / (k1 - k0)), gskew,
-                                            k1 - k0);
+            // room for one partial per work item of the shape used (of any candidate
+            // shape when the autotuner runs; items past the room would go atomically)
             long long items = 0;
-            for (int k = k0; k < k1; ++k) items += pair_items(geo[k].N, ln.jt);
+            for (int ci = 0; ci < (tune_auto ? kTuneCount : 1); ++ci) {
+                const vdwdf_tuning *t = tune_auto ? &kTuneCandidates[ci] : use;
+                const Launch ln = choose_launch(precision, false, t, table, std::max<long long>(1, gsum / (k1 - k0)),
+                                                gskew, k1 - k0);
+                long long it = 0;
+                for (int k = k0; k < k1; ++k) it += pair_items(geo[k].N, ln.jt);
+                items = std::max(items, it);
+            }
             double *b = nullptr;
             if (scratch_malloc(reinterpret_cast<void **>(&b), sizeof(double) * std::max<long long>(items, 1)) != cudaSuccess) {
                 delete bp;
@@ -1639,6 +1635,38 @@ int vdwdf_energy_batched(int ninst, const vdwdf_grid *grids, const double *const
             }
             bp->item_bufs.push_back(b);
             bp->item_caps.push_back(items);
+        }
+        // VDWDF_TUNE_AUTO: the autotuner times every candidate shape on this very
+        // batch (the whole pass, uncaptured, on the caller's stream, twice; the
+        // second run counts) and the fastest is recorded.  The energy-mode default
+        // is a candidate, so the choice is never slower than it by more than noise.
+        if (tune_auto) {
+            Timer tt;
+            double best_ms = -1.0;
+            for (int ci = 0; ci < kTuneCount && rc == VDWDF_OK; ++ci) {
+                const vdwdf_tuning &cd = kTuneCandidates[ci];
+                if (precision == VDWDF_FP64 && cd.smem_rows != 0) continue;
+                bool ok = true;
+                for (int k = 0; k < ninst; ++k) ok = ok && check_tuning(&cd, geo[k].skew) == VDWDF_OK;
+                if (!ok) continue;
+                for (int rep = 0; rep < 2 && rc == VDWDF_OK; ++rep) {
+                    tt.mark(0, st);
+                    rc = record_batch(*bp, ninst, n_dev, n_cut, table, precision, &cd, d64, d32, st);
+                    tt.mark(1, st);
+                    if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
+                }
+                const double ms = tt.ms(0, 1);
+                if (rc == VDWDF_OK && ms > 0.0 && (best_ms < 0.0 || ms < best_ms)) {
+                    best_ms = ms;
+                    tuned = cd;
+                }
+            }
+            if (rc != VDWDF_OK) {
+                delete bp;
+                return rc;
+            }
+            use = &tuned;
+            bp->tuned = tuned;
         }
         // record the whole batch into a graph on a private stream
         cudaStream_t cs = nullptr;
