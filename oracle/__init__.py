@@ -88,6 +88,8 @@ def load_library(path):
     L.orc_pbe_H_many.argtypes = [_i, _p, _p, _p]
     L.orc_far_tail.restype = _i
     L.orc_far_tail.argtypes = [_i, _p, _p, _p, _p, _p, _i, _i, _i, _p, _i, _i, _i, _d, _p]
+    L.orc_far_tail_AB.restype = _i
+    L.orc_far_tail_AB.argtypes = [_i, _p, _p, _p, _p, _p, _i, _i, _i, _p, _i, _i, _i, _d, _i, _p, _p, _p]
     L.orc_semilocal.restype = _i
     L.orc_semilocal.argtypes = [_i, _p, _p, _p, _p]
     return L
@@ -570,6 +572,25 @@ class Problem:
         cell = np.diag(self.lengths) if self.cell is None else self.cell
         return far_tail_points(self.i0, self.i1, self.i2, self.na, self.qa, self.dims, cell,
                                self.periodic, self.rc)
+
+    def far_tail_potential(self):
+        """The potential of the far field T (far_tail): v_T = dT/dn / dV with the mask
+        frozen.  T has the pair sum's adjoint form with
+            A_m = -C sum_j n_j f(u_m, u_j) K_mj,
+            U_m = dT/dq_m / dV^2 = -C n_m 2 q_m sum_j n_j df/da(u_m, u_j) K_mj,
+        f(a, b) = 1 / (a b (a + b)), u = q0^2 (orc_far_tail_AB), so the grid
+        assembly of ``potential`` applies."""
+        cell = np.diag(self.lengths) if self.cell is None else self.cell
+        cell = _f64(cell).reshape(3, 3)
+        qidx = _i32(np.arange(self.n_active))
+        AT = np.zeros(self.n_active)
+        BT = np.zeros(self.n_active)
+        rc_ = lib().orc_far_tail_AB(self.n_active, _ptr(self.i0), _ptr(self.i1), _ptr(self.i2),
+                                    _ptr(self.na), _ptr(self.qa), *map(int, self.dims), _ptr(cell),
+                                    *self.periodic, self.rc, len(qidx), _ptr(qidx), _ptr(AT), _ptr(BT))
+        if rc_ != 0:
+            raise ValueError("far tail needs two or three periodic axes and rc > 0")
+        return self.potential(A=-C_ASYM * AT, U=-C_ASYM * self.na * 2.0 * self.qa * BT)
 
     def voxel(self):
         """Rows v_a = M_a / N_a spanning one voxel."""

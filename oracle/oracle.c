@@ -52,6 +52,8 @@
  *                                   cells), the exact lattice sum of eq. (17)
  *                                   beyond r_cut, convergence of E + T with
  *                                   r_cut against direct sums
+ *   orc_far_tail_AB                 pinned: the far field's potential against
+ *                                   central differences of orc_far_tail
  *   orc_phi0_many                   pinned: small-voxel logarithmic law,
  *                                   scale duality phi0(s q; v) = phi0(q; s v),
  *                                   Monte Carlo voxel average, quadrature
@@ -1215,5 +1217,68 @@ int orc_far_tail(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2
         sum += n[i] * acc;
     }
     *out = 0.5 * dV * dV * sum;
+    return 0;
+}
+
+/* The far field's own potential: with f(a, b) = 1 / (a b (a + b)), u = q0^2,
+ *   T = -1/2 dV^2 C sum_i sum_j n_i n_j f(u_i, u_j) K_ij   (orc_far_tail),
+ * so, for query points m,
+ *   AT_m = sum_j n_j f(u_m, u_j) K_mj         (dT/dn_m = -dV^2 C AT_m),
+ *   BT_m = sum_j n_j df/da(u_m, u_j) K_mj,    df/da = -f (1/a + 1/(a + b))
+ *                                             (dT/du_m = -dV^2 C n_m BT_m).
+ * Same points, cell and K_ij as orc_far_tail; returns -1 likewise. */
+int orc_far_tail_AB(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2,
+                    const double *n, const double *q, int n0, int n1, int n2, const double *cell,
+                    int per0, int per1, int per2, double rc, int nq, const int32_t *qidx,
+                    double *AT, double *BT)
+{
+    int per[3] = {per0, per1, per2};
+    int np = (per0 != 0) + (per1 != 0) + (per2 != 0);
+    if (np < 2 || !(rc > 0.0)) return -1;
+    const double *M0 = cell, *M1 = cell + 3, *M2 = cell + 6;
+    double x01[3] = {M0[1] * M1[2] - M0[2] * M1[1], M0[2] * M1[0] - M0[0] * M1[2], M0[0] * M1[1] - M0[1] * M1[0]};
+    double V = fabs(x01[0] * M2[0] + x01[1] * M2[1] + x01[2] * M2[2]);
+    if (!(V > 0.0)) return -1;
+    double e[3] = {0.0, 0.0, 0.0}, A = 0.0;
+    if (np == 2) {
+        const double *P[3] = {M0, M1, M2};
+        const double *a = NULL, *b = NULL;
+        for (int k = 0; k < 3; ++k)
+            if (per[k]) { if (!a) a = P[k]; else b = P[k]; }
+        double x[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+        A = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (int c = 0; c < 3; ++c) e[c] = x[c] / A;
+    }
+    int N[3] = {n0, n1, n2};
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int t = 0; t < nq; ++t) {
+        int i = qidx[t];
+        double ri[3];
+        for (int c = 0; c < 3; ++c)
+            ri[c] = i0[i] / (double)N[0] * M0[c] + i1[i] / (double)N[1] * M1[c] + i2[i] / (double)N[2] * M2[c];
+        double ui = q[i] * q[i];
+        double sa = 0.0, sb = 0.0;
+        for (int j = 0; j < Na; ++j) {
+            double uj = q[j] * q[j];
+            double K;
+            if (np == 3) {
+                K = (4.0 * M_PI / V) / (3.0 * rc * rc * rc);
+            } else {
+                double z = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    double rjc = i0[j] / (double)N[0] * M0[c] + i1[j] / (double)N[1] * M1[c] +
+                                 i2[j] / (double)N[2] * M2[c];
+                    z += (ri[c] - rjc) * e[c];
+                }
+                double R = fabs(z) > rc ? fabs(z) : rc;
+                K = (2.0 * M_PI / A) / (4.0 * R * R * R * R);
+            }
+            double f = 1.0 / (ui * uj * (ui + uj));
+            sa += n[j] * f * K;
+            sb += n[j] * (-f * (1.0 / ui + 1.0 / (ui + uj))) * K;
+        }
+        AT[t] = sa;
+        BT[t] = sb;
+    }
     return 0;
 }

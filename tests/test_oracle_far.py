@@ -119,3 +119,32 @@ def test_energy_plus_tail_converges(oracle_mod, oracle_spline):
     d_direct = abs(Es[0] - Es[2]), abs(Es[1] - Es[2])
     d_tail = abs(Es[0] + Ts[0] - Es[2] - Ts[2]), abs(Es[1] + Ts[1] - Es[2] - Ts[2])
     assert d_tail[0] < 0.1 * d_direct[0] and d_tail[1] < 0.01 * d_direct[1], (d_direct, d_tail)
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 0), (0, 1, 1), (1, 1, 1)])
+def test_tail_potential_is_derivative_of_tail(oracle_mod, oracle_spline, periodic):
+    """The far field's potential v_T = dT/dn_m / dV (mask frozen) against central
+    differences of the oracle's T, at active points and at inactive points next
+    to the active region (where only the gradient term of q0 acts)."""
+    rng = np.random.default_rng(41)
+    dims = (9, 8, 10)
+    L = (6.0, 6.4, 7.0)
+    n = 0.02 + 0.5 * rng.uniform(0, 1, size=dims) * np.exp(-rng.uniform(0, 3, size=dims))
+    n_cut = 0.05
+    n[np.abs(n - n_cut) < 0.01] += 0.03
+    rc = 5.0
+    P = oracle_mod.Problem(n, L, periodic, n_cut, rc, oracle_spline)
+    v = P.far_tail_potential()
+    flat = n.ravel()
+    act = np.nonzero(flat >= 2 * n_cut)[0]
+    ina = np.nonzero(flat < 0.5 * n_cut)[0]
+    pts = np.concatenate([rng.choice(act, 6, replace=False), rng.choice(ina, 4, replace=False)])
+    for m in pts:
+        hstep = 1e-4 * flat[m]
+
+        def T_at(delta):
+            nn = flat.copy()
+            nn[m] += delta
+            return oracle_mod.Problem(nn.reshape(dims), L, periodic, n_cut, rc, oracle_spline).far_tail()
+        fd = (T_at(hstep) - T_at(-hstep)) / (2 * hstep) / P.dV
+        assert abs(fd - v.ravel()[m]) < 1e-6 * np.max(np.abs(v)), (m, fd, v.ravel()[m])

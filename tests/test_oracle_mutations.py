@@ -111,6 +111,9 @@ MUTATIONS = [
     ("far tail: 2 pi / A written pi / A",
      "K = (2.0 * M_PI / A) / (4.0 * R * R * R * R);", "K = (M_PI / A) / (4.0 * R * R * R * R);", 0,
      FAR.test_continuum_approaches_the_lattice_sum, ("oracle_mod",)),
+    ("far tail's potential: the 1/(a + b) term of df/da dropped",
+     "sb += n[j] * (-f * (1.0 / ui + 1.0 / (ui + uj))) * K;", "sb += n[j] * (-f * (1.0 / ui)) * K;", 0,
+     FAR.test_tail_potential_is_derivative_of_tail, ("oracle_mod", "oracle_spline", (1, 1, 0))),
     ("PBE correlation: A^2 t^4 written A t^4",
      "double den = 1.0 + A * t2 + A * A * t2 * t2;", "double den = 1.0 + A * t2 + A * t2 * t2;", 0,
      SEMI.test_pbe_gradient_correction_limits, ("oracle_mod",)),
