@@ -231,6 +231,17 @@ def run_gpu(args):
         semi_ms.append(semi["ms"])
     semi_t = float(np.median(semi_ms[1:]))
 
+    # the far field past the cutoff (eq. 17 and the lattice continuum) on the same
+    # density, outside the timed steps: T, E + T and the call's own device time
+    tails = []
+    for _ in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        tails.append(V.far_tail(n, w["lengths"], w["periodic"], w["n_cut"], w["r_cut"]))
+    tail = {"T_hartree": tails[-1]["T"], "E_plus_T_hartree": results[-1][0] + tails[-1]["T"],
+            "ms_per_call": float(np.median([t["ms"] for t in tails[1:]])), "nodes": tails[-1]["nodes"],
+            "planes": tails[-1]["planes"], "bound": "fp64 (one exp per active point and quadrature node)"}
+
     ms, e2e, total_pairs = combine_ranks(ms, e2e, pairs, dev)
     if rank != 0:
         if ws > 1:
@@ -281,6 +292,7 @@ def run_gpu(args):
                       "bound": "fp64 (per-point cbrt, log, expm1 at GB300's FP64 rate)",
                       "E_hartree": {k: semi[k] for k in ("Ex_lda", "Ec_lda", "Ex_pbe", "Ec_pbe", "Ex_revpbe")},
                       "eq3_needed_number": semi["Ec_lda"] - semi["Ec_pbe"] + results[-1][0]},
+        "far_tail": tail,
         "cpu_baseline": cpu,
         "e2e": {"value": total_pairs / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(n.numel() * 8),
                 "d2h_bytes_per_step": int(n.numel() * 8 + 8), "ms_per_step": e2e},

@@ -344,13 +344,20 @@ typedef struct {
  * (17) as r_cut grows.  The library evaluates T in FP64, with
  * 1/(a + b) = int exp(-(a + b) s) ds by the trapezoidal rule in ln s
  * (relative error below 1e-15), from per-plane sums over the grid.
+ * v_dev: NULL, or an [N] FP64 device array that receives T's potential,
+ * v_T = dT/dn / dV with the active mask frozen, in the pair sum's adjoint form
+ * (vdwdf_potential) with
+ *   A_m = -C sum_j n_j f(u_m, u_j) K_mj,
+ *   U_m = -2 C n_m q0_m sum_j n_j (df/du_m)(u_m, u_j) K_mj,
+ * f(a, b) = 1/(a b (a + b)), u = q0^2; so v + v_T is the potential of E + T.
  * grid as in vdwdf_energy with exactly two or three periodic axes; grad_dev
- * as in vdwdf_q0; r_cut > 0.  Synchronises the stream.
- * Errors: VDWDF_EINVAL (bad argument, r_cut <= 0), VDWDF_EUNSUPPORTED (fewer
- * than two periodic axes, or a q0 range needing more than 4096 nodes),
- * VDWDF_ECUDA, VDWDF_EALLOC. */
+ * as in vdwdf_q0, and NULL when v_dev is given (the potential needs the
+ * library's own gradient); r_cut > 0.  Synchronises the stream.
+ * Errors: VDWDF_EINVAL (bad argument, r_cut <= 0, grad_dev with v_dev),
+ * VDWDF_EUNSUPPORTED (fewer than two periodic axes, or a q0 range needing
+ * more than 4096 nodes), VDWDF_ECUDA, VDWDF_EALLOC. */
 int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
-                   double r_cut, vdwdf_tail_result *out, void *cuda_stream);
+                   double r_cut, double *v_dev, vdwdf_tail_result *out, void *cuda_stream);
 
 /* --------------------------------------------------------------------- */
 /* Voxel-averaged diagonal (the "phi0" step of the paper's Appendix A      */

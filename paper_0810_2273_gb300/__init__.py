@@ -212,10 +212,10 @@ def semilocal(n, lengths, periodic, grad=None, gradient="fd"):
     return res.as_dict()
 
 
-def far_tail(n, lengths, periodic, n_cut, r_cut, grad=None, gradient="fd"):
+def far_tail(n, lengths, periodic, n_cut, r_cut, grad=None, gradient="fd", want_v=False):
     """The far field past r_cut from eq. (17) and the lattice continuum
     (vdwdf_far_tail): E(r_cut -> inf) reads E(r_cut) + T.  Returns the result dict
-    (T in Hartree)."""
+    (T in Hartree), and with want_v also T's potential on the grid."""
     _check_tensor(n, "n")
     if grad is not None:
         _check_tensor(grad, "grad")
@@ -223,12 +223,14 @@ def far_tail(n, lengths, periodic, n_cut, r_cut, grad=None, gradient="fd"):
     lib = _native.load()
     g = grid(lengths, n.shape, periodic, gradient)
     res = _native.vdwdf_tail_result()
+    v = torch.empty_like(n) if want_v else None
     with torch.cuda.device(n.device):
         st = lib.vdwdf_far_tail(ctypes.byref(g), ctypes.c_void_p(n.data_ptr()),
                                 ctypes.c_void_p(grad.data_ptr()) if grad is not None else None,
-                                float(n_cut), float(r_cut), ctypes.byref(res), _stream(n))
+                                float(n_cut), float(r_cut), ctypes.c_void_p(v.data_ptr()) if want_v else None,
+                                ctypes.byref(res), _stream(n))
     _native.check(st, "vdwdf_far_tail")
-    return res.as_dict()
+    return (res.as_dict(), v) if want_v else res.as_dict()
 
 
 def phi0_eval(table, voxel, q):

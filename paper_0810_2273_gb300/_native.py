@@ -94,8 +94,8 @@ PROTOTYPES = {
     "vdwdf_autotune": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_d, _c_d, _c_p, _c_i,
                               ctypes.POINTER(vdwdf_tuning), _c_p]),
     "vdwdf_total_energy_nl": (_c_i, [_c_d, ctypes.POINTER(vdwdf_semilocal_result), _c_d, _c_i, _c_p]),
-    "vdwdf_far_tail": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_d, _c_d, ctypes.POINTER(vdwdf_tail_result),
-                              _c_p]),
+    "vdwdf_far_tail": (_c_i, [ctypes.POINTER(vdwdf_grid), _c_p, _c_p, _c_d, _c_d, _c_p,
+                              ctypes.POINTER(vdwdf_tail_result), _c_p]),
     "vdwdf_strerror": (ctypes.c_char_p, [_c_i]),
     "vdwdf_version": (_c_i, []),
     "vdwdf_launch_count": (_c_i64, []),

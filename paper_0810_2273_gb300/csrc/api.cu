@@ -1373,12 +1373,14 @@ int autotune_one(const Geom &G, const double *n_dev, double n_cut, const vdwdf_t
 extern "C" {
 
 int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
-                   double r_cut, vdwdf_tail_result *out, void *cuda_stream) {
+                   double r_cut, double *v_dev, vdwdf_tail_result *out, void *cuda_stream) {
     using namespace vdwdf;
     Geom G;
     int rc = check_grid(grid, G);
     if (rc) return rc;
     if (!n_dev || !out) return VDWDF_EINVAL;
+    const bool pot = v_dev != nullptr;
+    if (pot && grad_dev) return VDWDF_EINVAL;  // the potential needs the library's own gradient
     if (!(n_cut > 0.0) || !std::isfinite(n_cut) || !(r_cut > 0.0) || !std::isfinite(r_cut)) return VDWDF_EINVAL;
     const int nper = (G.per[0] != 0) + (G.per[1] != 0) + (G.per[2] != 0);
     if (nper < 2) return VDWDF_EUNSUPPORTED;
@@ -1419,8 +1421,21 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
                  o_out = cv.take<double>(1);
     const size_t o_gsp = G.spectral ? cv.take<double>(3 * G.N) : 0,
                  o_coef = G.spectral ? cv.take<double>(G.dims[0] + G.dims[1] + G.dims[2]) : 0;
+    // the potential: G_k(p), dq0/dn, dq0/dgrad n, the slot map, A and U on the grid, and
+    // the spectral divergence
+    const size_t o_G = pot ? cv.take<double>(static_cast<size_t>(kMaxNodes) * np) : 0,
+                 o_qn = pot ? cv.take<double>(G.N) : 0, o_qg = pot ? cv.take<double>(3 * G.N) : 0,
+                 o_slot = pot ? cv.take<int>(G.N) : 0, o_A = pot ? cv.take<double>(G.N) : 0,
+                 o_U = pot ? cv.take<double>(G.N) : 0, o_div = (pot && G.spectral) ? cv.take<double>(G.N) : 0;
     unsigned char *base = nullptr;
     if (scratch_malloc_async(reinterpret_cast<void **>(&base), cv.off, st) != cudaSuccess) return VDWDF_EALLOC;
+    double *Gk = pot ? reinterpret_cast<double *>(base + o_G) : nullptr;
+    double *qn = pot ? reinterpret_cast<double *>(base + o_qn) : nullptr;
+    double *qgr = pot ? reinterpret_cast<double *>(base + o_qg) : nullptr;
+    int *slot = pot ? reinterpret_cast<int *>(base + o_slot) : nullptr;
+    double *Ad = pot ? reinterpret_cast<double *>(base + o_A) : nullptr;
+    double *Ud = pot ? reinterpret_cast<double *>(base + o_U) : nullptr;
+    double *divb = (pot && G.spectral) ? reinterpret_cast<double *>(base + o_div) : nullptr;
     double *q0 = reinterpret_cast<double *>(base + o_q0);
     unsigned long long *mm = reinterpret_cast<unsigned long long *>(base + o_mm);
     double *F = reinterpret_cast<double *>(base + o_F), *Tk = reinterpret_cast<double *>(base + o_Tk);
@@ -1436,15 +1451,16 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
         const double *g_use = nullptr;
         int r = q0_gradient(G, n_dev, grad_dev, gsp, coef, &g_use, st);
         if (r) return r;
-        r = launch_grad_q0(G.dims, G.am, n_dev, g_use, q0, nullptr, nullptr, st);
+        r = launch_grad_q0(G.dims, G.am, n_dev, g_use, q0, qn, qgr, st);
         if (r) return r;
+        if (pot) VDWDF_CUDA_TRY(cudaMemsetAsync(v_dev, 0, sizeof(double) * G.N, st));
         VDWDF_CUDA_TRY(cudaMemsetAsync(mm, 0xFF, sizeof(unsigned long long), st));
         VDWDF_CUDA_TRY(cudaMemsetAsync(mm + 1, 0, 2 * sizeof(unsigned long long), st));
         r = launch_diag_range(G.N, n_dev, q0, n_cut, mm, st);
         if (r) return r;
         VDWDF_CUDA_TRY(cudaMemcpyAsync(hmm, mm, sizeof(hmm), cudaMemcpyDeviceToHost, st));
         VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
-        if (hmm[2] == 0) return VDWDF_OK;
+        if (hmm[2] == 0) return VDWDF_OK;  // no active point: T = 0 and v = 0
         double qmin, qmax;
         std::memcpy(&qmin, &hmm[0], 8);
         std::memcpy(&qmax, &hmm[1], 8);
@@ -1459,8 +1475,14 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
         if (nodes > kMaxNodes) return VDWDF_EUNSUPPORTED;
         const double Cas = 12.0 * std::pow(4.0 * kPi / 9.0, 3);
         r = launch_far_tail(G.dims, ax, np, n_dev, q0, n_cut, x0, hx, nodes, dz, r_cut, c2, c3,
-                            -0.5 * G.dV * G.dV * Cas, F, Tk, Tout, st);
+                            -0.5 * G.dV * G.dV * Cas, F, Tk, Gk, Tout, st);
         if (r) return r;
+        if (pot) {
+            r = launch_far_tail_AU(G.dims, ax, np, n_dev, q0, n_cut, x0, hx, nodes, Gk, Cas, slot, Ad, Ud, st);
+            if (r) return r;
+            r = assemble_v(G, slot, Ad, Ud, qn, qgr, gsp, divb, coef, v_dev, nullptr, nullptr, st);
+            if (r) return r;
+        }
         tm.mark(1, st);
         VDWDF_CUDA_TRY(cudaMemcpyAsync(&T, Tout, sizeof(double), cudaMemcpyDeviceToHost, st));
         VDWDF_CUDA_TRY(cudaStreamSynchronize(st));

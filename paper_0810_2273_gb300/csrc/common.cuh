@@ -207,9 +207,15 @@ int launch_diag_AU(long long N, const double *n, const double *q0, double n_cut,
 // ln s; F (nodes x np) and Tk (nodes) scratch; out = scale sum_k hx e^{x_k} Tk[k]
 // with Tk[k] = sum_{p,p'} K(p, p') F_k(p) F_k(p'),
 // K = c2 / max(rc, |p - p'| dz)^4 (np > 1) or c3 (np = 1).
+// G (nodes x np, nullable) keeps G_k(p) = sum_{p'} K(p, p') F_k(p') for the potential.
 int launch_far_tail(const int dims[3], int ax, int np, const double *n, const double *q0, double n_cut,
                     double x0, double hx, int nodes, double dz, double rc, double c2, double c3, double scale,
-                    double *F, double *Tk, double *out, cudaStream_t st);
+                    double *F, double *Tk, double *G, double *out, cudaStream_t st);
+// The far field's potential in the pair sum's adjoint form on the grid: A, U (N)
+// at active points with slot[m] = m, slot[m] = -1 elsewhere (for launch_assemble).
+int launch_far_tail_AU(const int dims[3], int ax, int np, const double *n, const double *q0, double n_cut,
+                       double x0, double hx, int nodes, const double *G, double C, int *slot, double *A,
+                       double *U, cudaStream_t st);
 int launch_kernel_eval(int precision, const PairShared &sh, int64_t npts, const double *r,
                        const double *qi, const double *qj, double *phi, double *rdphi,
                        cudaStream_t st);

@@ -515,6 +515,43 @@ __device__ __forceinline__ void band_pair2(const Table<float> &tb, float2 tD, in
     }
 }
 
+// The same two evaluations from the table's copy in global memory (read-only
+// path, rows of stride S), for steps where a half lies off the resident band.
+template <bool POT>
+__device__ __forceinline__ void table_pair2(const Table<float> &tb, float2 tD, int l0, int l1, bool use0,
+                                           bool use1, const float2 wdb[4], const float2 dwdb[4],
+                                           float2 &p, float2 &pt, float2 &pu) {
+    int k0, k1;
+    const float2 t = floor_split2(tD, k0, k1);
+    float2 wD[4], dwD[4];
+    bw2(t, wD);
+    if (POT) bdw2(t, dwD);
+    const float *g0 = tb.g + static_cast<size_t>(k0) * tb.S + l0;
+    const float *g1 = tb.g + static_cast<size_t>(k1) * tb.S + l1;
+    const int rs = tb.S;
+    p = f2(0.0f);
+    pt = f2(0.0f);
+    pu = f2(0.0f);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        float2 c[4];
+#pragma unroll
+        for (int n = 0; n < 4; ++n)  // an unused half reads nothing
+            c[n] = make_float2(use0 ? __ldg(g0 + m * rs + n) : 0.0f, use1 ? __ldg(g1 + m * rs + n) : 0.0f);
+        const float2 row = fma2(wdb[3], c[3], fma2(wdb[2], c[2], fma2(wdb[1], c[1], mul2(wdb[0], c[0]))));
+        p = fma2(wD[m], row, p);
+        if (POT) {
+            // delta derivative from exact coefficient differences (see combine);
+            // fma(c0, -1, c_n) is c_n - c0 with one rounding
+            const float2 m1 = f2(-1.0f);
+            const float2 drow = fma2(dwdb[3], fma2(c[0], m1, c[3]),
+                                     fma2(dwdb[2], fma2(c[0], m1, c[2]), mul2(dwdb[1], fma2(c[0], m1, c[1]))));
+            pt = fma2(dwD[m], row, pt);
+            pu = fma2(wD[m], drow, pu);
+        }
+    }
+}
+
 // The images of two j points j0, j1 for one i point (FP32): half 0 runs over the
 // images of mask m0 (those of j0), half 1 over m1 (those of j1), one image of each
 // per step; a half whose mask is spent idles.  ex, ey, ez: x_i - x_j per half in
@@ -573,6 +610,19 @@ __device__ __forceinline__ void images2_f32(unsigned m0, unsigned m1, const floa
             const float2 tq = make_float2(in0 ? tD.x : band_lo, in1 ? tD.y : band_lo);
             float2 p, pt, pu;
             band_pair2<POT>(tb, tq, dp.l0, dp.l1, in0, in1, dp.wd, dp.dwd, p, pt, pu);
+            A2 = add2(A2, p);
+            if (POT) {
+                Srpt = fma2(rr, pt, Srpt);
+                Spu = add2(Spu, pu);
+            }
+        } else if (POT && (!in0 || tD.x <= K.tDmax) && (!in1 || tD.y <= K.tDmax)) {
+            // E + v: a half off the resident band but both on the table: both halves
+            // from the table's global copy, packed as in the band (measured 1-2 %
+            // faster on the monolayer and the molecule, 1 % slower on the slab;
+            // energy mode keeps the scalar path, where it cost registers)
+            const float2 tq = make_float2(in0 ? fminf(tD.x, K.tDclamp) : 0.0f, in1 ? fminf(tD.y, K.tDclamp) : 0.0f);
+            float2 p, pt, pu;
+            table_pair2<POT>(tb, tq, dp.l0, dp.l1, in0, in1, dp.wd, dp.dwd, p, pt, pu);
             A2 = add2(A2, p);
             if (POT) {
                 Srpt = fma2(rr, pt, Srpt);

@@ -17,7 +17,9 @@
 //   T = -1/2 dV^2 C sum_k hx s_k sum_{p, p'} K(p, p') F_k(p) F_k(p'),
 //   F_k(p) = sum over active points of plane p of (n / u) exp(-u s_k).
 // That is O(N_grid x nodes) work for the planes and O(planes^2 x nodes) for the
-// pairs of planes, instead of O(N_active^2): a few milliseconds in FP64.
+// pairs of planes, instead of O(N_active^2): a few milliseconds in FP64.  Its
+// potential (the derivative of T with the active mask frozen) comes from the
+// same sums, point by point (k_tail_AU), in the pair sum's adjoint form.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -87,10 +89,11 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_planes(int d0, int d1, in
 }
 
 // Tk[k] = sum_{p, p'} K(p, p') F_k(p) F_k(p') for node k = blockIdx.x, with
-// K(p, p') = c2 / max(rc, |p - p'| dz)^4 (two periodic axes) or c3 (three).
+// K(p, p') = c2 / max(rc, |p - p'| dz)^4 (two periodic axes) or c3 (three);
+// G (when given) keeps G_k(p) = sum_{p'} K(p, p') F_k(p') for the potential.
 __global__ void __launch_bounds__(kTailThreads) k_tail_pairs(int np, const double *__restrict__ F, double dz,
                                                              double rc, double c2, double c3,
-                                                             double *__restrict__ Tk) {
+                                                             double *__restrict__ Tk, double *__restrict__ G) {
     __shared__ double red[kTailThreads / 32];
     const double *f = F + static_cast<long long>(blockIdx.x) * np;
     double acc = 0.0;
@@ -106,6 +109,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_pairs(int np, const doubl
             }
             row += K * f[pp];
         }
+        if (G) G[static_cast<long long>(blockIdx.x) * np + p] = row;
         acc += f[p] * row;
     }
     acc = warp_sum_d(acc);
@@ -127,15 +131,73 @@ __global__ void k_tail_final(int nodes, const double *__restrict__ Tk, double x0
     *out = scale * s;
 }
 
+// The far field's potential in the pair sum's adjoint form, per grid point m:
+// with S0 = sum_k hx s_k e^{-u s_k} G_k(p) and S1 = sum_k hx s_k^2 e^{-u s_k} G_k(p)
+// (u = q0_m^2, p the plane of m),
+//   sum_j n_j f(u, u_j) K_mj = S0 / u,   sum_j n_j df/du K_mj = -S0 / u^2 - S1 / u,
+// f(a, b) = 1 / (a b (a + b)), since 1/(a + b) and 1/(a + b)^2 are the integrals of
+// e^{-(a + b) s} and s e^{-(a + b) s}.  A = -C S0 / u and U = -2 C n q (-S0/u^2 - S1/u)
+// at active points (slot[m] = m), slot[m] = -1 elsewhere.
+__global__ void __launch_bounds__(kTailThreads) k_tail_AU(int d0, int d1, int d2, int ax, int np,
+                                                          const double *__restrict__ n,
+                                                          const double *__restrict__ q0, double n_cut, double x0,
+                                                          double hx, int nodes, const double *__restrict__ G,
+                                                          double C, int *__restrict__ slot,
+                                                          double *__restrict__ A, double *__restrict__ U) {
+    extern __shared__ double s_nodes[];  // s_k = e^{x0 + k hx}, k < nodes
+    for (int k = threadIdx.x; k < nodes; k += blockDim.x) s_nodes[k] = exp(x0 + hx * k);
+    __syncthreads();
+    const long long N = static_cast<long long>(d0) * d1 * d2;
+    for (long long m = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; m < N;
+         m += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double nm = n[m];
+        if (!(nm >= n_cut)) {
+            slot[m] = -1;
+            continue;
+        }
+        int p = 0;
+        if (np > 1) {
+            const long long c2i = m % d2, c1i = (m / d2) % d1, c0i = m / (static_cast<long long>(d1) * d2);
+            p = static_cast<int>(ax == 0 ? c0i : (ax == 1 ? c1i : c2i));
+        }
+        const double q = q0[m];
+        const double u = q * q;
+        double S0 = 0.0, S1 = 0.0;
+        for (int k = 0; k < nodes; ++k) {
+            const double s = s_nodes[k];
+            const double t = hx * s * exp(-u * s) * G[static_cast<long long>(k) * np + p];
+            S0 += t;
+            S1 += s * t;
+        }
+        slot[m] = static_cast<int>(m);
+        A[m] = -C * S0 / u;
+        U[m] = -2.0 * C * nm * q * (-S0 / (u * u) - S1 / u);
+    }
+}
+
 }  // namespace
+
+int launch_far_tail_AU(const int dims[3], int ax, int np, const double *n, const double *q0, double n_cut,
+                       double x0, double hx, int nodes, const double *G, double C, int *slot, double *A,
+                       double *U, cudaStream_t st) {
+    const long long N = static_cast<long long>(dims[0]) * dims[1] * dims[2];
+    long long nb = (N + kTailThreads - 1) / kTailThreads;
+    if (nb > 152 * 16) nb = 152 * 16;
+    const size_t smem = sizeof(double) * static_cast<size_t>(nodes);  // at most 32 KB (4096 nodes)
+    k_tail_AU<<<static_cast<int>(nb), kTailThreads, smem, st>>>(dims[0], dims[1], dims[2], ax, np, n, q0, n_cut,
+                                                                x0, hx, nodes, G, C, slot, A, U);
+    count_launches(1);
+    VDWDF_CUDA_TRY(cudaGetLastError());
+    return VDWDF_OK;
+}
 
 int launch_far_tail(const int dims[3], int ax, int np, const double *n, const double *q0, double n_cut,
                     double x0, double hx, int nodes, double dz, double rc, double c2, double c3, double scale,
-                    double *F, double *Tk, double *out, cudaStream_t st) {
+                    double *F, double *Tk, double *G, double *out, cudaStream_t st) {
     const int chunks = (nodes + kTailChunk - 1) / kTailChunk;
     k_tail_planes<<<dim3(np, chunks), kTailThreads, 0, st>>>(dims[0], dims[1], dims[2], ax, np, n, q0, n_cut, x0,
                                                              hx, nodes, F);
-    k_tail_pairs<<<nodes, kTailThreads, 0, st>>>(np, F, dz, rc, c2, c3, Tk);
+    k_tail_pairs<<<nodes, kTailThreads, 0, st>>>(np, F, dz, rc, c2, c3, Tk, G);
     k_tail_final<<<1, 32, 0, st>>>(nodes, Tk, x0, hx, scale, out);
     count_launches(3);
     VDWDF_CUDA_TRY(cudaGetLastError());

@@ -94,3 +94,39 @@ def test_energy_plus_tail_converges_on_gpu(V, dev, oracle_table):
     d_direct = abs(Es[0] - Es[2]), abs(Es[1] - Es[2])
     d_tail = abs(Es[0] + Ts[0] - Es[2] - Ts[2]), abs(Es[1] + Ts[1] - Es[2] - Ts[2])
     assert d_tail[0] < 0.1 * d_direct[0] and d_tail[1] < 0.01 * d_direct[1], (d_direct, d_tail)
+
+
+@pytest.mark.parametrize("k", [0, 1, 3, 4, 5])
+def test_far_tail_potential_matches_oracle(V, dev, oracle_mod, oracle_spline, k):
+    """T's potential (dT/dn / dV, mask frozen) against the oracle's on the whole grid
+    (1e-10 of max|v_T|; 1e-9 with the FFT gradient): the monolayer, the skewed
+    hexagonal cell, three periodic axes, the FFT gradient and the periodic y, z
+    case."""
+    w = _cases()[k]
+    geom = w.get("cell", w["lengths"])
+    kind = w.get("gradient", "fd")
+    rc = 12.0
+    r, v = V.far_tail(_t(w["density"], dev), geom, w["periodic"], w["n_cut"], rc, gradient=kind, want_v=True)
+    P = oracle_mod.Problem(w["density"], w["lengths"], w["periodic"], w["n_cut"], rc, oracle_spline,
+                           cell=w.get("cell"), gradient=kind)
+    vo = P.far_tail_potential()
+    vg = v.cpu().numpy()
+    vmax = np.max(np.abs(vo))
+    assert vmax > 0
+    # the FFT gradient's rounding is absolute (every value sums a whole line) and
+    # v_T weights the low-density points, where dq0/dgrad n ~ 1/n^2, by about 1/q0^6:
+    # 1e-9 there (measured 2.5e-10), 1e-10 with the finite-difference gradient
+    tol = 1e-9 if kind == "spectral" else 1e-10
+    assert np.max(np.abs(vg - vo)) <= tol * vmax, (w["name"], np.max(np.abs(vg - vo)) / vmax)
+    assert abs(r["T"] - P.far_tail()) <= 1e-11 * abs(r["T"])
+
+
+def test_far_tail_potential_refuses_a_callers_gradient(V, dev):
+    import torch
+    from paper_0810_2273_gb300 import inputs
+    w = inputs.xe_monolayer((12, 21, 30))
+    n = _t(w["density"], dev)
+    g = torch.zeros((3,) + tuple(n.shape), dtype=torch.float64, device=n.device)
+    with pytest.raises(V.VdwdfError) as e:
+        V.far_tail(n, w["lengths"], w["periodic"], w["n_cut"], 20.0, grad=g, want_v=True)
+    assert e.value.status == -1
