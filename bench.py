@@ -241,6 +241,12 @@ def run_gpu(args):
     tail = {"T_hartree": tails[-1]["T"], "E_plus_T_hartree": results[-1][0] + tails[-1]["T"],
             "ms_per_call": float(np.median([t["ms"] for t in tails[1:]])), "nodes": tails[-1]["nodes"],
             "planes": tails[-1]["planes"], "bound": "fp64 (one exp per active point and quadrature node)"}
+    # the same at a 30 bohr cutoff (FP32 energy): E + T should hardly move
+    E30, _ = V.energy(n, w["lengths"], w["periodic"], w["n_cut"], 30.0, T, precision="fp32")
+    T30 = V.far_tail(n, w["lengths"], w["periodic"], w["n_cut"], 30.0)["T"]
+    tail["r_cut_30"] = {"E_hartree": E30, "T_hartree": T30, "E_plus_T_hartree": E30 + T30,
+                        "E_change_from_r_cut_20": E30 - results[-1][0],
+                        "E_plus_T_change_from_r_cut_20": E30 + T30 - tail["E_plus_T_hartree"]}
 
     ms, e2e, total_pairs = combine_ranks(ms, e2e, pairs, dev)
     if rank != 0:

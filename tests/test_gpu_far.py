@@ -130,3 +130,23 @@ def test_far_tail_potential_refuses_a_callers_gradient(V, dev):
     with pytest.raises(V.VdwdfError) as e:
         V.far_tail(n, w["lengths"], w["periodic"], w["n_cut"], 20.0, grad=g, want_v=True)
     assert e.value.status == -1
+
+
+def test_energy_plus_tail_converges_on_the_24x42x60_monolayer(V, dev, oracle_table, oracle_mod, oracle_spline):
+    """The monolayer on a 24x42x60 grid (38k active points), FP64 through the GPU: T
+    against the oracle, and E + T at r_cut = 20 and 30 bohr closer together than E
+    alone by more than a factor 20."""
+    from paper_0810_2273_gb300 import inputs
+    T = V.Table.from_nodes(oracle_table, 30.0)
+    w = inputs.xe_monolayer((24, 42, 60))
+    n = _t(w["density"], dev)
+    out = {}
+    for rc in (20.0, 30.0):
+        E = V.energy(n, w["lengths"], w["periodic"], w["n_cut"], rc, T, "fp64")[0]
+        out[rc] = (E, V.far_tail(n, w["lengths"], w["periodic"], w["n_cut"], rc)["T"])
+    P = oracle_mod.Problem(w["density"], w["lengths"], w["periodic"], w["n_cut"], 20.0, oracle_spline)
+    To = P.far_tail()
+    assert abs(out[20.0][1] - To) <= 1e-11 * abs(To)
+    d_direct = abs(out[20.0][0] - out[30.0][0])
+    d_tail = abs(sum(out[20.0]) - sum(out[30.0]))
+    assert d_tail < 0.05 * d_direct, (out, d_direct, d_tail)
