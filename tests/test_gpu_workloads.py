@@ -254,7 +254,7 @@ def test_slab_full_sampled(V, dev, gtable, oracle_mod, oracle_spline):
     """128x112x200 periodic slab + flake: FP32 E + v at full size with A, U at 12
     sampled points and v at 20 (active, and inactive next to active) against the
     oracle; FP32 vs FP64 E on a 64x56x100 regrid (the FP64 pass at full size takes
-    about 7 minutes)."""
+    about 11 minutes)."""
     from paper_0810_2273_gb300 import inputs
     w = inputs.slab_adsorbate()
     n = _t(w["density"], dev)
