@@ -1,7 +1,7 @@
 """Run one standard workload through the library and print per-call timings.
 
     python -m paper_0810_2273_gb300.run_case --workload xe_monolayer \
-        [--dims 24 42 60] [--mode potential|energy|semilocal|diag|gradient|tail]
+        [--dims 24 42 60] [--mode potential|energy|semilocal|diag|gradient|tail|compare]
         [--precision fp32|fp64] [--gradient fd|spectral] [--repeat 3]
 
 Workloads are the seeded densities of ``paper_0810_2273_gb300.inputs``
@@ -20,7 +20,7 @@ def main(argv=None):
                     choices=["kr_dimer", "xe_monolayer", "xe_monolayer_hex", "molecule24", "slab_adsorbate"])
     ap.add_argument("--dims", type=int, nargs=3, default=None)
     ap.add_argument("--mode", default="potential",
-                    choices=["potential", "energy", "semilocal", "diag", "gradient", "tail"])
+                    choices=["potential", "energy", "semilocal", "diag", "gradient", "tail", "compare"])
     ap.add_argument("--gradient", default="fd", choices=["fd", "spectral"], help="the library's density gradient")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--repeat", type=int, default=3)
@@ -56,6 +56,20 @@ def main(argv=None):
             print(json.dumps(dict(call=k, ms=e0.elapsed_time(e1), wall_ms=1e3 * (time.perf_counter() - t0),
                                   workload=a.workload, dims=list(n.shape), mode=a.mode, gradient=a.gradient,
                                   max_abs=float(g.abs().max()))), flush=True)
+            continue
+        if a.mode == "compare":
+            # the FP32 and FP64 paths on the same density: E relative and v max-norm
+            # relative differences, pair counts, and each path's pair-kernel time
+            E32, v32, r32 = V.potential(n, *args, precision="fp32", gradient=a.gradient)
+            E64, v64, r64 = V.potential(n, *args, precision="fp64", gradient=a.gradient)
+            torch.cuda.synchronize()
+            vmax = float(v64.abs().max())
+            print(json.dumps(dict(call=k, workload=a.workload, dims=list(n.shape), mode=a.mode,
+                                  E32=E32, E64=E64, E_rel=abs(E32 - E64) / abs(E64),
+                                  v_maxnorm_rel=float((v32 - v64).abs().max()) / vmax,
+                                  pairs32=r32["pairs"], pairs64=r64["pairs"],
+                                  ms_pairs32=r32["ms_pairs"], ms_pairs64=r64["ms_pairs"],
+                                  wall_ms=1e3 * (time.perf_counter() - t0))), flush=True)
             continue
         if a.mode == "tail":
             res = V.far_tail(n, cell, w["periodic"], w["n_cut"], w["r_cut"], gradient=a.gradient)
