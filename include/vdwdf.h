@@ -353,7 +353,8 @@ typedef struct {
  * grid as in vdwdf_energy with exactly two or three periodic axes; grad_dev
  * as in vdwdf_q0, and NULL when v_dev is given (the potential needs the
  * library's own gradient); r_cut > 0.  Synchronises the stream.
- * Errors: VDWDF_EINVAL (bad argument, r_cut <= 0, grad_dev with v_dev),
+ * Errors: VDWDF_EINVAL (bad argument, r_cut <= 0, grad_dev with v_dev, a
+ * non-finite T from a non-finite density; v_dev is then unspecified),
  * VDWDF_EUNSUPPORTED (fewer than two periodic axes, or a q0 range needing
  * more than 4096 nodes), VDWDF_ECUDA, VDWDF_EALLOC. */
 int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,

@@ -1486,6 +1486,7 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
         tm.mark(1, st);
         VDWDF_CUDA_TRY(cudaMemcpyAsync(&T, Tout, sizeof(double), cudaMemcpyDeviceToHost, st));
         VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!std::isfinite(T)) return VDWDF_EINVAL;  // a non-finite density (as vdwdf_energy)
         return VDWDF_OK;
     };
     rc = body();

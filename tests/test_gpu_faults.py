@@ -34,7 +34,8 @@ def test_allocation_failure_hook(V, setup, monkeypatch):
     n, args, E0, r0 = setup
     monkeypatch.setenv("VDWDF_FAIL_ALLOC", "1")
     for call in (lambda: V.energy(n, *args), lambda: V.potential(n, *args),
-                 lambda: V.semilocal(n, args[0], args[1])):
+                 lambda: V.semilocal(n, args[0], args[1]),
+                 lambda: V.far_tail(n, args[0], args[1], args[2], args[3])):
         with pytest.raises(V.VdwdfError) as e:
             call()
         assert e.value.status == -4  # VDWDF_EALLOC
@@ -68,6 +69,9 @@ def test_nonfinite_density_is_rejected(V, setup):
     with pytest.raises(V.VdwdfError) as e:
         V.energy(bad, *args)
     assert e.value.status == -1  # VDWDF_EINVAL
+    with pytest.raises(V.VdwdfError) as e:
+        V.far_tail(bad, args[0], args[1], args[2], args[3])
+    assert e.value.status == -1
     bad = n.clone()
     idx = torch.nonzero(n >= args[2])[0]
     bad[tuple(idx.tolist())] = float("nan")
