@@ -43,7 +43,7 @@ def test_struct_layouts_match_header(native, tmp_path):
     import subprocess
     fields = {"vdwdf_grid": native.vdwdf_grid, "vdwdf_result": native.vdwdf_result,
               "vdwdf_tuning": native.vdwdf_tuning, "vdwdf_semilocal_result": native.vdwdf_semilocal_result,
-              "vdwdf_diag_result": native.vdwdf_diag_result}
+              "vdwdf_diag_result": native.vdwdf_diag_result, "vdwdf_tail_result": native.vdwdf_tail_result}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "vdwdf.h"', "int main(void) {"]
     for s, cls in fields.items():
         src.append('printf("%s size %%zu\\n", sizeof(%s));' % (s, s))
