@@ -44,10 +44,13 @@ def _cases():
     side = inputs.xe_monolayer((12, 21, 30))
     side["name"] = "periodic along the second and third axes"
     side["periodic"] = (False, True, True)
-    return [mono, hexa, slab, bulk, spec, side]
+    hex3 = inputs.xe_monolayer_hex((16, 16, 40))
+    hex3["name"] = "skewed cell, three periodic axes"
+    hex3["periodic"] = (True, True, True)
+    return [mono, hexa, slab, bulk, spec, side, hex3]
 
 
-@pytest.mark.parametrize("k", range(6))
+@pytest.mark.parametrize("k", range(7))
 def test_far_tail_matches_oracle(V, dev, oracle_mod, oracle_spline, k):
     w = _cases()[k]
     geom = w.get("cell", w["lengths"])
@@ -96,12 +99,12 @@ def test_energy_plus_tail_converges_on_gpu(V, dev, oracle_table):
     assert d_tail[0] < 0.1 * d_direct[0] and d_tail[1] < 0.01 * d_direct[1], (d_direct, d_tail)
 
 
-@pytest.mark.parametrize("k", [0, 1, 3, 4, 5])
+@pytest.mark.parametrize("k", [0, 1, 3, 4, 5, 6])
 def test_far_tail_potential_matches_oracle(V, dev, oracle_mod, oracle_spline, k):
     """T's potential (dT/dn / dV, mask frozen) against the oracle's on the whole grid
     (1e-10 of max|v_T|; 1e-9 with the FFT gradient): the monolayer, the skewed
-    hexagonal cell, three periodic axes, the FFT gradient and the periodic y, z
-    case."""
+    hexagonal cell, three periodic axes, the FFT gradient, the periodic y, z
+    case and the skewed cell with three periodic axes."""
     w = _cases()[k]
     geom = w.get("cell", w["lengths"])
     kind = w.get("gradient", "fd")
