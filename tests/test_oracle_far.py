@@ -148,3 +148,31 @@ def test_tail_potential_is_derivative_of_tail(oracle_mod, oracle_spline, periodi
             return oracle_mod.Problem(nn.reshape(dims), L, periodic, n_cut, rc, oracle_spline).far_tail()
         fd = (T_at(hstep) - T_at(-hstep)) / (2 * hstep) / P.dV
         assert abs(fd - v.ravel()[m]) < 1e-6 * np.max(np.abs(v)), (m, fd, v.ravel()[m])
+
+
+def test_tail_potential_is_derivative_of_tail_skewed(oracle_mod, oracle_spline):
+    """The same on a skewed cell (periodic along its first two lattice vectors, the
+    third tilted), where the planes' normal separation comes from the cell."""
+    rng = np.random.default_rng(43)
+    dims = (8, 9, 10)
+    cell = np.array([[6.0, 0.0, 0.0], [2.5, 6.2, 0.0], [1.0, -0.8, 7.0]])
+    n = 0.02 + 0.5 * rng.uniform(0, 1, size=dims) * np.exp(-rng.uniform(0, 3, size=dims))
+    n_cut = 0.05
+    n[np.abs(n - n_cut) < 0.01] += 0.03
+    rc = 5.0
+    per = (1, 1, 0)
+    P = oracle_mod.Problem(n, None, per, n_cut, rc, oracle_spline, cell=cell)
+    v = P.far_tail_potential()
+    flat = n.ravel()
+    act = np.nonzero(flat >= 2 * n_cut)[0]
+    ina = np.nonzero(flat < 0.5 * n_cut)[0]
+    pts = np.concatenate([rng.choice(act, 5, replace=False), rng.choice(ina, 3, replace=False)])
+    for m in pts:
+        hstep = 1e-4 * flat[m]
+
+        def T_at(delta):
+            nn = flat.copy()
+            nn[m] += delta
+            return oracle_mod.Problem(nn.reshape(dims), None, per, n_cut, rc, oracle_spline, cell=cell).far_tail()
+        fd = (T_at(hstep) - T_at(-hstep)) / (2 * hstep) / P.dV
+        assert abs(fd - v.ravel()[m]) < 1e-6 * np.max(np.abs(v)), (m, fd, v.ravel()[m])
