@@ -221,6 +221,16 @@ def run_gpu(args):
     torch.cuda.synchronize()
     fp64_s = 1e-3 * e64a.elapsed_time(e64b)
 
+    # the GPU's own arithmetic rates (FMA microbenchmarks, outside the timed steps),
+    # with the SM clock sampled meanwhile: the measured denominators of the ALU rooflines
+    rsamp = ClockSampler(local)
+    rsamp.start()
+    lane = {}
+    for kind in ("fp32", "fp32x2", "fp64"):
+        V.lane_rate(kind, 20.0, dev)
+        lane[kind] = V.lane_rate(kind, 200.0, dev)
+    rclocks = rsamp.stop()
+
     # the semilocal terms of eq. 3 on the same density (outside the timed steps; the
     # call's own CUDA events, L2 flushed before each call)
     semi_ms = []
@@ -257,6 +267,13 @@ def run_gpu(args):
     value = total_pairs / (ms * 1e-3)
     sm_mhz = clocks["sm_mhz"] if clocks else None
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    r_mhz = (rclocks or {}).get("sm_mhz") or 2070.0
+    lane_rates = {k: {"T_lane_ops_per_s": r / 1e12, "ms": t, "per_sm_per_clock": r / (sms * r_mhz * 1e6)}
+                  for k, (r, t) in lane.items()}
+    lane_rates["clocks"] = rclocks
+    lane_rates["note"] = ("vdwdf_lane_rate: every SM full of 512-thread blocks, 8 independent FMA chains "
+                          "per thread; one FMA of one lane = 1 lane operation (2 per packed FP32x2 FMA)")
+    fp64_peak = lane["fp64"][0] / 1e12
     clk, clk_basis = (sm_mhz, "median SM clock sampled during the timed steps") if sm_mhz else \
         (2070.0, "maximum SM clock (no clock samples)")
     peak = sms * FP32_LANES_PER_SM * clk * 1e6 / 1e12
@@ -272,7 +289,7 @@ def run_gpu(args):
         except (OSError, ValueError):
             pass
     cpu = oracle_sample(w, T, seconds=args.cpu_seconds)
-    wl = None if args.no_workloads else run_workloads(V, inputs, T, dev, flush, sms)
+    wl = None if args.no_workloads else run_workloads(V, inputs, T, dev, flush, sms, fp64_peak)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -284,14 +301,22 @@ def run_gpu(args):
         "fp64_path": {"value": pairs / fp64_s, "unit": UNIT, "E_hartree": E64,
                       "rel_err_fp32_vs_fp64": abs(results[-1][0] - E64) / abs(E64),
                       "seconds": fp64_s, "fp32_over_fp64": value / (pairs / fp64_s),
-                      "timing": "CUDA events around one call, after an FP64 warm-up call on a 12x21x30 grid"},
+                      "timing": "CUDA events around one call, after an FP64 warm-up call on a 12x21x30 grid",
+                      "roofline": {"bound": "alu", "achieved": OPS_PER_PAIR_EV * pairs / fp64_s / 1e12,
+                                   "peak": fp64_peak, "unit": "T fp64-lane-ops/s",
+                                   "frac": OPS_PER_PAIR_EV * pairs / fp64_s / 1e12 / fp64_peak,
+                                   "ops_per_pair": OPS_PER_PAIR_EV,
+                                   "peak_basis": "measured FP64 FMA rate (lane_rates.fp64)"}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T fp32-lane-ops/s",
                      "frac": achieved / peak, "traffic": prof_traffic,
                      "kernel": "k_pair<float, potential, %d>" % results[-1][1]["pair_threads"],
                      "ms_per_launch": pms,
                      "ops_per_pair": OPS_PER_PAIR_EV,
                      "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (%s)" % (sms, FP32_LANES_PER_SM, clk,
-                                                                                clk_basis)},
+                                                                                clk_basis),
+                     "peak_measured_fp32_fma": lane["fp32"][0] / 1e12,
+                     "frac_of_measured_fp32_fma": achieved / (lane["fp32"][0] / 1e12)},
+        "lane_rates": lane_rates,
         "semilocal": {"ms_per_call": semi_t, "points": int(n.numel()),
                       "points_per_s": n.numel() / (semi_t * 1e-3),
                       "hbm_gbs": 8.0 * n.numel() / (semi_t * 1e-3) / 1e9,
@@ -312,12 +337,13 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
-def run_workloads(V, inputs, T, dev, flush, sms):
+def run_workloads(V, inputs, T, dev, flush, sms, fp64_peak):
     """Every standard workload in the launch configuration the library uses by
     default: pair interactions/s from the pair kernel's CUDA-event time (the
     call's ms_pairs; for the batched graph the replay's whole time), L2 flushed
     before each timed call, the fraction of the FP32 lane peak at the SM clock
-    sampled during these runs, and the FP64 path on the same input."""
+    sampled during these runs, and the FP64 path on the same input with its
+    fraction of the measured FP64 FMA rate (fp64_peak, T lane operations/s)."""
     import torch
 
     def to_dev(wk):
@@ -391,12 +417,14 @@ def run_workloads(V, inputs, T, dev, flush, sms):
     clk = clocks["sm_mhz"] if clocks else 2070.0
     peak = sms * FP32_LANES_PER_SM * clk * 1e6 / 1e12
 
-    def rate(t, ops):
+    def rate(t, ops, ops64=None):
         ms, pairs, E, r = t
         d = {"pairs_per_s": pairs / (ms * 1e-3), "ms_pairs": ms, "pairs": int(pairs), "E_hartree": E,
              "pair_threads": r.get("pair_threads")}
         if ops:
             d["frac"] = ops * pairs / (ms * 1e-3) / 1e12 / peak
+        if ops64:
+            d["frac_of_measured_fp64"] = ops64 * pairs / (ms * 1e-3) / 1e12 / fp64_peak
         return d
 
     out = {"clocks": clocks, "peak_T_lane_ops": peak,
@@ -406,7 +434,7 @@ def run_workloads(V, inputs, T, dev, flush, sms):
         ops = OPS_PER_PAIR_EV if d["mode"] == "potential" else OPS_PER_PAIR_E
         e = {"workload": d["workload"], "fp32": rate(d["f32"], ops)}
         if "f64" in d:
-            e["fp64"] = rate(d["f64"], None)
+            e["fp64"] = rate(d["f64"], None, ops)
             e["fp32_over_fp64"] = e["fp32"]["pairs_per_s"] / e["fp64"]["pairs_per_s"]
             e["rel_err_fp32_vs_fp64"] = abs(d["f32"][2] - d["f64"][2]) / abs(d["f64"][2])
         if "f32_auto" in d:
@@ -415,7 +443,7 @@ def run_workloads(V, inputs, T, dev, flush, sms):
                              "batched_auto_over_default": d["f32_auto"][0] and d["f32"][0] / d["f32_auto"][0]}
         if "f64_regrid" in d:
             e["fp32_64x56x100"] = rate(d["f32_regrid"], ops)
-            e["fp64_64x56x100"] = rate(d["f64_regrid"], None)
+            e["fp64_64x56x100"] = rate(d["f64_regrid"], None, ops)
             e["fp32_over_fp64"] = e["fp32_64x56x100"]["pairs_per_s"] / e["fp64_64x56x100"]["pairs_per_s"]
             e["rel_err_fp32_vs_fp64"] = abs(d["f32_regrid"][2] - d["f64_regrid"][2]) / abs(d["f64_regrid"][2])
             e["fp64_note"] = "the FP64 E + v pass at full size takes about 11 min; ratio on the 64x56x100 regrid"

@@ -486,6 +486,31 @@ int vdwdf_version(void);
 /* Number of kernels this library has launched in this process. */
 int64_t vdwdf_launch_count(void);
 
+/* Arithmetic rate of the current device, measured: the denominators of the
+ * pair kernels' rooflines.  The pair sum (section 2, eq. (2)) is a
+ * gather-and-interpolate on the CUDA cores, so its ceiling is a rate of lane
+ * operations (one fused multiply-add of one lane counts as one), not a tensor
+ * or memory rate.
+ *  kind:           VDWDF_RATE_FP32 (FP32 FMA), VDWDF_RATE_FP32X2 (packed
+ *                  FP32x2 FMA, two lane operations per instruction) or
+ *                  VDWDF_RATE_FP64 (FP64 FMA).
+ *  target_ms:      duration of the timed launch, 1..1000 ms.
+ *  lane_ops_per_s: out (host), lane operations per second over the whole
+ *                  device.
+ *  ms_out:         out (host, may be NULL), the timed launch's duration.
+ * Every SM runs as many 512-thread blocks as fit at once, each thread 8
+ * independent FMA chains, so the launch measures the pipe's throughput.  One
+ * calibration launch sizes the timed one; both are timed with CUDA events on
+ * the stream, which the call synchronises.  A 16-byte device scratch is
+ * allocated on the stream and freed before return.
+ * Errors: VDWDF_EINVAL for an unknown kind, a NULL lane_ops_per_s or a
+ * target_ms outside 1..1000 (checked before any CUDA call); VDWDF_EALLOC;
+ * VDWDF_ECUDA. */
+#define VDWDF_RATE_FP32 0
+#define VDWDF_RATE_FP32X2 1
+#define VDWDF_RATE_FP64 2
+int vdwdf_lane_rate(int kind, double target_ms, double *lane_ops_per_s, double *ms_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ from ._native import (VDWDF_FP32, VDWDF_FP64, VdwdfError, vdwdf_diag_result, vdw
 
 __all__ = ["Table", "grid", "energy", "energy_noalloc", "potential", "energy_batched", "q0", "kernel_eval",
            "semilocal", "total_energy_nl", "far_tail", "phi0_eval", "diag_voxel", "diag_voxel_potential",
-           "autotune", "launch_count", "NonlocalEnergy", "nonlocal_energy", "VdwdfError",
+           "autotune", "launch_count", "lane_rate", "NonlocalEnergy", "nonlocal_energy", "VdwdfError",
            "VDWDF_FP32", "VDWDF_FP64"]
 
 
@@ -418,6 +418,27 @@ def autotune(n, lengths, periodic, n_cut, r_cut, table, precision="fp32", gradie
 def launch_count():
     """Kernels the library has launched in this process."""
     return int(_native.load().vdwdf_launch_count())
+
+
+LANE_RATE_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
+
+
+def lane_rate(kind="fp32", target_ms=20.0, device=None):
+    """Measured arithmetic rate of the device (vdwdf_lane_rate): lane operations
+    per second for kind "fp32" (FMA), "fp32x2" (packed FMA, two lane operations
+    per instruction) or "fp64" (FMA), and the timed launch's milliseconds."""
+    if kind not in LANE_RATE_KINDS:
+        raise ValueError("kind must be one of %s" % sorted(LANE_RATE_KINDS))
+    torch = _torch()
+    lib = _native.load()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    with torch.cuda.device(dev):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        st = lib.vdwdf_lane_rate(LANE_RATE_KINDS[kind], float(target_ms), ctypes.byref(rate), ctypes.byref(ms),
+                                 stream)
+    _native.check(st, "vdwdf_lane_rate")
+    return rate.value, ms.value
 
 
 def _make_function():

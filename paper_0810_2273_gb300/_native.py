@@ -99,6 +99,7 @@ PROTOTYPES = {
     "vdwdf_strerror": (ctypes.c_char_p, [_c_i]),
     "vdwdf_version": (_c_i, []),
     "vdwdf_launch_count": (_c_i64, []),
+    "vdwdf_lane_rate": (_c_i, [_c_i, _c_d, _c_p, _c_p, _c_p]),
 }
 
 _LIB = None

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvdwdf.so")
 
-CU_SOURCES = ["api.cu", "pair.cu", "prep.cu", "assemble.cu", "spectral.cu", "tail.cu"]
+CU_SOURCES = ["api.cu", "pair.cu", "prep.cu", "assemble.cu", "spectral.cu", "tail.cu", "peak.cu"]
 CXX_SOURCES = ["table.cpp"]
 HEADERS = ["common.cuh", "table.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

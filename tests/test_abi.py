@@ -147,6 +147,13 @@ def test_host_side_argument_errors(native):
     g.n[0], g.n[1], g.n[2] = 64, 64, 17
     assert lib.vdwdf_energy_noalloc(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1),
                                     0, ctypes.byref(res), None) == -2
+    # lane-rate measurement: unknown kind, no output, duration outside 1..1000 ms
+    rate = ctypes.c_double()
+    assert lib.vdwdf_lane_rate(3, 20.0, ctypes.byref(rate), None, None) == -1
+    assert lib.vdwdf_lane_rate(-1, 20.0, ctypes.byref(rate), None, None) == -1
+    assert lib.vdwdf_lane_rate(0, 20.0, None, None, None) == -1
+    for ms in (0.5, 1001.0, float("nan")):
+        assert lib.vdwdf_lane_rate(2, ms, ctypes.byref(rate), None, None) == -1
 
 
 def test_table_build_matches_oracle_quadrature(oracle_mod):
