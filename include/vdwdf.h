@@ -110,9 +110,11 @@ typedef struct {
  *  - 0 <= D <= Dmax: the tensor-product interpolating cubic spline of the
  *    nodes, zero slope at D = 0 and delta = 0, zero curvature at the last
  *    node of each axis;
- *  - D > Dmax: Dion eq. 17 times rho(delta), the cubic spline (same end
- *    conditions) of phi(Dmax, delta_l) / eq. 17 (Dmax, delta_l), so that the
- *    kernel is continuous at Dmax for every delta;
+ *  - D > Dmax: Dion eq. 17 times g = rho(delta*) + (1 - rho(0)) (1 - (Dmax/D)^2),
+ *    delta* = max(0, 1 - min(d1, d2)/Dmax), with rho the cubic spline (same
+ *    end conditions) of phi(Dmax, delta_l) / eq. 17 (Dmax, delta_l): the
+ *    kernel is continuous at Dmax for every delta, and g tends to 1 (the
+ *    kernel to eq. 17) as both d1 and d2 grow;
  *  - delta above the last node: the spline's linear continuation in delta
  *    (its curvature is zero there), counted in vdwdf_result.n_clamped. */
 typedef struct vdwdf_table vdwdf_table;
@@ -229,6 +231,10 @@ int vdwdf_gradient(const vdwdf_grid *grid, const double *n_dev, double *grad_dev
  * periodic); r_cut <= 0 means no cutoff for open cells.  grad_dev as in
  * vdwdf_q0.  A pair is inside the cutoff iff |r_i - r_j + L|^2 <= r_cut^2 (1 + 1e-12)
  * (distances equal to r_cut up to rounding count as inside, in both precisions).
+ * Image shifts run over |m_a| <= M_a = ceil(r_cut |B_a|) + 1 along each
+ * periodic axis a (B_a the reciprocal row, |B_a| = 1/L_a on a diagonal cell);
+ * M_a above 64 (a cutoff more than about 63 cell lengths) returns VDWDF_EINVAL
+ * before any device work.
  * precision: VDWDF_FP32 or VDWDF_FP64.  Synchronises the stream.
  * Errors: VDWDF_EINVAL, VDWDF_EUNSUPPORTED, VDWDF_ENOTABLE, VDWDF_ECUDA,
  * VDWDF_EALLOC, VDWDF_ETIMEOUT. */

@@ -87,6 +87,11 @@ def test_host_side_argument_errors(native):
     assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1), 0,
                             None, ctypes.byref(res), None) == -1
     g.periodic[0] = 0
+    # more than 64 image shifts along a periodic axis (r_cut of 70 cell lengths)
+    g.periodic[0] = 1
+    assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 700.0, ctypes.c_void_p(1), 0,
+                            None, ctypes.byref(res), None) == -1
+    g.periodic[0] = 0
     # non-positive density cutoff, bad precision
     assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 0.0, 0.0, ctypes.c_void_p(1), 0,
                             None, ctypes.byref(res), None) == -1
@@ -97,8 +102,13 @@ def test_host_side_argument_errors(native):
     assert lib.vdwdf_energy(ctypes.byref(g), ctypes.c_void_p(8), None, 1e-6, 0.0, ctypes.c_void_p(1), 0,
                             None, ctypes.byref(res), None) == -1
     g.cell[1][0], g.cell[1][1] = 0.0, 10.0
-    # batched: bad count
+    # batched: bad count (at least 1, at most 4096 instances)
     assert lib.vdwdf_energy_batched(0, None, None, 1e-6, 0.0, ctypes.c_void_p(1), 0, None, None, None,
+                                    None) == -1
+    gs = (native.vdwdf_grid * 4097)(*([g] * 4097))
+    ptrs = (ctypes.c_void_p * 4097)(*([8] * 4097))
+    E_out = (ctypes.c_double * 4097)()
+    assert lib.vdwdf_energy_batched(4097, gs, ptrs, 1e-6, 0.0, ctypes.c_void_p(1), 0, None, E_out, None,
                                     None) == -1
     # semilocal energies: null density or result, singular cell
     sres = native.vdwdf_semilocal_result()

@@ -102,3 +102,34 @@ def test_more_plans_than_the_cache_holds(V, dev, oracle_table):
             Eb, _ = V.energy_batched([x], [L], [(0, 0, 0)], 1e-6, 0.0, table, "fp64")
             assert abs(Eb[0] - ref[k]) <= 1e-10 * abs(ref[k]), (rounds, k)
     table.free()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-6)])
+def test_more_instances_than_one_launch_holds(V, dev, oracle_table, prec, tol):
+    """Thirty uneven densities (one pair launch holds 24, so two launches in one
+    graph), among them one with no point above the cutoff and one with a single
+    point, against one-at-a-time calls; then the graph's replay with new values."""
+    table = V.Table.from_nodes(oracle_table, 30.0)
+    rng = np.random.default_rng(30)
+    shapes = [tuple(int(x) for x in rng.integers(8, 15, 3)) for _ in range(30)]
+    Ls = [tuple(0.55 * d for d in s) for s in shapes]
+    hosts = [_blob(s, L, 40 + k) for k, (s, L) in enumerate(zip(shapes, Ls))]
+    hosts[7] = np.full(shapes[7], 1e-8)              # nothing above the cutoff
+    hosts[19] = np.full(shapes[19], 1e-8)
+    hosts[19][3, 4, 5] = 0.3                         # a single active point
+    ns = [_t(h, dev) for h in hosts]
+    per = [(0, 0, 0)] * 30
+    for scale in (1.0, 1.25):
+        if scale != 1.0:
+            for x in ns:
+                x.mul_(scale)                        # same tensors: the recorded graph replays
+        Eb, _ = V.energy_batched(ns, Ls, per, 1e-6, 0.0, table, prec)
+        for k in range(30):
+            Es, res = V.energy(ns[k], Ls[k], per[k], 1e-6, 0.0, table, prec)
+            if k == 7:
+                assert Eb[k] == 0.0 and Es == 0.0 and res["n_active"] == 0
+                continue
+            if k == 19:
+                assert res["n_active"] == 1 and res["pairs"] == 0
+            assert abs(Eb[k] - Es) <= tol * abs(Es), (scale, k, Eb[k], Es)
+    table.free()
