@@ -256,8 +256,9 @@ int vdwdf_potential(const vdwdf_grid *grid, const double *n_dev, double n_cut, d
                     double *v_dev, double *A_dev, double *U_dev, vdwdf_result *out,
                     void *cuda_stream);
 
-/* E_c^nl of ninst independent densities (grids[k], n_dev[k]) in one
- * persistent launch of the pair kernel, recorded once into a CUDA graph and
+/* E_c^nl of ninst independent densities (grids[k], n_dev[k]), 1 <= ninst <=
+ * 4096, in one persistent launch of the pair kernel per 24 instances (in
+ * order: instances 0..23, 24..47, ...), recorded once into a CUDA graph and
  * replayed on later calls that would record the same graph: the same device,
  * pointers, shapes, cells, periodicity, gradient kind, cutoffs, precision,
  * tuning and table (binding curves, section 6.1).  Up to 8 recorded graphs are

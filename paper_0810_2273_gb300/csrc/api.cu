@@ -914,7 +914,7 @@ const char *vdwdf_strerror(int s) {
     switch (s) {
         case VDWDF_OK: return "ok";
         case VDWDF_EINVAL: return "invalid argument";
-        case VDWDF_EUNSUPPORTED: return "unsupported input (non-orthorhombic cell)";
+        case VDWDF_EUNSUPPORTED: return "valid input beyond what this entry point supports";
         case VDWDF_ECUDA: return "CUDA runtime error";
         case VDWDF_EALLOC: return "allocation failed";
         case VDWDF_ETIMEOUT: return "device work loop hit its iteration cap";

@@ -279,8 +279,9 @@ int build_phi_nodes(int nD, double Dmax, int ndelta, int level, double *nodes) {
 }
 
 void rho_coefficients(int nD, double Dmax, int nd, const double *nodes, double *coef) {
-    // rho(delta_l) = phi(Dmax, delta_l) / phi17(Dmax, delta_l): the large-D branch is
-    // eq. (17) times the cubic spline of rho, continuous with the table at Dmax.
+    // rho(delta_l) = phi(Dmax, delta_l) / phi17(Dmax, delta_l).  Past Dmax the kernel is
+    // eq. (17) times g = rho(delta*) + (1 - rho(0)) (1 - (Dmax/D)^2) with the cubic
+    // spline of rho, so that it is continuous with the table at Dmax.
     const double C = 12.0 * std::pow(4.0 * kPi / 9.0, 3);
     std::vector<double> r(nd), cp, dp;
     for (int l = 0; l < nd; ++l) {

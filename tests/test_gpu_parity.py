@@ -162,7 +162,7 @@ def test_potential_far_pairs(V, dev, gtable, oracle_mod, oracle_spline, prec, to
     """A metal-like slab under a 20 bohr cutoff on a coarse 24x20x40 grid: dense
     layers (q0 up to ~4) put almost half of the pairs at D above 30 258/399 (past
     the table rows the FP32 kernel keeps in shared memory) and a tenth past the
-    table (D > 30, eq. 17 times rho).  E, A, U and v against the oracle."""
+    table (D > 30, eq. 17 times the factor g).  E, A, U and v against the oracle."""
     from paper_0810_2273_gb300 import inputs
     w = inputs.slab_adsorbate((24, 20, 40))
     P = _problem(oracle_mod, oracle_spline, w)
