@@ -257,3 +257,41 @@ def test_autograd_function(V, dev, gtable):
     _, v, _ = V.potential(n.detach(), w["lengths"], w["periodic"], w["n_cut"], w["r_cut"], gtable, "fp64")
     dV = np.prod(w["lengths"]) / n.numel()
     assert torch.allclose(n.grad, dV * v, rtol=1e-12, atol=1e-14 * float(torch.max(torch.abs(dV * v))))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_every_pattern_of_periodic_axes(V, dev, gtable, oracle_mod, oracle_spline, prec, tol):
+    """One and two periodic axes in every direction (a wire along each axis, a
+    slab normal to each axis) and a skewed cell periodic along its second axis
+    only: E, v, A, U and the pair count against the oracle.  Each pattern drops
+    the images of different axes, which the culling and the image lists must
+    follow."""
+    from paper_0810_2273_gb300 import inputs
+    rng = np.random.default_rng(77)
+    dims, L = (10, 11, 12), (8.0, 8.8, 9.6)
+    atoms = [(tuple(rng.uniform(0.2, 0.8, 3) * np.asarray(L)), inputs.single_exponential(z, a))
+             for z, a in ((6.0, 0.7), (4.0, 0.6), (1.0, 0.5))]
+    patterns = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1)]
+    for per in patterns:
+        n = inputs.density(dims, L, atoms, periodic=per)
+        P = oracle_mod.Problem(n, L, per, 1e-4, 9.0, oracle_spline)
+        e = P.energy()
+        vo = P.potential(e["A"], e["U"])
+        E, v, res, A, U = V.potential(_t(n, dev), L, per, 1e-4, 9.0, gtable, prec, want_AU=True)
+        assert _relerr(E, e["E"]) < (tol if prec == "fp64" else 1e-6), (per, E, e["E"])
+        assert res["pairs"] == e["pairs"], per
+        v = v.cpu().numpy()
+        assert np.max(np.abs(v - vo)) < tol * np.max(np.abs(vo)), per
+        act = n.ravel() >= 1e-4
+        assert np.max(np.abs(A.cpu().numpy().ravel()[act] - e["A"])) < tol * np.max(np.abs(e["A"])), per
+        assert np.max(np.abs(U.cpu().numpy().ravel()[act] - e["U"])) < tol * np.max(np.abs(e["U"])), per
+    cell = np.array([[8.0, 0.0, 0.0], [3.0, 8.8, 0.0], [1.0, -0.5, 9.6]])
+    per = (0, 1, 0)
+    n = inputs.density_cell(dims, cell, atoms, periodic=per)
+    P = oracle_mod.Problem(n, None, per, 1e-4, 9.0, oracle_spline, cell=cell)
+    e = P.energy()
+    vo = P.potential(e["A"], e["U"])
+    E, v, res = V.potential(_t(n, dev), cell, per, 1e-4, 9.0, gtable, prec)
+    assert _relerr(E, e["E"]) < (tol if prec == "fp64" else 1e-6), ("skewed", E, e["E"])
+    assert res["pairs"] == e["pairs"]
+    assert np.max(np.abs(v.cpu().numpy() - vo)) < tol * np.max(np.abs(vo))
