@@ -548,10 +548,11 @@ Launch choose_launch(int precision, bool pot, const vdwdf_tuning *tu, const vdwd
     Launch ln;
     const int S = t->nd + 2;
     // Default shape: 512 threads, and for FP32 E + v 448 (384 on skewed cells).  The
-    // potential pass holds more live values: with 146 registers a thread it ran
-    // 1-2 % faster than with 128 (512 threads) or with fewer warps (384); the
-    // skewed instance, with its cross terms, was fastest at 384 and 8 % slower at
-    // 448.  Energy mode needs fewer registers and gains from the extra warps.
+    // potential pass ran 1-3 % faster with 14 warps (448 threads) than with 16 (512)
+    // or 12 (384); 448 and 512 threads both cap a thread at 128 registers (up to
+    // four warps share one scheduler's 16384), 384 at 168.  The skewed instance,
+    // with its cross terms, was fastest at 384 and 8 % slower at 448.  Energy mode
+    // gains from the extra warps of 512 threads.
     if (pot && precision == VDWDF_FP32) ln.threads = skew ? 384 : 448;
     if (tu && (tu->threads == 384 || tu->threads == 448 || tu->threads == 512 ||
                (!skew && (tu->threads == 256 || tu->threads == 1024))))
