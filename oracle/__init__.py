@@ -88,6 +88,8 @@ def load_library(path):
     L.orc_pbe_H_many.argtypes = [_i, _p, _p, _p]
     L.orc_far_tail.restype = _i
     L.orc_far_tail.argtypes = [_i, _p, _p, _p, _p, _p, _i, _i, _i, _p, _i, _i, _i, _d, _p]
+    L.orc_line_tail_integral.restype = _d
+    L.orc_line_tail_integral.argtypes = [_d, _d]
     L.orc_far_tail_AB.restype = _i
     L.orc_far_tail_AB.argtypes = [_i, _p, _p, _p, _p, _p, _i, _i, _i, _p, _i, _i, _i, _d, _i, _p, _p, _p]
     L.orc_semilocal.restype = _i
@@ -589,7 +591,7 @@ class Problem:
                                     _ptr(self.na), _ptr(self.qa), *map(int, self.dims), _ptr(cell),
                                     *self.periodic, self.rc, len(qidx), _ptr(qidx), _ptr(AT), _ptr(BT))
         if rc_ != 0:
-            raise ValueError("far tail needs two or three periodic axes and rc > 0")
+            raise ValueError("far tail needs a periodic axis and rc > 0")
         return self.potential(A=-C_ASYM * AT, U=-C_ASYM * self.na * 2.0 * self.qa * BT)
 
     def voxel(self):
@@ -617,6 +619,11 @@ class Problem:
         return 0.5 * self.dV ** 2 * out.value
 
 
+def line_tail_integral(rho, x0):
+    """orc_line_tail_integral: int_{x0}^inf dx / (rho^2 + x^2)^3."""
+    return float(lib().orc_line_tail_integral(float(rho), float(x0)))
+
+
 def far_tail_points(i0, i1, i2, n, q, dims, cell, periodic, rc):
     """orc_far_tail on given points (grid indices), densities and q0 values."""
     i0, i1, i2 = _i32(i0), _i32(i1), _i32(i2)
@@ -626,7 +633,7 @@ def far_tail_points(i0, i1, i2, n, q, dims, cell, periodic, rc):
     rc_ = lib().orc_far_tail(len(n), _ptr(i0), _ptr(i1), _ptr(i2), _ptr(n), _ptr(q), *map(int, dims),
                              _ptr(cell), *[int(bool(p)) for p in periodic], float(rc), ctypes.byref(out))
     if rc_ != 0:
-        raise ValueError("far tail needs two or three periodic axes and rc > 0")
+        raise ValueError("far tail needs a periodic axis and rc > 0")
     return out.value
 
 

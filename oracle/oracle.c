@@ -48,10 +48,13 @@
  *                                   brute-force pair counts
  *   orc_far_tail                    pinned: the radial integrals of the
  *                                   lattice continuum by adaptive quadrature
- *                                   (two and three periodic axes, skewed
+ *                                   (one, two and three periodic axes, skewed
  *                                   cells), the exact lattice sum of eq. (17)
- *                                   beyond r_cut, convergence of E + T with
- *                                   r_cut against direct sums
+ *                                   beyond r_cut (for one axis: averaged over
+ *                                   the offset along it), convergence of
+ *                                   E + T with r_cut against direct sums
+ *   orc_line_tail_integral          pinned: adaptive quadrature of its
+ *                                   integral on both of its branches
  *   orc_far_tail_AB                 pinned: the far field's potential against
  *                                   central differences of orc_far_tail
  *   orc_phi0_many                   pinned: small-voxel logarithmic law,
@@ -1141,6 +1144,93 @@ int orc_phi0_many(int nD, double hD, int nd, double hd, const double *f,
 }
 
 /* ---------------------------------------------------------------------- */
+/* I(rho, x0) = int_{x0}^inf dx / (rho^2 + x^2)^3, rho >= 0, x0 >= 0, not   */
+/* both 0: the continuum of one periodic axis (orc_far_tail).               */
+/*  - x0 = 0: 3 pi / (16 rho^5).                                            */
+/*  - rho / x0 = e < 1/2: with x = x0 t, (t^2 + e^2)^-3 = t^-6 (1 + e^2 / t^2)^-3 */
+/*    expands by the binomial series into sum_k (-1)^k C(k+2, 2) e^2k t^-(6+2k), */
+/*    and term by term over [1, inf): I = x0^-5 sum_k (-1)^k C(k+2, 2) e^2k / (2k + 5). */
+/*  - otherwise the antiderivative of (rho^2 + x^2)^-3 (two steps of the     */
+/*    reduction formula for int dx / (x^2 + a^2)^n),                         */
+/*      x / (4 rho^2 (rho^2 + x^2)^2) + 3 x / (8 rho^4 (rho^2 + x^2))         */
+/*      + 3 / (8 rho^5) atan(x / rho),                                       */
+/*    taken from x0 to infinity.  The series avoids its cancellation when    */
+/*    rho is small beside x0.                                               */
+/* ---------------------------------------------------------------------- */
+double orc_line_tail_integral(double rho, double x0)
+{
+    if (!(x0 > 0.0)) return 3.0 * M_PI / (16.0 * pow(rho, 5));
+    double e = rho / x0;
+    if (e < 0.5) {
+        double sum = 0.0, p = 1.0;
+        for (int k = 0; k < 80; ++k) {
+            double term = 0.5 * (k + 1.0) * (k + 2.0) * p / (2.0 * k + 5.0);
+            sum += (k % 2) ? -term : term;
+            if (term < 1e-19) break;
+            p *= e * e;
+        }
+        return sum / pow(x0, 5);
+    }
+    double r2 = rho * rho, s2 = r2 + x0 * x0;
+    return 3.0 / (8.0 * pow(rho, 5)) * atan(rho / x0) - x0 / (4.0 * r2 * s2 * s2) -
+           3.0 * x0 / (8.0 * r2 * r2 * s2);
+}
+
+/* The continuum factor K_ij of the far field (orc_far_tail) for the pair of  */
+/* points at ri, rj; geometry from far_geometry.                             */
+typedef struct {
+    int np;          /* periodic axes: 1, 2 or 3                               */
+    double V;        /* cell volume                                            */
+    double A;        /* two axes: |a x b|                                      */
+    double alen;     /* one axis: |a|                                          */
+    double e[3];     /* two axes: unit normal of the periodic plane; one axis:  */
+                     /* unit vector along the periodic lattice vector         */
+} far_geom;
+
+static int far_geometry(const double *cell, const int per[3], far_geom *g)
+{
+    const double *M0 = cell, *M1 = cell + 3, *M2 = cell + 6;
+    const double *P[3] = {M0, M1, M2};
+    g->np = (per[0] != 0) + (per[1] != 0) + (per[2] != 0);
+    double x01[3] = {M0[1] * M1[2] - M0[2] * M1[1], M0[2] * M1[0] - M0[0] * M1[2], M0[0] * M1[1] - M0[1] * M1[0]};
+    g->V = fabs(x01[0] * M2[0] + x01[1] * M2[1] + x01[2] * M2[2]);
+    if (!(g->V > 0.0) || g->np < 1) return -1;
+    g->A = 0.0;
+    g->alen = 0.0;
+    g->e[0] = g->e[1] = g->e[2] = 0.0;
+    if (g->np == 2) {
+        const double *a = NULL, *b = NULL;
+        for (int k = 0; k < 3; ++k)
+            if (per[k]) { if (!a) a = P[k]; else b = P[k]; }
+        double x[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+        g->A = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (int c = 0; c < 3; ++c) g->e[c] = x[c] / g->A;
+    } else if (g->np == 1) {
+        const double *a = per[0] ? M0 : (per[1] ? M1 : M2);
+        g->alen = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        for (int c = 0; c < 3; ++c) g->e[c] = a[c] / g->alen;
+    }
+    return 0;
+}
+
+static double far_K(const far_geom *g, const double ri[3], const double rj[3], double rc)
+{
+    if (g->np == 3) return (4.0 * M_PI / g->V) / (3.0 * rc * rc * rc);
+    double d[3] = {ri[0] - rj[0], ri[1] - rj[1], ri[2] - rj[2]};
+    double z = d[0] * g->e[0] + d[1] * g->e[1] + d[2] * g->e[2];
+    if (g->np == 2) {
+        double R = fabs(z) > rc ? fabs(z) : rc;
+        return (2.0 * M_PI / g->A) / (4.0 * R * R * R * R);
+    }
+    /* one axis: rho the distance from the line through rj along the axis */
+    double p2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - z * z;
+    double rho = p2 > 0.0 ? sqrt(p2) : 0.0;
+    double x0 = rc * rc - rho * rho;
+    x0 = x0 > 0.0 ? sqrt(x0) : 0.0;
+    return (2.0 / g->alen) * orc_line_tail_integral(rho, x0);
+}
+
+/* ---------------------------------------------------------------------- */
 /* Far field past the cutoff from the asymptote alone.  Section 7 names      */
 /* image sums sped up by the kernel's asymptotic form as future work;       */
 /* sections 3 and 6.2 repeat the cell until the energy converges.           */
@@ -1154,12 +1244,18 @@ int orc_phi0_many(int nD, double hD, int nd, double hd, const double *f,
 /*        = (2 pi / A) int_{R}^inf g(r) r dr,  z = d . e,  R = max(rc, |z|), */
 /*     which for g = r^-6 is (2 pi / A) / (4 R^4);                           */
 /*   three periodic axes (volume V): (4 pi / V) int_rc^inf g(r) r^2 dr       */
-/*     = (4 pi / V) / (3 rc^3).                                             */
+/*     = (4 pi / V) / (3 rc^3);                                             */
+/*   one periodic axis a (length |a|): with rho the distance of d from the  */
+/*   axis direction and x the coordinate along it,                          */
+/*     sum_{m : |d + m a| > rc} g(|d + m a|)                                */
+/*       -> (1/|a|) int_{rho^2 + x^2 > rc^2} g(sqrt(rho^2 + x^2)) dx         */
+/*        = (2 / |a|) I(rho, x0),  x0 = sqrt(max(0, rc^2 - rho^2)),          */
+/*     I from orc_line_tail_integral for g = r^-6.                          */
 /* So the tail is                                                           */
 /*   T = 1/2 dV^2 sum_i sum_j n_i n_j (-C / (q_i^2 q_j^2 (q_i^2 + q_j^2))) K_ij */
 /* over all ordered pairs of active points, i = j included (the self term's */
-/* own images), and E(r_cut -> inf) is read as E(r_cut) + T.  Cells with    */
-/* fewer than two periodic axes have no lattice continuum: returns -1.      */
+/* own images), and E(r_cut -> inf) is read as E(r_cut) + T.  Open cells    */
+/* have no lattice images: returns -1.                                      */
 /* Points i at fractional index (i0/n0, i1/n1, i2/n2) of the cell (rows of  */
 /* `cell` are the lattice vectors).                                          */
 /* ---------------------------------------------------------------------- */
@@ -1168,27 +1264,12 @@ int orc_far_tail(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2
                  int per0, int per1, int per2, double rc, double *out)
 {
     int per[3] = {per0, per1, per2};
-    int np = (per0 != 0) + (per1 != 0) + (per2 != 0);
-    if (np < 2 || !(rc > 0.0)) return -1;
+    far_geom g;
+    if (far_geometry(cell, per, &g) != 0 || !(rc > 0.0)) return -1;
     const double C = 12.0 * pow(4.0 * M_PI / 9.0, 3);
     const double *M0 = cell, *M1 = cell + 3, *M2 = cell + 6;
-    /* volume and, for two periodic axes, the area and unit normal of the plane */
-    double x01[3] = {M0[1] * M1[2] - M0[2] * M1[1], M0[2] * M1[0] - M0[0] * M1[2], M0[0] * M1[1] - M0[1] * M1[0]};
-    double V = fabs(x01[0] * M2[0] + x01[1] * M2[1] + x01[2] * M2[2]);
-    if (!(V > 0.0)) return -1;
-    double e[3] = {0.0, 0.0, 0.0}, A = 0.0;
-    if (np == 2) {
-        /* the two periodic lattice vectors, in axis order */
-        const double *P[3] = {M0, M1, M2};
-        const double *a = NULL, *b = NULL;
-        for (int k = 0; k < 3; ++k)
-            if (per[k]) { if (!a) a = P[k]; else b = P[k]; }
-        double x[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
-        A = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-        for (int c = 0; c < 3; ++c) e[c] = x[c] / A;
-    }
     int N[3] = {n0, n1, n2};
-    double dV = V / ((double)n0 * n1 * n2);
+    double dV = g.V / ((double)n0 * n1 * n2);
     double sum = 0.0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : sum)
     for (int i = 0; i < Na; ++i) {
@@ -1198,20 +1279,11 @@ int orc_far_tail(int Na, const int32_t *i0, const int32_t *i1, const int32_t *i2
         double ui = q[i] * q[i];
         double acc = 0.0;
         for (int j = 0; j < Na; ++j) {
+            double rj[3];
+            for (int c = 0; c < 3; ++c)
+                rj[c] = i0[j] / (double)N[0] * M0[c] + i1[j] / (double)N[1] * M1[c] + i2[j] / (double)N[2] * M2[c];
             double uj = q[j] * q[j];
-            double K;
-            if (np == 3) {
-                K = (4.0 * M_PI / V) / (3.0 * rc * rc * rc);
-            } else {
-                double z = 0.0;
-                for (int c = 0; c < 3; ++c) {
-                    double rjc = i0[j] / (double)N[0] * M0[c] + i1[j] / (double)N[1] * M1[c] +
-                                 i2[j] / (double)N[2] * M2[c];
-                    z += (ri[c] - rjc) * e[c];
-                }
-                double R = fabs(z) > rc ? fabs(z) : rc;
-                K = (2.0 * M_PI / A) / (4.0 * R * R * R * R);
-            }
+            double K = far_K(&g, ri, rj, rc);
             acc += n[j] * (-C / (ui * uj * (ui + uj))) * K;
         }
         sum += n[i] * acc;
@@ -1233,22 +1305,9 @@ int orc_far_tail_AB(int Na, const int32_t *i0, const int32_t *i1, const int32_t 
                     double *AT, double *BT)
 {
     int per[3] = {per0, per1, per2};
-    int np = (per0 != 0) + (per1 != 0) + (per2 != 0);
-    if (np < 2 || !(rc > 0.0)) return -1;
+    far_geom g;
+    if (far_geometry(cell, per, &g) != 0 || !(rc > 0.0)) return -1;
     const double *M0 = cell, *M1 = cell + 3, *M2 = cell + 6;
-    double x01[3] = {M0[1] * M1[2] - M0[2] * M1[1], M0[2] * M1[0] - M0[0] * M1[2], M0[0] * M1[1] - M0[1] * M1[0]};
-    double V = fabs(x01[0] * M2[0] + x01[1] * M2[1] + x01[2] * M2[2]);
-    if (!(V > 0.0)) return -1;
-    double e[3] = {0.0, 0.0, 0.0}, A = 0.0;
-    if (np == 2) {
-        const double *P[3] = {M0, M1, M2};
-        const double *a = NULL, *b = NULL;
-        for (int k = 0; k < 3; ++k)
-            if (per[k]) { if (!a) a = P[k]; else b = P[k]; }
-        double x[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
-        A = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-        for (int c = 0; c < 3; ++c) e[c] = x[c] / A;
-    }
     int N[3] = {n0, n1, n2};
 #pragma omp parallel for schedule(dynamic, 4)
     for (int t = 0; t < nq; ++t) {
@@ -1259,20 +1318,11 @@ int orc_far_tail_AB(int Na, const int32_t *i0, const int32_t *i1, const int32_t 
         double ui = q[i] * q[i];
         double sa = 0.0, sb = 0.0;
         for (int j = 0; j < Na; ++j) {
+            double rj[3];
+            for (int c = 0; c < 3; ++c)
+                rj[c] = i0[j] / (double)N[0] * M0[c] + i1[j] / (double)N[1] * M1[c] + i2[j] / (double)N[2] * M2[c];
             double uj = q[j] * q[j];
-            double K;
-            if (np == 3) {
-                K = (4.0 * M_PI / V) / (3.0 * rc * rc * rc);
-            } else {
-                double z = 0.0;
-                for (int c = 0; c < 3; ++c) {
-                    double rjc = i0[j] / (double)N[0] * M0[c] + i1[j] / (double)N[1] * M1[c] +
-                                 i2[j] / (double)N[2] * M2[c];
-                    z += (ri[c] - rjc) * e[c];
-                }
-                double R = fabs(z) > rc ? fabs(z) : rc;
-                K = (2.0 * M_PI / A) / (4.0 * R * R * R * R);
-            }
+            double K = far_K(&g, ri, rj, rc);
             double f = 1.0 / (ui * uj * (ui + uj));
             sa += n[j] * f * K;
             sb += n[j] * (-f * (1.0 / ui + 1.0 / (ui + uj))) * K;

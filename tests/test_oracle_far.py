@@ -1,7 +1,8 @@
 """Pins of the oracle's far field past the cutoff (orc_far_tail): eq. (17) for
 every pair beyond r_cut, with the lattice images beyond r_cut replaced by the
 lattice continuum (section 7's asymptote-accelerated image sums; sections 3
-and 6.2 repeat the cell until the energy converges)."""
+and 6.2 repeat the cell until the energy converges), for one, two and three
+periodic axes."""
 import numpy as np
 import pytest
 
@@ -64,8 +65,83 @@ def test_three_axis_continuum_is_the_radial_integral(oracle_mod):
     ref = float(np.sum(_pref(n, q, V / 512) * (val / V)))
     got = oracle_mod.far_tail_points(idx[:, 0], idx[:, 1], idx[:, 2], n, q, dims, cell, (1, 1, 1), rc)
     assert abs(got - ref) < 1e-11 * abs(ref), (got, ref)
-    with pytest.raises(ValueError):   # one periodic axis: no lattice continuum
-        oracle_mod.far_tail_points(idx[:, 0], idx[:, 1], idx[:, 2], n, q, dims, cell, (1, 0, 0), rc)
+    with pytest.raises(ValueError):   # an open cell: no lattice images
+        oracle_mod.far_tail_points(idx[:, 0], idx[:, 1], idx[:, 2], n, q, dims, cell, (0, 0, 0), rc)
+
+
+@pytest.mark.parametrize("rho", [0.0, 1e-4, 0.3, 2.0, 4.4, 4.5, 7.0, 9.99, 10.0, 10.01, 13.0, 30.0])
+def test_line_integral_matches_quadrature(oracle_mod, rho):
+    """orc_line_tail_integral, int_{x0}^inf dx / (rho^2 + x^2)^3 with
+    x0 = sqrt(max(0, r_c^2 - rho^2)), r_c = 10, against scipy's adaptive quadrature:
+    the series branch (rho / x0 < 1/2, up to rho = 4.47), the closed form beyond
+    it, and x0 = 0 past the cutoff."""
+    quad = pytest.importorskip("scipy.integrate").quad
+    rc = 10.0
+    x0 = np.sqrt(max(0.0, rc * rc - rho * rho))
+    ref, _ = quad(lambda x: (rho * rho + x * x) ** -3, x0, np.inf, epsabs=0, epsrel=1e-13, limit=400)
+    got = oracle_mod.line_tail_integral(rho, x0)
+    assert abs(got - ref) < 2e-12 * abs(ref), (rho, got, ref)
+
+
+def test_one_axis_continuum_is_the_line_integral(oracle_mod):
+    """One periodic axis (the second lattice vector of a skewed cell): each pair's
+    factor is (1/|a|) times the integral of r^-6 along the line of images outside
+    the cutoff sphere, done here by scipy's adaptive quadrature with the pair's
+    distance rho from the axis direction taken from the cell."""
+    quad = pytest.importorskip("scipy.integrate").quad
+    dims = (12, 10, 14)
+    cell = np.array([[14.0, 0, 0], [3.0, 9.0, 0], [1.0, -2.0, 15.0]])
+    idx = np.array([[0, 0, 0], [3, 4, 5], [7, 1, 11], [2, 9, 8], [11, 6, 3]])
+    n = np.array([0.7, 1.3, 0.4, 0.9, 0.2])
+    q = np.array([0.5, 1.1, 0.35, 2.0, 0.8])
+    rc = 9.0
+    a = cell[1]
+    alen = np.linalg.norm(a)
+    e = a / alen
+    pos = _positions(idx, dims, cell)
+    K = np.zeros((5, 5))
+    for i in range(5):
+        for j in range(5):
+            d = pos[i] - pos[j]
+            rho = np.linalg.norm(d - np.dot(d, e) * e)
+            x0 = np.sqrt(rc * rc - rho * rho) if rho < rc else 0.0
+            val, _ = quad(lambda x: (rho * rho + x * x) ** -3, x0, np.inf, epsabs=0, epsrel=1e-13, limit=400)
+            K[i, j] = 2.0 * val / alen
+    assert np.max(K) > 5 * np.min(K)           # pairs near and far from the axis
+    dV = abs(np.linalg.det(cell)) / np.prod(dims)
+    ref = float(np.sum(_pref(n, q, dV) * K))
+    got = oracle_mod.far_tail_points(idx[:, 0], idx[:, 1], idx[:, 2], n, q, dims, cell, (0, 1, 0), rc)
+    assert abs(got - ref) < 1e-11 * abs(ref), (got, ref)
+
+
+@pytest.mark.parametrize("rc", [10.0, 25.0])
+def test_one_axis_continuum_is_the_offset_average_of_the_lattice_sum(oracle_mod, rc):
+    """The continuum stands for the images beyond r_cut.  For one periodic axis the
+    lattice sum of r^-6 over the images beyond r_cut jumps as images cross the
+    cutoff sphere, but its average over the pair's offset along the axis is the
+    continuum: 20000 offsets across one period against the oracle's factor for
+    pairs at several distances from the axis (2e-4)."""
+    dims = (40, 8, 8)
+    cell = np.array([[6.0, 0, 0], [0, 30.0, 0], [0, 0, 30.0]])
+    n = np.array([1.0, 1.0])
+    q = np.array([0.6, 0.9])
+    dV = abs(np.linalg.det(cell)) / np.prod(dims)
+    P = _pref(n, q, dV)
+    for jb, jc in ((0, 0), (1, 0), (2, 3), (4, 5)):
+        idx = np.array([[0, 0, 0], [0, jb, jc]])
+        both = oracle_mod.far_tail_points(idx[:, 0], idx[:, 1], idx[:, 2], n, q, dims, cell, (1, 0, 0), rc)
+        only0 = oracle_mod.far_tail_points(idx[:1, 0], idx[:1, 1], idx[:1, 2], n[:1], q[:1], dims, cell, (1, 0, 0), rc)
+        only1 = oracle_mod.far_tail_points(idx[1:, 0], idx[1:, 1], idx[1:, 2], n[1:], q[1:], dims, cell, (1, 0, 0), rc)
+        K01 = (both - only0 - only1) / (2 * P[0, 1])      # the cross term's factor
+        rho = np.hypot(jb * 30.0 / 8, jc * 30.0 / 8)
+        x = (np.arange(20000) + 0.5) / 20000 * 6.0
+        M = int(np.ceil(8 * rc / 6.0)) + 2
+        y = x[:, None] + 6.0 * np.arange(-M, M + 1)[None, :]
+        r2 = y * y + rho * rho
+        S = np.where(r2 > rc * rc, r2, np.inf) ** -3
+        tail = 2.0 / 6.0 * oracle_mod.line_tail_integral(rho, 6.0 * M - 6.0)  # images past the window
+        lat = float(np.mean(S.sum(axis=1))) + tail
+        assert abs(K01 - lat) < 2e-4 * abs(lat), (rc, jb, jc, K01, lat)
 
 
 def test_continuum_approaches_the_lattice_sum(oracle_mod):
@@ -121,7 +197,27 @@ def test_energy_plus_tail_converges(oracle_mod, oracle_spline):
     assert d_tail[0] < 0.1 * d_direct[0] and d_tail[1] < 0.01 * d_direct[1], (d_direct, d_tail)
 
 
-@pytest.mark.parametrize("periodic", [(1, 1, 0), (0, 1, 1), (1, 1, 1)])
+def test_energy_plus_tail_converges_on_a_wire(oracle_mod, oracle_spline):
+    """A chain of rare-gas atoms 6 bohr apart, periodic along the chain only: the
+    oracle's direct sums E(r_cut) and E(r_cut) + T(r_cut) at r_cut = 15, 20, 25, 35.
+    Against r_cut = 35, E + T moves by under a twentieth of what E moves from 15
+    and under a hundredth from 20 and from 25."""
+    from paper_0810_2273_gb300 import inputs
+    L, dims = (6.0, 14.0, 14.0), (8, 18, 18)
+    n = inputs.density(dims, L, [((3.0, 7.0, 7.0), inputs.rare_gas_shells())], periodic=(1, 0, 0))
+    Es, Ts = [], []
+    for rc in (15.0, 20.0, 25.0, 35.0):
+        P = oracle_mod.Problem(n, L, (1, 0, 0), 1e-6, rc, oracle_spline)
+        Es.append(P.energy()["E"])
+        Ts.append(P.far_tail())
+    Es, Ts = np.array(Es), np.array(Ts)
+    assert np.all(Ts < 0) and np.all(np.diff(np.abs(Ts)) < 0)
+    d_direct = np.abs(Es[:3] - Es[3])
+    d_tail = np.abs(Es[:3] + Ts[:3] - Es[3] - Ts[3])
+    assert d_tail[0] < 0.05 * d_direct[0] and np.all(d_tail[1:] < 0.01 * d_direct[1:]), (d_direct, d_tail)
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 0), (0, 1, 1), (1, 1, 1), (1, 0, 0), (0, 0, 1)])
 def test_tail_potential_is_derivative_of_tail(oracle_mod, oracle_spline, periodic):
     """The far field's potential v_T = dT/dn_m / dV (mask frozen) against central
     differences of the oracle's T, at active points and at inactive points next

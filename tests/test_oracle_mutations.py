@@ -109,8 +109,22 @@ MUTATIONS = [
      "double R = fabs(z) > rc ? fabs(z) : rc;", "double R = rc;", 0,
      FAR.test_two_axis_continuum_is_the_radial_integral, ("oracle_mod", False)),
     ("far tail: 2 pi / A written pi / A",
-     "K = (2.0 * M_PI / A) / (4.0 * R * R * R * R);", "K = (M_PI / A) / (4.0 * R * R * R * R);", 0,
+     "return (2.0 * M_PI / g->A) / (4.0 * R * R * R * R);", "return (M_PI / g->A) / (4.0 * R * R * R * R);", 0,
      FAR.test_continuum_approaches_the_lattice_sum, ("oracle_mod",)),
+    ("far tail, one axis: the factor 2 of the two half-lines dropped",
+     "return (2.0 / g->alen) * orc_line_tail_integral(rho, x0);",
+     "return (1.0 / g->alen) * orc_line_tail_integral(rho, x0);", 0,
+     FAR.test_one_axis_continuum_is_the_offset_average_of_the_lattice_sum, ("oracle_mod", 10.0)),
+    ("far tail, one axis: rho taken as the full distance (axial part not removed)",
+     "double p2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - z * z;",
+     "double p2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];", 0,
+     FAR.test_one_axis_continuum_is_the_line_integral, ("oracle_mod",)),
+    ("line integral: the series' alternating sign dropped",
+     "sum += (k % 2) ? -term : term;", "sum += term;", 0,
+     FAR.test_line_integral_matches_quadrature, ("oracle_mod", 2.0)),
+    ("line integral: closed form's second term with (rho^2 + x0^2) once, not squared",
+     "x0 / (4.0 * r2 * s2 * s2)", "x0 / (4.0 * r2 * s2)", 0,
+     FAR.test_line_integral_matches_quadrature, ("oracle_mod", 7.0)),
     ("far tail's potential: the 1/(a + b) term of df/da dropped",
      "sb += n[j] * (-f * (1.0 / ui + 1.0 / (ui + uj))) * K;", "sb += n[j] * (-f * (1.0 / ui)) * K;", 0,
      FAR.test_tail_potential_is_derivative_of_tail, ("oracle_mod", "oracle_spline", (1, 1, 0))),
