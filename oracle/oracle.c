@@ -1222,11 +1222,14 @@ static double far_K(const far_geom *g, const double ri[3], const double rj[3], d
         double R = fabs(z) > rc ? fabs(z) : rc;
         return (2.0 * M_PI / g->A) / (4.0 * R * R * R * R);
     }
-    /* one axis: rho the distance from the line through rj along the axis */
+    /* one axis: rho the distance from the line through rj along the axis.  x0 has  */
+    /* a square-root singularity at rho = rc, where many grid pairs sit exactly;   */
+    /* as the pair sum's inclusive cutoff does, rc^2 - rho^2 within 1e-12 rc^2 of   */
+    /* zero counts as zero, so that rounding does not decide those pairs.          */
     double p2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - z * z;
     double rho = p2 > 0.0 ? sqrt(p2) : 0.0;
-    double x0 = rc * rc - rho * rho;
-    x0 = x0 > 0.0 ? sqrt(x0) : 0.0;
+    double t = rc * rc - p2;
+    double x0 = t > 1e-12 * rc * rc ? sqrt(t) : 0.0;
     return (2.0 / g->alen) * orc_line_tail_integral(rho, x0);
 }
 
@@ -1250,7 +1253,8 @@ static double far_K(const far_geom *g, const double ri[3], const double rj[3], d
 /*     sum_{m : |d + m a| > rc} g(|d + m a|)                                */
 /*       -> (1/|a|) int_{rho^2 + x^2 > rc^2} g(sqrt(rho^2 + x^2)) dx         */
 /*        = (2 / |a|) I(rho, x0),  x0 = sqrt(max(0, rc^2 - rho^2)),          */
-/*     I from orc_line_tail_integral for g = r^-6.                          */
+/*     I from orc_line_tail_integral for g = r^-6 (rc^2 - rho^2 below       */
+/*     1e-12 rc^2 counts as 0, see far_K).                                  */
 /* So the tail is                                                           */
 /*   T = 1/2 dV^2 sum_i sum_j n_i n_j (-C / (q_i^2 q_j^2 (q_i^2 + q_j^2))) K_ij */
 /* over all ordered pairs of active points, i = j included (the self term's */

@@ -114,6 +114,29 @@ def test_one_axis_continuum_is_the_line_integral(oracle_mod):
     assert abs(got - ref) < 1e-11 * abs(ref), (got, ref)
 
 
+def test_one_axis_factor_at_the_cutoff_radius(oracle_mod):
+    """A pair whose distance from the axis is r_cut exactly (6 grid steps of
+    16.4/8 bohr = 12.3 bohr = r_cut): x0 = sqrt(r_cut^2 - rho^2) is 0, and the
+    factor is (2/|a|) 3 pi / (16 r_cut^5).  In floating point rho^2 comes out
+    5.7e-14 below r_cut^2 here; the factor's square-root singularity at rho = r_cut
+    would turn that into a 3e-8 change, so differences within 1e-12 r_cut^2 count
+    as zero (as the pair sum's inclusive cutoff treats distances equal to r_cut)."""
+    dims = (8, 5, 5)
+    cell = np.diag([16.4, 9.0, 9.0])
+    rc = 12.3
+    n = np.array([1.0, 1.0])
+    q = np.array([0.6, 0.9])
+    dV = abs(np.linalg.det(cell)) / np.prod(dims)
+    P = _pref(n, q, dV)
+    idx = np.array([[0, 0, 0], [6, 0, 0]])
+    both = oracle_mod.far_tail_points(idx[:, 0], idx[:, 1], idx[:, 2], n, q, dims, cell, (0, 1, 0), rc)
+    only0 = oracle_mod.far_tail_points(idx[:1, 0], idx[:1, 1], idx[:1, 2], n[:1], q[:1], dims, cell, (0, 1, 0), rc)
+    only1 = oracle_mod.far_tail_points(idx[1:, 0], idx[1:, 1], idx[1:, 2], n[1:], q[1:], dims, cell, (0, 1, 0), rc)
+    K01 = (both - only0 - only1) / (2 * P[0, 1])
+    ref = 2.0 / 9.0 * 3.0 * np.pi / (16.0 * rc ** 5)
+    assert abs(K01 - ref) < 1e-12 * ref, (K01, ref)
+
+
 @pytest.mark.parametrize("rc", [10.0, 25.0])
 def test_one_axis_continuum_is_the_offset_average_of_the_lattice_sum(oracle_mod, rc):
     """The continuum stands for the images beyond r_cut.  For one periodic axis the

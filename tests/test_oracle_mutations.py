@@ -119,6 +119,9 @@ MUTATIONS = [
      "double p2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - z * z;",
      "double p2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];", 0,
      FAR.test_one_axis_continuum_is_the_line_integral, ("oracle_mod",)),
+    ("far tail, one axis: no allowance at rho = r_cut (rounding decides x0)",
+     "double x0 = t > 1e-12 * rc * rc ? sqrt(t) : 0.0;", "double x0 = t > 0.0 ? sqrt(t) : 0.0;", 0,
+     FAR.test_one_axis_factor_at_the_cutoff_radius, ("oracle_mod",)),
     ("line integral: the series' alternating sign dropped",
      "sum += (k % 2) ? -term : term;", "sum += term;", 0,
      FAR.test_line_integral_matches_quadrature, ("oracle_mod", 2.0)),
