@@ -332,7 +332,9 @@ typedef struct {
     double T;            /* the far field past r_cut, Hartree: E(r_cut -> inf) reads E + T */
     int64_t n_active;    /* grid points with n >= n_cut                          */
     int32_t nodes;       /* nodes of the quadrature in ln s                       */
-    int32_t planes;      /* grid planes along the non-periodic axis (1: three periodic axes) */
+    int32_t planes;      /* groups the sums run over: grid planes along the open axis
+                            (two periodic axes), grid lines along the periodic axis
+                            that hold an active point (one), 1 (three)            */
     float ms;            /* device time of the call                               */
     int32_t launches;    /* kernels launched by the call                          */
 } vdwdf_tail_result;
@@ -345,25 +347,30 @@ typedef struct {
  *   T = 1/2 dV^2 sum_{i,j active} n_i n_j (-C / (q_i^2 q_j^2 (q_i^2 + q_j^2))) K_ij,
  *   K_ij = (2 pi / A) / (4 max(r_cut, |z_ij|)^4)   two periodic axes (A the
  *          area of the periodic plane, z_ij the separation normal to it),
- *   K    = (4 pi / V) / (3 r_cut^3)                 three periodic axes.
+ *   K    = (4 pi / V) / (3 r_cut^3)                 three periodic axes,
+ *   K_ij = (2 / |a|) I(rho_ij, x0),  I(rho, x0) = int_{x0}^inf dx / (rho^2 + x^2)^3,
+ *          x0 = sqrt(max(0, r_cut^2 - rho_ij^2))    one periodic axis a (rho_ij
+ *          the distance of r_i - r_j from the direction of a).
  * E(r_cut) + T estimates the fully converged periodic energy; the estimate
  * is exact for the continuum of images and tends to the lattice sum of eq.
  * (17) as r_cut grows.  The library evaluates T in FP64, with
  * 1/(a + b) = int exp(-(a + b) s) ds by the trapezoidal rule in ln s
- * (relative error below 1e-15), from per-plane sums over the grid.
+ * (relative error below 1e-15), from per-plane sums over the grid (per-line
+ * sums with one periodic axis, and K over pairs of lines with an active point:
+ * at most 65536 such lines).
  * v_dev: NULL, or an [N] FP64 device array that receives T's potential,
  * v_T = dT/dn / dV with the active mask frozen, in the pair sum's adjoint form
  * (vdwdf_potential) with
  *   A_m = -C sum_j n_j f(u_m, u_j) K_mj,
  *   U_m = -2 C n_m q0_m sum_j n_j (df/du_m)(u_m, u_j) K_mj,
  * f(a, b) = 1/(a b (a + b)), u = q0^2; so v + v_T is the potential of E + T.
- * grid as in vdwdf_energy with exactly two or three periodic axes; grad_dev
+ * grid as in vdwdf_energy with one, two or three periodic axes; grad_dev
  * as in vdwdf_q0, and NULL when v_dev is given (the potential needs the
  * library's own gradient); r_cut > 0.  Synchronises the stream.
  * Errors: VDWDF_EINVAL (bad argument, r_cut <= 0, grad_dev with v_dev, a
  * non-finite T from a non-finite density; v_dev is then unspecified),
- * VDWDF_EUNSUPPORTED (fewer than two periodic axes, or a q0 range needing
- * more than 4096 nodes), VDWDF_ECUDA, VDWDF_EALLOC. */
+ * VDWDF_EUNSUPPORTED (no periodic axis, a q0 range needing more than 4096
+ * nodes, or more than 65536 active lines), VDWDF_ECUDA, VDWDF_EALLOC. */
 int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *grad_dev, double n_cut,
                    double r_cut, double *v_dev, vdwdf_tail_result *out, void *cuda_stream);
 

@@ -1384,10 +1384,11 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
     if (pot && grad_dev) return VDWDF_EINVAL;  // the potential needs the library's own gradient
     if (!(n_cut > 0.0) || !std::isfinite(n_cut) || !(r_cut > 0.0) || !std::isfinite(r_cut)) return VDWDF_EINVAL;
     const int nper = (G.per[0] != 0) + (G.per[1] != 0) + (G.per[2] != 0);
-    if (nper < 2) return VDWDF_EUNSUPPORTED;
+    if (nper < 1) return VDWDF_EUNSUPPORTED;
     // geometry: the cell's volume; with two periodic axes the area of their plane, its
     // unit normal e and the spacing dz = |M_ax . e| / N_ax of the planes along the
-    // third axis ax
+    // third axis ax; with one periodic axis ax its length, and the metric of the
+    // other two axes' grid steps with their components along M_ax removed
     double M[3][3];
     for (int a = 0; a < 3; ++a)
         for (int c = 0; c < 3; ++c) M[a][c] = grid->cell[a][c];
@@ -1396,35 +1397,63 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
         z[1] = x[2] * y[0] - x[0] * y[2];
         z[2] = x[0] * y[1] - x[1] * y[0];
     };
+    auto dot = [](const double *x, const double *y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
     double x01[3];
     cross(M[0], M[1], x01);
-    const double V = std::fabs(x01[0] * M[2][0] + x01[1] * M[2][1] + x01[2] * M[2][2]);
+    const double V = std::fabs(dot(x01, M[2]));
     int ax = 0, np = 1;
     double dz = 0.0, c2 = 0.0, c3 = 0.0;
+    double gbb = 0.0, gbc = 0.0, gcc = 0.0, pref = 0.0;
+    int nlines = 0, Nc = 1;
     if (nper == 2) {
         ax = G.per[0] == 0 ? 0 : (G.per[1] == 0 ? 1 : 2);
         const int a = ax == 0 ? 1 : 0, b = ax == 2 ? 1 : 2;
         double e[3];
         cross(M[a], M[b], e);
-        const double A = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-        dz = std::fabs(M[ax][0] * e[0] + M[ax][1] * e[1] + M[ax][2] * e[2]) / A / G.dims[ax];
+        const double A = std::sqrt(dot(e, e));
+        dz = std::fabs(dot(M[ax], e)) / A / G.dims[ax];
         np = G.dims[ax];
         c2 = (2.0 * kPi / A) / 4.0;
-    } else {
+    } else if (nper == 3) {
         c3 = (4.0 * kPi / V) / (3.0 * r_cut * r_cut * r_cut);
+    } else {
+        ax = G.per[0] ? 0 : (G.per[1] ? 1 : 2);
+        const int b = ax == 0 ? 1 : 0, c = ax == 2 ? 1 : 2;
+        const double alen = std::sqrt(dot(M[ax], M[ax]));
+        double wb[3], wc[3];
+        for (int k = 0; k < 3; ++k) {
+            wb[k] = M[b][k] / G.dims[b];
+            wc[k] = M[c][k] / G.dims[c];
+        }
+        const double pb = dot(wb, M[ax]) / (alen * alen), pc = dot(wc, M[ax]) / (alen * alen);
+        for (int k = 0; k < 3; ++k) {
+            wb[k] -= pb * M[ax][k];
+            wc[k] -= pc * M[ax][k];
+        }
+        gbb = dot(wb, wb);
+        gbc = dot(wb, wc);
+        gcc = dot(wc, wc);
+        pref = 2.0 / alen;
+        Nc = G.dims[c];
+        nlines = G.dims[b] * G.dims[c];
     }
     constexpr int kMaxNodes = 4096;
+    constexpr int kMaxLines = 65536;   // active lines of one periodic axis (K over their pairs)
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const long long launches0 = g_launches.load();
+    // the planes' F and G; for one periodic axis the lines' buffers come later, once
+    // the active lines are known
+    const size_t ngroup = nper == 1 ? 1 : static_cast<size_t>(np);
     Carve cv;
     const size_t o_q0 = cv.take<double>(G.N), o_mm = cv.take<unsigned long long>(3),
-                 o_F = cv.take<double>(static_cast<size_t>(kMaxNodes) * np), o_Tk = cv.take<double>(kMaxNodes),
+                 o_F = cv.take<double>(static_cast<size_t>(kMaxNodes) * ngroup), o_Tk = cv.take<double>(kMaxNodes),
                  o_out = cv.take<double>(1);
     const size_t o_gsp = G.spectral ? cv.take<double>(3 * G.N) : 0,
                  o_coef = G.spectral ? cv.take<double>(G.dims[0] + G.dims[1] + G.dims[2]) : 0;
+    const size_t o_flags = nper == 1 ? cv.take<int>(nlines) : 0;
     // the potential: G_k(p), dq0/dn, dq0/dgrad n, the slot map, A and U on the grid, and
     // the spectral divergence
-    const size_t o_G = pot ? cv.take<double>(static_cast<size_t>(kMaxNodes) * np) : 0,
+    const size_t o_G = pot ? cv.take<double>(static_cast<size_t>(kMaxNodes) * ngroup) : 0,
                  o_qn = pot ? cv.take<double>(G.N) : 0, o_qg = pot ? cv.take<double>(3 * G.N) : 0,
                  o_slot = pot ? cv.take<int>(G.N) : 0, o_A = pot ? cv.take<double>(G.N) : 0,
                  o_U = pot ? cv.take<double>(G.N) : 0, o_div = (pot && G.spectral) ? cv.take<double>(G.N) : 0;
@@ -1443,10 +1472,12 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
     double *Tout = reinterpret_cast<double *>(base + o_out);
     double *gsp = G.spectral ? reinterpret_cast<double *>(base + o_gsp) : nullptr;
     double *coef = G.spectral ? reinterpret_cast<double *>(base + o_coef) : nullptr;
+    int *flags = nper == 1 ? reinterpret_cast<int *>(base + o_flags) : nullptr;
+    unsigned char *lbase = nullptr;  // one periodic axis: the lines' buffers
     Timer tm;
     unsigned long long hmm[3] = {0, 0, 0};
     double T = 0.0;
-    int nodes = 0;
+    int nodes = 0, groups = np;
     auto body = [&]() -> int {
         tm.mark(0, st);
         const double *g_use = nullptr;
@@ -1475,11 +1506,55 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
         nodes = static_cast<int>(std::ceil((x1 - x0) / hx)) + 1;
         if (nodes > kMaxNodes) return VDWDF_EUNSUPPORTED;
         const double Cas = 12.0 * std::pow(4.0 * kPi / 9.0, 3);
-        r = launch_far_tail(G.dims, ax, np, n_dev, q0, n_cut, x0, hx, nodes, dz, r_cut, c2, c3,
-                            -0.5 * G.dV * G.dV * Cas, F, Tk, Gk, Tout, st);
-        if (r) return r;
+        const double scale = -0.5 * G.dV * G.dV * Cas;
+        const int *line_slot = nullptr;
+        double *Gl = Gk;
+        if (nper == 1) {
+            // the lines along the periodic axis that hold an active point
+            VDWDF_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * nlines, st));
+            r = launch_far_tail_line_flags(G.dims, ax, n_dev, n_cut, flags, st);
+            if (r) return r;
+            std::vector<int> hf(nlines), list, lslot(nlines, -1);
+            VDWDF_CUDA_TRY(cudaMemcpyAsync(hf.data(), flags, sizeof(int) * nlines, cudaMemcpyDeviceToHost, st));
+            VDWDF_CUDA_TRY(cudaStreamSynchronize(st));
+            for (int l = 0; l < nlines; ++l)
+                if (hf[l]) {
+                    lslot[l] = static_cast<int>(list.size());
+                    list.push_back(l);
+                }
+            const int La = static_cast<int>(list.size());
+            if (La < 1) return VDWDF_EINVAL;  // active points counted above, so not reached
+            if (La > kMaxLines) return VDWDF_EUNSUPPORTED;
+            groups = La;
+            // K in blocks of rows of at most 256 MB
+            const long long kb_rows = std::max<long long>(1, std::min<long long>(La, (256LL << 20) / (8LL * La)));
+            Carve lc;
+            const size_t o_list = lc.take<int>(La), o_lslot = lc.take<int>(nlines),
+                         o_lF = lc.take<double>(static_cast<size_t>(nodes) * La),
+                         o_lG = lc.take<double>(static_cast<size_t>(nodes) * La),
+                         o_Kb = lc.take<double>(static_cast<size_t>(kb_rows) * La);
+            if (scratch_malloc_async(reinterpret_cast<void **>(&lbase), lc.off, st) != cudaSuccess) return VDWDF_EALLOC;
+            int *dlist = reinterpret_cast<int *>(lbase + o_list);
+            int *dlslot = reinterpret_cast<int *>(lbase + o_lslot);
+            double *lF = reinterpret_cast<double *>(lbase + o_lF), *lG = reinterpret_cast<double *>(lbase + o_lG);
+            double *Kb = reinterpret_cast<double *>(lbase + o_Kb);
+            VDWDF_CUDA_TRY(cudaMemcpyAsync(dlist, list.data(), sizeof(int) * La, cudaMemcpyHostToDevice, st));
+            VDWDF_CUDA_TRY(cudaMemcpyAsync(dlslot, lslot.data(), sizeof(int) * nlines, cudaMemcpyHostToDevice, st));
+            r = launch_far_tail_lines(G.dims, ax, La, dlist, n_dev, q0, n_cut, x0, hx, nodes, gbb, gbc, gcc, r_cut,
+                                      pref, scale, lF, Kb, kb_rows, lG, Tk, Tout, st);
+            if (r) return r;
+            line_slot = dlslot;
+            Gl = lG;
+            // the host vectors are read by the copies above before they are freed: the
+            // copies from pageable memory return once the data is staged
+        } else {
+            r = launch_far_tail(G.dims, ax, np, n_dev, q0, n_cut, x0, hx, nodes, dz, r_cut, c2, c3, scale, F, Tk,
+                                Gk, Tout, st);
+            if (r) return r;
+        }
         if (pot) {
-            r = launch_far_tail_AU(G.dims, ax, np, n_dev, q0, n_cut, x0, hx, nodes, Gk, Cas, slot, Ad, Ud, st);
+            r = launch_far_tail_AU(G.dims, ax, groups, line_slot, n_dev, q0, n_cut, x0, hx, nodes, Gl, Cas, slot, Ad,
+                                   Ud, st);
             if (r) return r;
             r = assemble_v(G, slot, Ad, Ud, qn, qgr, gsp, divb, coef, v_dev, nullptr, nullptr, st);
             if (r) return r;
@@ -1491,6 +1566,7 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
         return VDWDF_OK;
     };
     rc = body();
+    if (lbase) cudaFreeAsync(lbase, st);
     cudaFreeAsync(base, st);
     if (rc == VDWDF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = VDWDF_ECUDA;
     if (rc) return rc;
@@ -1498,7 +1574,7 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
     out->T = T;
     out->n_active = static_cast<int64_t>(hmm[2]);
     out->nodes = nodes;
-    out->planes = np;
+    out->planes = groups;
     if (hmm[2]) out->ms = tm.ms(0, 1);
     out->launches = static_cast<int32_t>(g_launches.load() - launches0);
     return VDWDF_OK;

@@ -211,11 +211,25 @@ int launch_diag_AU(long long N, const double *n, const double *q0, double n_cut,
 int launch_far_tail(const int dims[3], int ax, int np, const double *n, const double *q0, double n_cut,
                     double x0, double hx, int nodes, double dz, double rc, double c2, double c3, double scale,
                     double *F, double *Tk, double *G, double *out, cudaStream_t st);
+// One periodic axis ax: flags[ib * N_c + ic] = 1 for the lines along ax (b < c the
+// other axes) that hold an active point (flags zeroed by the caller).
+int launch_far_tail_line_flags(const int dims[3], int ax, const double *n, double n_cut, int *flags,
+                               cudaStream_t st);
+// One periodic axis: the same sums over the La active lines `lines` (line ids):
+// F (nodes x La), K between lines (pref I(rho, x0), rho^2 from the index
+// differences through gbb, gbc, gcc) kb_rows rows at a time in Kb (kb_rows x La),
+// G (nodes x La) = K F, Tk (nodes) and out as launch_far_tail.
+int launch_far_tail_lines(const int dims[3], int ax, int La, const int *lines, const double *n, const double *q0,
+                          double n_cut, double x0, double hx, int nodes, double gbb, double gbc, double gcc,
+                          double rc, double pref, double scale, double *F, double *Kb, long long kb_rows,
+                          double *G, double *Tk, double *out, cudaStream_t st);
 // The far field's potential in the pair sum's adjoint form on the grid: A, U (N)
 // at active points with slot[m] = m, slot[m] = -1 elsewhere (for launch_assemble).
-int launch_far_tail_AU(const int dims[3], int ax, int np, const double *n, const double *q0, double n_cut,
-                       double x0, double hx, int nodes, const double *G, double C, int *slot, double *A,
-                       double *U, cudaStream_t st);
+// line_slot (one periodic axis; else NULL): the active-line index of every line,
+// which then indexes G (np = La).
+int launch_far_tail_AU(const int dims[3], int ax, int np, const int *line_slot, const double *n, const double *q0,
+                       double n_cut, double x0, double hx, int nodes, const double *G, double C, int *slot,
+                       double *A, double *U, cudaStream_t st);
 int launch_kernel_eval(int precision, const PairShared &sh, int64_t npts, const double *r,
                        const double *qi, const double *qj, double *phi, double *rdphi,
                        cudaStream_t st);

@@ -1,4 +1,5 @@
-"""vdwdf_far_tail (the far field past r_cut from eq. 17 and the lattice continuum)
+"""vdwdf_far_tail (the far field past r_cut from eq. 17 and the lattice continuum,
+for one, two and three periodic axes)
 through the C ABI against the oracle's plain O(N^2) sum: FP64 throughout on the
 GPU, so the bar is 1e-11 relative (the GPU's quadrature in ln s errs by less
 than 1e-15).  Also its refusals and E + T through the GPU converging with r_cut."""
@@ -47,10 +48,38 @@ def _cases():
     hex3 = inputs.xe_monolayer_hex((16, 16, 40))
     hex3["name"] = "skewed cell, three periodic axes"
     hex3["periodic"] = (True, True, True)
-    return [mono, hexa, slab, bulk, spec, side, hex3]
+    # one periodic axis: a chain of rare-gas atoms along x; the monolayer periodic
+    # along y alone; a skewed cell periodic along its third lattice vector
+    L = (6.0, 14.0, 14.0)
+    chain = dict(name="chain along x, one periodic axis", lengths=L, periodic=(True, False, False), n_cut=1e-6,
+                 density=inputs.density((8, 18, 18), L, [((3.0, 7.0, 7.0), inputs.rare_gas_shells())],
+                                        periodic=(1, 0, 0)))
+    ystrip = inputs.xe_monolayer((12, 21, 30))
+    ystrip["name"] = "periodic along the second axis only"
+    ystrip["periodic"] = (False, True, False)
+    cell = np.array([[12.0, 0.0, 0.0], [3.0, 11.0, 0.0], [1.5, -1.0, 7.0]])
+    skw = dict(name="skewed cell periodic along its third vector", cell=cell, lengths=None,
+               periodic=(False, False, True), n_cut=1e-6,
+               density=inputs.density_cell((14, 13, 9), cell,
+                                           [((6.0, 5.0, 3.5), inputs.rare_gas_shells()),
+                                            ((9.5, 7.5, 3.0), inputs.single_exponential(4.0, 0.6))],
+                                           periodic=(0, 0, 1)))
+    return [mono, hexa, slab, bulk, spec, side, hex3, chain, ystrip, skw]
 
 
-@pytest.mark.parametrize("k", range(7))
+def _groups(w):
+    """Planes along the open axis (two periodic axes), active lines along the
+    periodic axis (one), 1 (three)."""
+    per = [bool(p) for p in w["periodic"]]
+    if sum(per) == 3:
+        return 1
+    if sum(per) == 2:
+        return w["density"].shape[per.index(False)]
+    ax = per.index(True)
+    return int(np.count_nonzero(np.any(w["density"] >= w["n_cut"], axis=ax)))
+
+
+@pytest.mark.parametrize("k", range(10))
 def test_far_tail_matches_oracle(V, dev, oracle_mod, oracle_spline, k):
     w = _cases()[k]
     geom = w.get("cell", w["lengths"])
@@ -63,8 +92,7 @@ def test_far_tail_matches_oracle(V, dev, oracle_mod, oracle_spline, k):
         assert r["n_active"] == P.n_active
         assert abs(r["T"] - To) <= 1e-11 * abs(To), (w["name"], rc, r["T"], To)
         assert r["T"] < 0 and r["nodes"] > 0 and r["launches"] >= 5
-        nper = sum(bool(p) for p in w["periodic"])
-        assert r["planes"] == (1 if nper == 3 else w["density"].shape[list(map(bool, w["periodic"])).index(False)])
+        assert r["planes"] == _groups(w)
 
 
 def test_far_tail_refusals_and_empty(V, dev):
@@ -72,8 +100,8 @@ def test_far_tail_refusals_and_empty(V, dev):
     w = inputs.xe_monolayer((12, 21, 30))
     n = _t(w["density"], dev)
     with pytest.raises(V.VdwdfError) as e:
-        V.far_tail(n, w["lengths"], (True, False, False), w["n_cut"], 20.0)
-    assert e.value.status == -2  # one periodic axis: no lattice continuum
+        V.far_tail(n, w["lengths"], (False, False, False), w["n_cut"], 20.0)
+    assert e.value.status == -2  # an open cell: no lattice images
     with pytest.raises(V.VdwdfError) as e:
         V.far_tail(n, w["lengths"], w["periodic"], w["n_cut"], 0.0)
     assert e.value.status == -1
@@ -99,12 +127,31 @@ def test_energy_plus_tail_converges_on_gpu(V, dev, oracle_table):
     assert d_tail[0] < 0.1 * d_direct[0] and d_tail[1] < 0.01 * d_direct[1], (d_direct, d_tail)
 
 
-@pytest.mark.parametrize("k", [0, 1, 3, 4, 5, 6])
+def test_energy_plus_tail_converges_on_a_chain(V, dev, oracle_table):
+    """The chain of atoms 6 bohr apart, periodic along it only, through the GPU in
+    FP64: E(r_cut) + T(r_cut) at 15, 20, 25 and 35 bohr moves, against 35, by under
+    a twentieth of what E moves from 15 and under a hundredth from 20 and 25 (as the
+    oracle's own sums do)."""
+    T = V.Table.from_nodes(oracle_table, 30.0)
+    w = _cases()[7]
+    n = _t(w["density"], dev)
+    Es, Ts = [], []
+    for rc in (15.0, 20.0, 25.0, 35.0):
+        Es.append(V.energy(n, w["lengths"], w["periodic"], w["n_cut"], rc, T, "fp64")[0])
+        Ts.append(V.far_tail(n, w["lengths"], w["periodic"], w["n_cut"], rc)["T"])
+    Es, Ts = np.array(Es), np.array(Ts)
+    d_direct = np.abs(Es[:3] - Es[3])
+    d_tail = np.abs(Es[:3] + Ts[:3] - Es[3] - Ts[3])
+    assert d_tail[0] < 0.05 * d_direct[0] and np.all(d_tail[1:] < 0.01 * d_direct[1:]), (d_direct, d_tail)
+
+
+@pytest.mark.parametrize("k", [0, 1, 3, 4, 5, 6, 7, 8, 9])
 def test_far_tail_potential_matches_oracle(V, dev, oracle_mod, oracle_spline, k):
     """T's potential (dT/dn / dV, mask frozen) against the oracle's on the whole grid
     (1e-10 of max|v_T|; 1e-9 with the FFT gradient): the monolayer, the skewed
     hexagonal cell, three periodic axes, the FFT gradient, the periodic y, z
-    case and the skewed cell with three periodic axes."""
+    case, the skewed cell with three periodic axes, and the three cases with one
+    periodic axis."""
     w = _cases()[k]
     geom = w.get("cell", w["lengths"])
     kind = w.get("gradient", "fd")
