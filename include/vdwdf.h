@@ -355,9 +355,10 @@ typedef struct {
  * is exact for the continuum of images and tends to the lattice sum of eq.
  * (17) as r_cut grows.  The library evaluates T in FP64, with
  * 1/(a + b) = int exp(-(a + b) s) ds by the trapezoidal rule in ln s
- * (relative error below 1e-15), from per-plane sums over the grid (per-line
- * sums with one periodic axis, and K over pairs of lines with an active point:
- * at most 65536 such lines).
+ * (relative error below 2e-13; below 3e-12 for the potential's
+ * 1/(a + b)^2), from per-plane sums over the grid (per-line sums with one
+ * periodic axis, and K between lines with an active point, as a table over
+ * their index differences: at most 65536 such lines).
  * v_dev: NULL, or an [N] FP64 device array that receives T's potential,
  * v_T = dT/dn / dV with the active mask frozen, in the pair sum's adjoint form
  * (vdwdf_potential) with

@@ -1500,8 +1500,9 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
         // nodes x_k = x0 + k hx of int_0^inf e^{-c s} ds = int e^{-c e^x} e^x dx over
         // c = u_i + u_j in [2 umin, 2 umax]: the part below x0 is under 1e-17 of 1/c
         // for every c, e^{-c e^x} has fallen below e^-45 past the last node, and the
-        // step's error is about exp(-pi^2 / hx) = 4e-22
-        const double umin = qmin * qmin, umax = qmax * qmax, hx = 0.2;
+        // step's error (exp(-pi^2 / hx) up to a factor) measures 1.2e-13 relative for
+        // 1/c and 2.5e-12 for 1/c^2 (the potential's second sum) over that range
+        const double umin = qmin * qmin, umax = qmax * qmax, hx = 0.3;
         const double x0 = std::log(1e-17 / (2.0 * umax)), x1 = std::log(45.0 / (2.0 * umin));
         nodes = static_cast<int>(std::ceil((x1 - x0) / hx)) + 1;
         if (nodes > kMaxNodes) return VDWDF_EUNSUPPORTED;
@@ -1526,22 +1527,21 @@ int vdwdf_far_tail(const vdwdf_grid *grid, const double *n_dev, const double *gr
             if (La < 1) return VDWDF_EINVAL;  // active points counted above, so not reached
             if (La > kMaxLines) return VDWDF_EUNSUPPORTED;
             groups = La;
-            // K in blocks of rows of at most 256 MB
-            const long long kb_rows = std::max<long long>(1, std::min<long long>(La, (256LL << 20) / (8LL * La)));
+            const int Nb = nlines / Nc;
             Carve lc;
             const size_t o_list = lc.take<int>(La), o_lslot = lc.take<int>(nlines),
                          o_lF = lc.take<double>(static_cast<size_t>(nodes) * La),
                          o_lG = lc.take<double>(static_cast<size_t>(nodes) * La),
-                         o_Kb = lc.take<double>(static_cast<size_t>(kb_rows) * La);
+                         o_Kt = lc.take<double>(static_cast<size_t>(Nb) * (2 * Nc - 1));
             if (scratch_malloc_async(reinterpret_cast<void **>(&lbase), lc.off, st) != cudaSuccess) return VDWDF_EALLOC;
             int *dlist = reinterpret_cast<int *>(lbase + o_list);
             int *dlslot = reinterpret_cast<int *>(lbase + o_lslot);
             double *lF = reinterpret_cast<double *>(lbase + o_lF), *lG = reinterpret_cast<double *>(lbase + o_lG);
-            double *Kb = reinterpret_cast<double *>(lbase + o_Kb);
+            double *Kt = reinterpret_cast<double *>(lbase + o_Kt);
             VDWDF_CUDA_TRY(cudaMemcpyAsync(dlist, list.data(), sizeof(int) * La, cudaMemcpyHostToDevice, st));
             VDWDF_CUDA_TRY(cudaMemcpyAsync(dlslot, lslot.data(), sizeof(int) * nlines, cudaMemcpyHostToDevice, st));
             r = launch_far_tail_lines(G.dims, ax, La, dlist, n_dev, q0, n_cut, x0, hx, nodes, gbb, gbc, gcc, r_cut,
-                                      pref, scale, lF, Kb, kb_rows, lG, Tk, Tout, st);
+                                      pref, scale, lF, Kt, lG, Tk, Tout, st);
             if (r) return r;
             line_slot = dlslot;
             Gl = lG;

@@ -217,12 +217,12 @@ int launch_far_tail_line_flags(const int dims[3], int ax, const double *n, doubl
                                cudaStream_t st);
 // One periodic axis: the same sums over the La active lines `lines` (line ids):
 // F (nodes x La), K between lines (pref I(rho, x0), rho^2 from the index
-// differences through gbb, gbc, gcc) kb_rows rows at a time in Kb (kb_rows x La),
-// G (nodes x La) = K F, Tk (nodes) and out as launch_far_tail.
+// differences through gbb, gbc, gcc) as a table Kt (N_b x (2 N_c - 1)) over the
+// index differences, G (nodes x La) = K F, Tk (nodes) and out as launch_far_tail.
 int launch_far_tail_lines(const int dims[3], int ax, int La, const int *lines, const double *n, const double *q0,
                           double n_cut, double x0, double hx, int nodes, double gbb, double gbc, double gcc,
-                          double rc, double pref, double scale, double *F, double *Kb, long long kb_rows,
-                          double *G, double *Tk, double *out, cudaStream_t st);
+                          double rc, double pref, double scale, double *F, double *Kt, double *G, double *Tk,
+                          double *out, cudaStream_t st);
 // The far field's potential in the pair sum's adjoint form on the grid: A, U (N)
 // at active points with slot[m] = m, slot[m] = -1 elsewhere (for launch_assemble).
 // line_slot (one periodic axis; else NULL): the active-line index of every line,

@@ -12,8 +12,8 @@
 //
 // On the grid, z depends only on the plane of the non-periodic axis, and
 // 1/(u_i + u_j) = int_0^inf exp(-(u_i + u_j) s) ds separates i from j.  With
-// s = e^x and the trapezoidal rule in x (step hx; the integrand is analytic in
-// the strip |Im x| < pi/2, so the error falls like exp(-pi^2 / hx)),
+// s = e^x and the trapezoidal rule in x (step hx = 0.3; the integrand is analytic
+// in the strip |Im x| < pi/2, so the error falls like exp(-pi^2 / hx)),
 //   T = -1/2 dV^2 C sum_k hx s_k sum_{p, p'} K(p, p') F_k(p) F_k(p'),
 //   F_k(p) = sum over active points of plane p of (n / u) exp(-u s_k).
 // That is O(N_grid x nodes) work for the planes and O(planes^2 x nodes) for the
@@ -27,8 +27,8 @@
 // rho_ij the distance of r_i - r_j from the axis direction and
 // x0 = sqrt(max(0, r_cut^2 - rho^2)).  rho depends only on the grid lines along
 // a that hold i and j, so the lines take the place of the planes: F_k per
-// line with an active point, K over pairs of such lines (k_tail_line_K, in
-// blocks of rows), G_k = K F_k as a tiled FP64 product (k_tail_line_G).
+// line with an active point, K as a table over the lines' index differences
+// (k_tail_line_Ktab), G_k = K F_k as a tiled FP64 product (k_tail_line_G).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -291,42 +291,61 @@ __device__ double line_tail_I(double rho, double x0) {
     return 3.0 * atan(e) / (8.0 * r2 * r2 * rho) - x0 / (4.0 * r2 * s * s) - 3.0 * x0 / (8.0 * r2 * r2 * s);
 }
 
-// Kb[i * La + a'] = K(lines[r0 + i], lines[a']) for i < R: the squared distance
-// between two lines from their index differences through the metric (gbb, gbc,
-// gcc) of the axis steps with their components along the periodic axis removed.
-__global__ void k_tail_line_K(int r0, int R, int La, const int *__restrict__ lines, int Nc, double gbb,
-                              double gbc, double gcc, double rc, double pref, double *__restrict__ Kb) {
-    const long long total = static_cast<long long>(R) * La;
+// Kt[db * (2 N_c - 1) + dc + N_c - 1] = K between two lines whose index differences
+// are (db, dc), 0 <= db < N_b, |dc| < N_c: the squared distance through the metric
+// (gbb, gbc, gcc) of the axis steps with their components along the periodic axis
+// removed.  K depends on the lines only through (db, dc), and K(-db, -dc) = K(db, dc).
+__global__ void k_tail_line_Ktab(int Nb, int Nc, double gbb, double gbc, double gcc, double rc, double pref,
+                                 double *__restrict__ Kt) {
+    const int W = 2 * Nc - 1;
+    const long long total = static_cast<long long>(Nb) * W;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(e / La), a2 = static_cast<int>(e % La);
-        const int l1 = lines[r0 + i], l2 = lines[a2];
-        const double db = static_cast<double>(l1 / Nc - l2 / Nc), dc = static_cast<double>(l1 % Nc - l2 % Nc);
+        const double db = static_cast<double>(e / W), dc = static_cast<double>(e % W - (Nc - 1));
         double p2 = gbb * db * db + 2.0 * gbc * db * dc + gcc * dc * dc;
         p2 = p2 > 0.0 ? p2 : 0.0;
         // x0 = sqrt(rc^2 - rho^2) is singular at rho = rc, where lattice-aligned line
         // pairs sit exactly: a difference within 1e-12 rc^2 of zero counts as zero
         // (as the pair sum's inclusive cutoff), so rounding does not decide them
         const double x2 = rc * rc - p2;
-        Kb[e] = pref * line_tail_I(sqrt(p2), x2 > 1e-12 * rc * rc ? sqrt(x2) : 0.0);
+        Kt[e] = pref * line_tail_I(sqrt(p2), x2 > 1e-12 * rc * rc ? sqrt(x2) : 0.0);
     }
 }
 
-// G[k * La + r0 + i] = sum_a' Kb[i * La + a'] F[k * La + a'] for i < R, k < nodes: a
-// 32 x 32 output tile per block of 16 x 16 threads (2 x 2 each), the a' range in
-// shared-memory tiles of 32, summed in a fixed order.
+// G[k * La + i] = sum_a K(lines[i], lines[a]) F[k * La + a] for every active line i
+// and node k: a 32 x 32 output tile per block of 16 x 16 threads (2 x 2 each), the a
+// range in shared-memory tiles of 32, K from the table Kt, summed in a fixed order.
 constexpr int kGT = 32;
-__global__ void __launch_bounds__(256) k_tail_line_G(int r0, int R, int La, int nodes, const double *__restrict__ Kb,
-                                                     const double *__restrict__ F, double *__restrict__ G) {
+__global__ void __launch_bounds__(256) k_tail_line_G(int La, int nodes, const int *__restrict__ lines, int Nc,
+                                                     const double *__restrict__ Kt, const double *__restrict__ F,
+                                                     double *__restrict__ G) {
     __shared__ double sK[kGT][kGT + 1], sF[kGT][kGT + 1];
+    __shared__ int rb[kGT], rcl[kGT];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int i0 = blockIdx.x * kGT, k0 = blockIdx.y * kGT;
+    const int W = 2 * Nc - 1;
+    if (threadIdx.x < kGT) {
+        const int l = (i0 + threadIdx.x < La) ? lines[i0 + threadIdx.x] : 0;
+        rb[threadIdx.x] = l / Nc;
+        rcl[threadIdx.x] = l % Nc;
+    }
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
     for (int a0 = 0; a0 < La; a0 += kGT) {
+        __syncthreads();  // rb, rcl written; the previous tiles read
         for (int e = threadIdx.x; e < kGT * kGT; e += 256) {
             const int r = e / kGT, cc = e % kGT;
             const int i = i0 + r, k = k0 + r, a = a0 + cc;
-            sK[r][cc] = (i < R && a < La) ? Kb[static_cast<long long>(i) * La + a] : 0.0;
+            double kv = 0.0;
+            if (i < La && a < La) {
+                const int l2 = lines[a];
+                int db = rb[r] - l2 / Nc, dc = rcl[r] - l2 % Nc;
+                if (db < 0) {
+                    db = -db;
+                    dc = -dc;
+                }
+                kv = Kt[static_cast<long long>(db) * W + dc + Nc - 1];
+            }
+            sK[r][cc] = kv;
             sF[r][cc] = (k < nodes && a < La) ? F[static_cast<long long>(k) * La + a] : 0.0;
         }
         __syncthreads();
@@ -339,14 +358,13 @@ __global__ void __launch_bounds__(256) k_tail_line_G(int r0, int R, int La, int 
             acc[1][0] += k_1 * f_0;
             acc[1][1] += k_1 * f_1;
         }
-        __syncthreads();
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int v = 0; v < 2; ++v) {
             const int i = i0 + ty + 16 * u, k = k0 + tx + 16 * v;
-            if (i < R && k < nodes) G[static_cast<long long>(k) * La + r0 + i] = acc[u][v];
+            if (i < La && k < nodes) G[static_cast<long long>(k) * La + i] = acc[u][v];
         }
 }
 
@@ -383,27 +401,21 @@ int launch_far_tail_line_flags(const int dims[3], int ax, const double *n, doubl
 
 int launch_far_tail_lines(const int dims[3], int ax, int La, const int *lines, const double *n, const double *q0,
                           double n_cut, double x0, double hx, int nodes, double gbb, double gbc, double gcc,
-                          double rc, double pref, double scale, double *F, double *Kb, long long kb_rows,
-                          double *G, double *Tk, double *out, cudaStream_t st) {
-    const int Nc = ax == 2 ? dims[1] : dims[2];  // lines are ib * N_c + ic, b < c the other axes
+                          double rc, double pref, double scale, double *F, double *Kt, double *G, double *Tk,
+                          double *out, cudaStream_t st) {
+    // lines are ib * N_c + ic, b < c the other two axes
+    const int Nb = ax == 0 ? dims[1] : dims[0], Nc = ax == 2 ? dims[1] : dims[2];
     const int wpb = kTailThreads / 32;
     k_tail_line_F<<<(La + wpb - 1) / wpb, kTailThreads, 0, st>>>(dims[0], dims[1], dims[2], ax, La, lines, n, q0,
                                                                  n_cut, x0, hx, nodes, F);
-    int launches = 1;
-    for (int r0 = 0; r0 < La; r0 += static_cast<int>(kb_rows)) {
-        const int R = static_cast<int>(std::min<long long>(kb_rows, La - r0));
-        const long long total = static_cast<long long>(R) * La;
-        long long nb = (total + kTailThreads - 1) / kTailThreads;
-        if (nb > 152 * 32) nb = 152 * 32;
-        k_tail_line_K<<<static_cast<int>(nb), kTailThreads, 0, st>>>(r0, R, La, lines, Nc, gbb, gbc, gcc, rc,
-                                                                     pref, Kb);
-        k_tail_line_G<<<dim3((R + kGT - 1) / kGT, (nodes + kGT - 1) / kGT), 256, 0, st>>>(r0, R, La, nodes, Kb, F,
-                                                                                          G);
-        launches += 2;
-    }
+    const long long kt = static_cast<long long>(Nb) * (2 * Nc - 1);
+    k_tail_line_Ktab<<<static_cast<int>(std::min<long long>((kt + kTailThreads - 1) / kTailThreads, 152 * 8)),
+                       kTailThreads, 0, st>>>(Nb, Nc, gbb, gbc, gcc, rc, pref, Kt);
+    k_tail_line_G<<<dim3((La + kGT - 1) / kGT, (nodes + kGT - 1) / kGT), 256, 0, st>>>(La, nodes, lines, Nc, Kt, F,
+                                                                                       G);
     k_tail_line_Tk<<<nodes, kTailThreads, 0, st>>>(La, F, G, Tk);
     k_tail_final<<<1, 32, 0, st>>>(nodes, Tk, x0, hx, scale, out);
-    count_launches(launches + 2);
+    count_launches(5);
     VDWDF_CUDA_TRY(cudaGetLastError());
     return VDWDF_OK;
 }

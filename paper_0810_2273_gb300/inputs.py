@@ -157,6 +157,18 @@ def xe_monolayer_hex(dims=(48, 48, 120)):
     return w
 
 
+def rare_gas_chain(dims=(24, 72, 72)):
+    """A chain of rare-gas atoms 8.2 bohr apart along x (one per 8.2 x 24 x 24 cell,
+    at the centre of the cross-section), periodic along x only: the one-axis
+    counterpart of xe_monolayer, with its grid spacing (0.34 bohr), 20 bohr pair
+    cutoff, 1% multiplicative noise and density cutoff 1e-6."""
+    L = (8.2, 24.0, 24.0)
+    atoms = [((4.1, 12.0, 12.0), rare_gas_shells())]
+    n = density(dims, L, atoms, periodic=(True, False, False))
+    n = _noise(n, _rng(6), 0.01)
+    return _workload("rare_gas_chain", 6, n, L, (True, False, False), 1e-6, 20.0, atoms=atoms)
+
+
 def molecule24(dims=(64, 64, 64)):
     """24 atoms uniform in [3, 21]^3 (minimum separation 2.5 bohr) in a 24 bohr open
     cube; each Z / (8 pi a^3) exp(-r / a), a ~ U[0.4, 0.9], Z from {1, 4, 6}."""

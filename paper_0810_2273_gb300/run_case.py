@@ -5,7 +5,8 @@
         [--precision fp32|fp64] [--gradient fd|spectral] [--repeat 3]
 
 Workloads are the seeded densities of ``paper_0810_2273_gb300.inputs``
-(kr_dimer, xe_monolayer, molecule24, slab_adsorbate); --dims regrids the
+(kr_dimer, xe_monolayer, xe_monolayer_hex, rare_gas_chain, molecule24,
+slab_adsorbate); --dims regrids the
 same cell.  The kernel table is built on the host (quadrature level 1) or
 loaded from --table (an .npz written by Table.save).
 """
@@ -17,7 +18,8 @@ import time
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--workload", default="xe_monolayer",
-                    choices=["kr_dimer", "xe_monolayer", "xe_monolayer_hex", "molecule24", "slab_adsorbate"])
+                    choices=["kr_dimer", "xe_monolayer", "xe_monolayer_hex", "rare_gas_chain", "molecule24",
+                             "slab_adsorbate"])
     ap.add_argument("--dims", type=int, nargs=3, default=None)
     ap.add_argument("--mode", default="potential",
                     choices=["potential", "energy", "semilocal", "diag", "gradient", "tail", "compare"])

@@ -2,7 +2,7 @@
 for one, two and three periodic axes)
 through the C ABI against the oracle's plain O(N^2) sum: FP64 throughout on the
 GPU, so the bar is 1e-11 relative (the GPU's quadrature in ln s errs by less
-than 1e-15).  Also its refusals and E + T through the GPU converging with r_cut."""
+than 2e-13).  Also its refusals and E + T through the GPU converging with r_cut."""
 import numpy as np
 import pytest
 
