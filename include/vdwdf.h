@@ -515,9 +515,10 @@ int64_t vdwdf_launch_count(void);
  *  ms_out:         out (host, may be NULL), the timed launch's duration.
  * Every SM runs as many 512-thread blocks as fit at once, each thread 8
  * independent FMA chains, so the launch measures the pipe's throughput.  One
- * calibration launch sizes the timed one; both are timed with CUDA events on
- * the stream, which the call synchronises.  A 16-byte device scratch is
- * allocated on the stream and freed before return.
+ * calibration launch sizes the timed one, which is sized again (at most three
+ * times) while it lasts under half of target_ms; all are timed with CUDA
+ * events on the stream, which the call synchronises: 2 to 4 launches.  A
+ * 16-byte device scratch is allocated on the stream and freed before return.
  * Errors: VDWDF_EINVAL for an unknown kind, a NULL lane_ops_per_s or a
  * target_ms outside 1..1000 (checked before any CUDA call); VDWDF_EALLOC;
  * VDWDF_ECUDA. */

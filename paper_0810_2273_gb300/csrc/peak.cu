@@ -10,8 +10,9 @@
 // its counter and branch take about 2 % of the issue slots.  kChains chains per thread and full
 // occupancy keep far more independent operations in flight per scheduler than
 // the pipes' latency needs, so the launch measures the pipe's throughput.  The
-// host times one calibration launch, then one launch sized to the requested
-// duration, with CUDA events on the caller's stream.
+// host times one calibration launch, then a launch sized to the requested
+// duration (sized again while it comes out under half of it, at most three
+// times), with CUDA events on the caller's stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -130,9 +131,11 @@ extern "C" int vdwdf_lane_rate(int kind, double target_ms, double *lane_ops_per_
     auto body = [&]() -> int {
         VDWDF_CUDA_TRY(cudaEventCreate(&e0));
         VDWDF_CUDA_TRY(cudaEventCreate(&e1));
-        // calibration: launch overhead makes this estimate of the rate low, so the
-        // sized launch below lasts at most about target_ms
-        for (int pass = 0; pass < 2; ++pass) {
+        // calibration: launch overhead makes each estimate of the rate low, so a
+        // sized launch lasts at most about target_ms; one that came out shorter
+        // than half of it (an overhead-dominated estimate) is sized again, up to
+        // three times
+        for (int pass = 0; pass < 4; ++pass) {
             VDWDF_CUDA_TRY(cudaEventRecord(e0, st));
             int r = launch_rate(kind, blocks, static_cast<int>(steps), out, st);
             if (r) return r;
@@ -141,11 +144,10 @@ extern "C" int vdwdf_lane_rate(int kind, double target_ms, double *lane_ops_per_
             float f = 0.0f;
             VDWDF_CUDA_TRY(cudaEventElapsedTime(&f, e0, e1));
             ms = f;
-            if (pass == 0) {
-                const double scale = target_ms / std::max(ms, 1e-3);
-                steps = std::clamp(static_cast<long long>(static_cast<double>(steps) * scale), 256LL, 1LL << 28);
-                steps &= ~15LL;  // whole unrolled blocks of the step loop
-            }
+            if (pass > 0 && (ms >= 0.5 * target_ms || steps >= (1LL << 28))) break;
+            const double scale = target_ms / std::max(ms, 1e-3);
+            steps = std::clamp(static_cast<long long>(static_cast<double>(steps) * scale), 256LL, 1LL << 28);
+            steps &= ~15LL;  // whole unrolled blocks of the step loop
         }
         return VDWDF_OK;
     };

@@ -1,7 +1,8 @@
 """vdwdf_lane_rate, the measured denominators of the pair kernels' ALU rooflines:
 the FP32 FMA rate must sit near the unit-count peak (SMs x 128 FP32 lanes x the
-SM clock, at most 2070 MHz on GB300), FP64 below FP32, and each call launches
-exactly two kernels (calibration and timed)."""
+SM clock, at most 2070 MHz on GB300), FP64 below FP32, each call launches
+two to four kernels (a calibration and the sized timed launches), and the
+timed launch lasts at least half of what was asked."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -25,8 +26,8 @@ def test_lane_rates(V):
     for kind in ("fp32", "fp32x2", "fp64"):
         l0 = V.launch_count()
         r, ms = V.lane_rate(kind, 20.0)
-        assert V.launch_count() - l0 == 2, kind
-        assert r > 0.0 and 0.0 < ms < 200.0, (kind, r, ms)
+        assert 2 <= V.launch_count() - l0 <= 4, kind
+        assert r > 0.0 and 10.0 <= ms < 200.0, (kind, r, ms)
         rates[kind] = r
     # the FP32 pipe: 128 lanes per SM; more than the unit count would mean the
     # kernel did less work than it counts, far less that it is not pipe-bound
