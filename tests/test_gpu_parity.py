@@ -295,3 +295,26 @@ def test_every_pattern_of_periodic_axes(V, dev, gtable, oracle_mod, oracle_splin
     assert _relerr(E, e["E"]) < (tol if prec == "fp64" else 1e-6), ("skewed", E, e["E"])
     assert res["pairs"] == e["pairs"]
     assert np.max(np.abs(v.cpu().numpy() - vo)) < tol * np.max(np.abs(vo))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-6)])
+def test_tiny_and_cell_sized_cutoffs(V, dev, gtable, oracle_mod, oracle_spline, prec, tol):
+    """r_cut below the grid spacing: no pair is inside, and E is the self term
+    alone.  r_cut just past one cell length along the only periodic axis: every
+    point meets its own first images (self-images are ordinary pairs), which the
+    pair count and E of the oracle show too."""
+    rng = np.random.default_rng(19)
+    L = (3.5, 4.2, 5.4)
+    n = rng.uniform(0.01, 0.5, size=(7, 8, 9))
+    per = (1, 0, 0)
+    E, res = V.energy(_t(n, dev), L, per, 0.2, 0.3, gtable, prec)   # h = 0.5, 0.525, 0.6 bohr
+    P = oracle_mod.Problem(n, L, per, 0.2, 0.3, oracle_spline)
+    e = P.energy()
+    assert res["pairs"] == 0 == e["pairs"]
+    # (the FP32 path sums the self term with the FP32 table's phi(0,0); E_diag is FP64)
+    assert abs(E - res["E_diag"]) <= tol * abs(E) and abs(E - e["E"]) <= tol * abs(e["E"])
+    E, res = V.energy(_t(n, dev), L, per, 0.2, 3.6, gtable, prec)
+    P = oracle_mod.Problem(n, L, per, 0.2, 3.6, oracle_spline)
+    e = P.energy()
+    assert res["pairs"] == e["pairs"] and res["pairs"] >= 2 * res["n_active"]
+    assert _relerr(E, e["E"]) < tol, (E, e["E"])
